@@ -1,0 +1,123 @@
+"""Preconditioners of Sec. 3 (oracle; test infrastructure only).
+
+M_BD (Eq. 10)      (P^T diag(N^-1) P)^-1: one n_c x n_c block per observed pixel,
+                   B_p = sum_{t in p} t^(i(t))_0 w_t w_t^T, w_t = (1, cos 2phi, sin 2phi).
+R (Eq. 11)         I - A Z E^-1 Z^T with the coarse operator E = Z^T A Z.
+M_2lvl (Eq. 12)    M_BD R + Z E^-1 Z^T, applied left to right as in App. C:
+                   v = E^-1 (Z^T r); z = M_BD (r - (AZ) v) + Z v, with AZ and the
+                   LU factors of E precomputed once (App. C, "Constructing").
+Z_D (Sec. 3.3.2)   Ritz vectors of M_BD A from a first M_BD-preconditioned solve.
+
+Reading R8 (the paper builds the Ritz pairs from GMRES/Arnoldi, Algorithm 1, and notes
+that CG serves as well): CG-Lanczos.  The k smallest eigenpairs (theta, s) of the
+tridiagonal T_m built from the CG step scalars,
+    T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},   T_{j,j+1} = sqrt(beta_j)/alpha_j,
+give Ritz vectors V_m s with Lanczos vectors v_j = (-1)^j z_j / sqrt(r_j^T z_j)
+(z_j = M_BD r_j, the preconditioned CG residuals).  The selected vectors are
+orthonormalised (Euclidean QR) and columns with |R_jj| < 1e-10 max |R_jj| dropped.
+Reading R9: E is factored by LU with partial pivoting (as App. C does).
+"""
+import numpy as np
+import scipy.linalg
+
+
+class BlockJacobi:
+    """M_BD of Eq. 10 for a oracle.system.Problem."""
+
+    def __init__(self, prob):
+        self.ncomp = prob.ncomp
+        self.npix = prob.npix_obs
+        dg = prob.ninv_diag()
+        kept = prob.pix_c >= 0
+        p = prob.pix_c[kept]
+        d = dg[kept]
+        nc = self.ncomp
+        B = np.zeros((self.npix, nc, nc), dtype=np.float64)
+        if nc == 1:
+            B[:, 0, 0] = np.bincount(p, weights=d, minlength=self.npix)
+        else:
+            w = prob.weights[kept]
+            comps = [np.ones_like(d), w[:, 0], w[:, 1]]
+            for a in range(3):
+                for b in range(a, 3):
+                    v = np.bincount(p, weights=d * comps[a] * comps[b], minlength=self.npix)
+                    B[:, a, b] = v
+                    B[:, b, a] = v
+        self.blocks = B
+        self.inv = np.linalg.inv(B)
+
+    def apply(self, r):
+        R = np.asarray(r, dtype=np.float64).reshape(self.npix, self.ncomp)
+        return np.einsum("pab,pb->pa", self.inv, R).reshape(-1)
+
+    def dense(self):
+        return scipy.linalg.block_diag(*list(self.inv))
+
+
+class TwoLevel:
+    """M_2lvl of Eq. 12 for a given deflation matrix Z (n x r)."""
+
+    def __init__(self, prob, bd, Z, route="direct"):
+        self.bd = bd
+        self.Z = np.asarray(Z, dtype=np.float64)
+        self.AZ = np.stack([prob.A(self.Z[:, j], route) for j in range(self.Z.shape[1])], axis=1)
+        self.E = self.Z.T @ self.AZ
+        self.lu = scipy.linalg.lu_factor(self.E)
+
+    def coarse(self, r):
+        """v = E^-1 Z^T r."""
+        return scipy.linalg.lu_solve(self.lu, self.Z.T @ r)
+
+    def apply(self, r):
+        r = np.asarray(r, dtype=np.float64)
+        v = self.coarse(r)
+        return self.bd.apply(r - self.AZ @ v) + self.Z @ v
+
+    def deflate(self, y):
+        """R y = y - A Z E^-1 Z^T y (Eq. 11)."""
+        return y - self.AZ @ self.coarse(y)
+
+
+def lanczos_tridiagonal(alphas, betas):
+    """T_m from m CG steps (alphas[0..m-1], betas[0..m-2])."""
+    m = len(alphas)
+    T = np.zeros((m, m), dtype=np.float64)
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    return T
+
+
+def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10):
+    """Reading R8.  zs[j] = z_j, rzs[j] = r_j^T z_j for j = 0..m-1.
+    Returns (Z with orthonormal columns, the k smallest Ritz values)."""
+    m = len(alphas)
+    T = lanczos_tridiagonal(alphas, betas)
+    theta, S = np.linalg.eigh(T)
+    kk = min(k, m)
+    V = np.stack([((-1.0) ** j) * zs[j] / np.sqrt(rzs[j]) for j in range(m)], axis=1)
+    Y = V @ S[:, :kk]
+    Q, R = np.linalg.qr(Y)
+    d = np.abs(np.diag(R))
+    keep = d >= drop_rtol * d.max()
+    return Q[:, keep], theta[:kk]
+
+
+def deflation_apriori(prob):
+    """Z_S of Eq. 16-17 (the a priori coarse space of Sec. 3.3.1): column j = fraction
+    of each pixel's hits inside interval j, Q/U rows zero; each T row sums to 1."""
+    K = prob.offsets.size - 1
+    nc = prob.ncomp
+    Z = np.zeros((prob.n, K), dtype=np.float64)
+    for j in range(K):
+        a, b = int(prob.offsets[j]), int(prob.offsets[j + 1])
+        pc = prob.pix_c[a:b]
+        pc = pc[pc >= 0]
+        cnt = np.bincount(pc, minlength=prob.npix_obs).astype(np.float64)
+        Z[0::nc, j] = cnt / prob.hits
+    return Z
+
+
+__all__ = ["BlockJacobi", "TwoLevel", "lanczos_tridiagonal", "ritz_coarse_space",
+           "deflation_apriori"]

@@ -1,0 +1,158 @@
+"""Pins of the oracle's preconditioners and Ritz construction (Sec. 3, App. A-C) -- CPU."""
+import numpy as np
+import pytest
+
+from oracle import precond
+from oracle.pcg import pcg
+from problems import oracle_problem, tiny_scan
+
+
+@pytest.fixture(scope="module", params=[1, 3])
+def prob(request):
+    ncomp = request.param
+    scan = tiny_scan(ncomp=ncomp, psds=((1.0, 3.0, 1.8), (1.2, 1.5, 1.2)), lam=10)
+    return oracle_problem(scan)
+
+
+def test_bd_equals_dense_inverse(prob):
+    bd = precond.BlockJacobi(prob)
+    P = prob.dense_P()
+    D = np.diag(prob.ninv_diag())
+    ref = np.linalg.inv(P.T @ D @ P)
+    np.testing.assert_allclose(bd.dense(), ref, rtol=1e-9, atol=1e-9)
+
+
+def _z_from_eigvecs(prob, bd, k):
+    A = prob.dense_A()
+    Minv = np.linalg.inv(bd.dense())
+    # smallest generalised eigenvectors of M_BD A  (A v = theta M_BD^-1 v)
+    import scipy.linalg
+    th, V = scipy.linalg.eigh(A, Minv)
+    return A, th, V[:, :k]
+
+
+def test_deflation_and_two_level_identities(prob):
+    bd = precond.BlockJacobi(prob)
+    rng = np.random.default_rng(0)
+    Z = rng.standard_normal((prob.n, 4))
+    tl = precond.TwoLevel(prob, bd, Z)
+    A = prob.dense_A()
+    AZ = A @ Z
+    # E = Z^T A Z is SPD (Cholesky succeeds)
+    np.linalg.cholesky(0.5 * (tl.E + tl.E.T))
+    # T4: R A Z = 0 (Eq. 11)
+    RAZ = np.stack([tl.deflate(AZ[:, j]) for j in range(4)], axis=1)
+    assert np.linalg.norm(RAZ) <= 1e-10 * np.linalg.norm(AZ)
+    # T5: M_2lvl A Z = Z (Eq. 13)
+    MAZ = np.stack([tl.apply(AZ[:, j]) for j in range(4)], axis=1)
+    assert np.linalg.norm(MAZ - Z) <= 1e-10 * np.linalg.norm(Z)
+    # T6: M_2lvl A Y = M_BD A Y when Z^T A Y = 0 (Eq. 14)
+    Y = rng.standard_normal((prob.n, 3))
+    Y = Y - Z @ np.linalg.solve(Z.T @ A @ Z, Z.T @ A @ Y)      # A-orthogonalise against Z
+    assert np.linalg.norm(Z.T @ A @ Y) <= 1e-10 * np.linalg.norm(A @ Y)
+    AY = A @ Y
+    lhs = np.stack([tl.apply(AY[:, j]) for j in range(3)], axis=1)
+    rhs = np.stack([bd.apply(AY[:, j]) for j in range(3)], axis=1)
+    assert np.linalg.norm(lhs - rhs) <= 1e-9 * np.linalg.norm(rhs)
+
+
+def test_two_level_maps_deflated_eigenvalues_to_one(prob):
+    bd = precond.BlockJacobi(prob)
+    A, th, Z = _z_from_eigvecs(prob, bd, 5)
+    tl = precond.TwoLevel(prob, bd, Z)
+    M2 = np.stack([tl.apply(e) for e in np.eye(prob.n)], axis=1)
+    ev = np.sort(np.linalg.eigvals(M2 @ A).real)
+    evbd = np.sort(th)
+    # the 5 smallest eigenvalues of M_BD A are replaced by 1, the rest are unchanged
+    expect = np.sort(np.concatenate([np.ones(5), evbd[5:]]))
+    np.testing.assert_allclose(ev, expect, rtol=1e-7, atol=1e-8)
+
+
+def test_lanczos_ritz_values_converge_to_the_spectrum(prob):
+    # T9 / Eq. 22-23: after CG has converged, the smallest Ritz value of T_m equals the
+    # smallest eigenvalue of M_BD A, every Ritz value lies inside the spectrum, and the
+    # Ritz vector of the smallest one is an eigenvector (small residual).
+    bd = precond.BlockJacobi(prob)
+    A, th, V = _z_from_eigvecs(prob, bd, 1)
+    b = np.random.default_rng(1).standard_normal(prob.n)
+    res = pcg(prob.A, bd.apply, b, 1e-14, 5 * prob.n, record=True)
+    T = precond.lanczos_tridiagonal(res.alphas, res.betas)
+    rv = np.linalg.eigvalsh(T)
+    # (CG stops after ~20 steps on a 90-dim, well clustered spectrum: the smallest
+    # Ritz value is converged to a few 1e-6, a wrong T_m would be off by O(1))
+    assert rv[0] == pytest.approx(th[0], rel=1e-4)
+    assert rv[0] >= th[0] * (1 - 1e-10) and rv[-1] <= th[-1] * (1 + 1e-10)
+    Z, theta = precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 3)
+    assert np.allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-10)
+    np.testing.assert_allclose(theta, rv[:3], rtol=1e-13)
+    v = V[:, 0] / np.linalg.norm(V[:, 0])
+    assert np.linalg.norm(v - Z @ (Z.T @ v)) < 0.05
+
+
+def test_lanczos_vectors_are_minv_orthonormal(prob):
+    bd = precond.BlockJacobi(prob)
+    b = np.random.default_rng(2).standard_normal(prob.n)
+    res = pcg(prob.A, bd.apply, b, 1e-10, 20, record=True)
+    m = len(res.alphas)
+    V = np.stack([((-1.0) ** j) * res.zs[j] / np.sqrt(res.rzs[j]) for j in range(m)], axis=1)
+    Minv = np.linalg.inv(bd.dense())
+    G = V.T @ Minv @ V
+    assert np.abs(G - np.eye(m)).max() < 1e-8
+    # M A V = V T + (rank-one remainder in the last column only)
+    A = prob.dense_A()
+    T = precond.lanczos_tridiagonal(res.alphas, res.betas)
+    Rm = bd.dense() @ A @ V - V @ T
+    assert np.linalg.norm(Rm[:, :-1]) <= 1e-8 * np.linalg.norm(V)
+
+
+def test_apriori_rows_sum_to_one(prob):
+    Z = precond.deflation_apriori(prob)
+    nc = prob.ncomp
+    np.testing.assert_allclose(Z[0::nc].sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    if nc == 3:
+        assert np.all(Z[1::3] == 0) and np.all(Z[2::3] == 0)
+
+
+def test_ones_near_nullspace_with_one_over_f():
+    # Eq. 15: A 1_p is small when the noise has a 1/f excess (N^-1 1_t ~ 0).
+    s1 = tiny_scan(ncomp=1, psds=((1.0, 20.0, 1.0),), lam=100, nper=2000)
+    s0 = tiny_scan(ncomp=1, psds=((1.0, 0.0, 1.0),), lam=100, nper=2000)
+    r = []
+    for s in (s1, s0):
+        pr = oracle_problem(s)
+        one = np.ones(pr.n)
+        A = pr.dense_A()
+        r.append(np.linalg.norm(A @ one) / (np.linalg.norm(A, 2) * np.linalg.norm(one)))
+    assert r[0] < 0.1 * r[1]
+
+
+def test_cg_iterations_obey_the_condition_number_bound(prob):
+    # Eq. 9 for PCG: ||x - x_j||_A <= 2 ||x||_A ((sqrt k - 1)/(sqrt k + 1))^j with k the
+    # condition number of M_BD A.
+    bd = precond.BlockJacobi(prob)
+    A, th, _ = _z_from_eigvecs(prob, bd, 1)
+    kappa = th[-1] / th[0]
+    b = np.random.default_rng(3).standard_normal(prob.n)
+    xs = np.linalg.solve(A, b)
+    rate = (np.sqrt(kappa) - 1) / (np.sqrt(kappa) + 1)
+    for j in (2, 5, 10):
+        res = pcg(prob.A, bd.apply, b, 0.0, j)
+        e = xs - res.x
+        assert np.sqrt(e @ A @ e) <= 2 * np.sqrt(xs @ A @ xs) * rate ** j * (1 + 1e-8)
+
+
+def test_two_level_needs_fewer_iterations():
+    # T13 (Sec. 5.1): with strong 1/f noise the a posteriori two-level preconditioner
+    # converges in fewer iterations than M_BD.
+    scan = tiny_scan(ncomp=3, W=8, H=8, ndet=2, nper=1200, K_per_det=2, lam=40,
+                     psds=((1.0, 5.0, 2.0), (1.0, 4.0, 1.5)))
+    pr = oracle_problem(scan)
+    bd = precond.BlockJacobi(pr)
+    b = np.random.default_rng(9).standard_normal(pr.n)
+    r0 = pcg(pr.A, bd.apply, b, 1e-6, 2000, record=True)
+    Z, _ = precond.ritz_coarse_space(r0.alphas, r0.betas, r0.zs, r0.rzs, 8)
+    tl = precond.TwoLevel(pr, bd, Z)
+    b2 = np.random.default_rng(10).standard_normal(pr.n)
+    it_bd = pcg(pr.A, bd.apply, b2, 1e-6, 2000).iters
+    it_2l = pcg(pr.A, tl.apply, b2, 1e-6, 2000).iters
+    assert it_2l < it_bd
