@@ -1,0 +1,223 @@
+/*
+ * libmm -- GLS map-making on one GB300 (sm_103a).
+ *
+ * Solves (P^T N^-1 P) m = P^T N^-1 d by preconditioned conjugate gradients, after
+ * Szydlarski, Grigori & Stompor, "Accelerating the cosmic microwave background
+ * map-making procedure through preconditioning" (arXiv 1408.3048):
+ *   P      pointing matrix, Eq. 1-2 (one pixel per sample; I/Q/U weights
+ *          (1, cos 2phi, sin 2phi) for a polarisation-sensitive detector)
+ *   N^-1   block-diagonal, one banded symmetric Toeplitz block per stationary
+ *          interval, Eq. 4 and Sec. 4.1.4; rows from the noise PSD of Eq. 19 apodised
+ *          by the window of Eq. 28 (App. D)
+ *   A      = P^T N^-1 P (Eq. 5), applied matrix-free as in Eq. 8
+ *   M_BD   block-Jacobi preconditioner, Eq. 10
+ *   M_2lvl two-level preconditioner, Eq. 12, with the a posteriori coarse space of
+ *          Sec. 3.3.2 (Ritz vectors of M_BD A) and the application order of App. C
+ *
+ * Conventions (every entry point):
+ *   - A plan owns all of its device buffers; it never frees caller memory.
+ *   - "device" pointers are CUDA device (or managed) memory of the current device;
+ *     "host" pointers are ordinary host memory.  Where an argument says
+ *     "host or device", the library inspects the pointer and copies as needed.
+ *   - Maps are observed-pixel ordered (ascending sky index), pixel-major, with the
+ *     ncomp Stokes components of one pixel adjacent: x[q*ncomp + c]  (n = npix_obs*ncomp).
+ *   - Time-domain vectors are in sample order, length nt.
+ *   - Work is issued on opts->stream; calls return after that work completes.
+ *   - On error a call returns a non-zero mm_status and mm_last_error() describes it;
+ *     output buffers are then unspecified.  The plan stays usable unless the status is
+ *     MM_ERR_CUDA or MM_ERR_TIMEOUT.
+ *   - Not thread-safe per plan: one call at a time on a given plan.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_plan_s* mm_plan_t;
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_ARG = 1,            /* invalid argument (sizes, offsets, pixel range, lambda) */
+    MM_ERR_CUDA = 2,           /* a CUDA runtime call failed                              */
+    MM_ERR_OOM = 3,            /* device allocation failed                                */
+    MM_ERR_NOT_SPD = 4,        /* Toeplitz symbol <= 0, p^T A p <= 0 or E not SPD         */
+    MM_ERR_NOT_CONVERGED = 5,  /* maxit reached; the best iterate is returned             */
+    MM_ERR_NUMERIC = 6,        /* NaN/Inf met in a reduction                              */
+    MM_ERR_TIMEOUT = 7,        /* a bounded device-side wait ran out                      */
+    MM_ERR_STATE = 8           /* call needs state that is not built (e.g. coarse space)  */
+} mm_status;
+
+enum { MM_FP64 = 0, MM_FP32 = 1 };                 /* operator arithmetic               */
+enum { MM_WINDOW_GAUSS = 0, MM_WINDOW_RECT = 1 };  /* apodisation window (Eq. 28 / none) */
+enum { MM_PREC_BD = 0, MM_PREC_TWOLEVEL = 1 };     /* preconditioner kind               */
+enum { MM_SOLVE_FP64 = 0, MM_SOLVE_MIXED = 1 };    /* solver arithmetic                 */
+
+/* Noise PSD of one stationary piece, Eq. 19 with exponent alpha:
+ * P(f) = sigma^2 t_samp (1 + (fknee/f)^alpha). */
+typedef struct {
+    double sigma;
+    double fknee;
+    double alpha;
+} mm_psd;
+
+typedef struct {
+    int32_t ncomp;          /* 1 (temperature) or 3 (I, Q, U)                             */
+    int32_t lambda;         /* Toeplitz half bandwidth: lags |k| <= lambda are kept       */
+    int32_t window;         /* MM_WINDOW_GAUSS (default) or MM_WINDOW_RECT                */
+    int32_t fft_log2_f64;   /* 0: automatic; else overlap-save block 2^v for FP64 (9..14) */
+    int32_t fft_log2_f32;   /* 0: automatic; else overlap-save block 2^v for FP32 (9..15) */
+    int32_t reserved;
+    double fsamp;           /* sampling frequency in Hz (> 0)                             */
+    double rcond_min;       /* I/Q/U pixel acceptance (<= 0: 1e-6), see mm_plan           */
+    void* stream;           /* cudaStream_t; NULL = legacy default stream                 */
+} mm_opts;
+
+typedef struct {
+    int32_t iters;          /* A p products in PCG (all refinement steps)                 */
+    int32_t outer;          /* refinement steps (1 for MM_SOLVE_FP64)                     */
+    int32_t converged;      /* 1 when ||b - A m|| / ||b|| <= tol                         */
+    int32_t fp64_products;  /* FP64 products A x spent on residuals (mixed)               */
+    double rel_resid;       /* final true relative residual ||b - A m||_2 / ||b||_2       */
+    double rel_resid_rec;   /* final recursive relative residual of the last PCG          */
+    double ms_total;        /* device time of the call in milliseconds                   */
+    double ms_rhs;          /* device time of b = P^T N^-1 d                             */
+} mm_stats;
+
+/*
+ * mm_plan -- build the operators of one map-making problem.
+ *
+ * Paper: Sec. 2 (data model, Eq. 1-2, full-column-rank P), Eq. 4 and Sec. 4.1.4
+ * (block-diagonal banded Toeplitz N^-1), Eq. 19 and App. D / Eq. 28 (rows from the PSD),
+ * Eq. 10 (M_BD).
+ *
+ *   out          receives the plan (host pointer to a handle).
+ *   pix          host or device int32[nt]: sky pixel of each sample, 0 <= pix < npix_sky.
+ *   nt           number of samples, 1 <= nt < 2^31.
+ *   npix_sky     number of sky pixels.
+ *   weights      host or device double[nt][2] = (cos 2phi_t, sin 2phi_t) for ncomp = 3;
+ *                must be NULL for ncomp = 1.
+ *   interval_off host int64[K+1]: interval i is samples [off[i], off[i+1]);
+ *                off[0] = 0, off[K] = nt, strictly increasing.
+ *   K            number of stationary intervals (>= 1).
+ *   interval_psd host int32[K]: PSD id of each interval, 0 <= id < npsd.
+ *   psd          host mm_psd[npsd]: sigma > 0, fknee >= 0, alpha > 0.
+ *   opts         host options; lambda must satisfy 0 <= lambda < shortest interval.
+ *
+ * Observed pixels (the columns of P): ncomp = 1 every pixel with >= 1 hit; ncomp = 3
+ * every pixel with >= 3 hits whose unit-weight block sum_t w_t w_t^T has
+ * lambda_min / lambda_max >= rcond_min.  Samples on other pixels have no entry in P.
+ * Toeplitz row: r_k = (1/L) sum_{j<L} S_{min(j,L-j)}^-1 cos(2 pi j k / L) on the grid
+ * L = 2^ceil(log2(longest interval)), S_j = sigma^2 (1 + (fknee/f_j)^alpha),
+ * f_j = j fsamp / L, S_0^-1 = lim f->0 (0 if fknee > 0); t_k = w_k r_k with
+ * w_k = exp(-2 (k/lambda)^2) (GAUSS) or 1 (RECT).  A row whose symbol
+ * t_0 + 2 sum t_k cos(w k) is <= 0 anywhere on 2^ceil(log2(8 lambda)) frequencies is
+ * rejected with MM_ERR_NOT_SPD.
+ * Errors: MM_ERR_ARG (sizes, offsets, pixels, lambda, psd), MM_ERR_NOT_SPD,
+ * MM_ERR_OOM, MM_ERR_CUDA.  On error *out is NULL.
+ */
+mm_status mm_plan(mm_plan_t* out, const int32_t* pix, int64_t nt, int32_t npix_sky,
+                  const double* weights, const int64_t* interval_off, int32_t K,
+                  const int32_t* interval_psd, const mm_psd* psd, int32_t npsd,
+                  const mm_opts* opts);
+
+/* Sizes of a plan.  Any output pointer may be NULL.  n = npix_obs * ncomp. */
+mm_status mm_plan_info(mm_plan_t plan, int32_t* npix_obs, int64_t* n, int64_t* nkept,
+                       int32_t* fft_block_f64, int32_t* fft_block_f32);
+
+/* obs2sky[q] (sky index of observed pixel q) and hits[q] (its sample count), both
+ * host or device int32[npix_obs]; either may be NULL.  Bit-exact integer outputs. */
+mm_status mm_plan_pixels(mm_plan_t plan, int32_t* obs2sky, int32_t* hits);
+
+/* The Toeplitz row t_k, k = 0..lambda, of PSD id `psd_id` (host double[lambda+1]). */
+mm_status mm_plan_row(mm_plan_t plan, int32_t psd_id, double* row);
+
+/*
+ * y = P x (de-pointing, Eq. 2; Sec. 2).  x device [n], y device [nt], in the arithmetic
+ * `precision` (double for MM_FP64, float for MM_FP32).  Dropped samples give 0.
+ */
+mm_status mm_gather(mm_plan_t plan, int precision, const void* x, void* y);
+
+/*
+ * z = N^-1 y: the banded Toeplitz block of each stationary interval applied to that
+ * interval only (Eq. 4, band of Sec. 4.1.4).  y, z device [nt] in `precision`.
+ * Computed by overlap-save FFT in shared memory.
+ */
+mm_status mm_apply_ninv(mm_plan_t plan, int precision, const void* y, void* z);
+
+/*
+ * w = P^T z (pointing / scatter-add, Sec. 2).  z device [nt], w device [n] in
+ * `precision`.  Deterministic segmented reduction over pixel-sorted samples.
+ */
+mm_status mm_scatter(mm_plan_t plan, int precision, const void* z, void* w);
+
+/* y = A x = P^T [N^-1 [P x]] (Eq. 5, 8).  x, y device [n] in `precision`. */
+mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y);
+
+/* b = P^T N^-1 d (Eq. 7).  d device [nt] double, b device [n] double (FP64 arithmetic). */
+mm_status mm_rhs(mm_plan_t plan, const double* d, double* b);
+
+/*
+ * z = M r with M = M_BD (Eq. 10; kind MM_PREC_BD) or M_2lvl (Eq. 12; MM_PREC_TWOLEVEL,
+ * applied as in App. C: v = E^-1 Z^T r, z = M_BD (r - (AZ) v) + Z v).
+ * r, z device [n] in `precision`.  TWOLEVEL needs mm_build_coarse first (MM_ERR_STATE).
+ */
+mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, void* z);
+
+/*
+ * Build the a posteriori coarse space Z_D of Sec. 3.3.2 (steps listed there; App. A):
+ * one M_BD-preconditioned CG solve of A x' = b' (in `precision`, to rel. residual `tol`,
+ * at most `maxit` steps), the Lanczos tridiagonal of that solve
+ * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), its k
+ * smallest Ritz pairs, Ritz vectors Z = sum_j (-1)^j z_j / sqrt(r_j^T z_j) s_j,
+ * Euclidean orthonormalisation (columns with R_jj < 1e-10 max R_jj dropped), then
+ * AZ = A Z (FP64) and E = Z^T A Z, Cholesky-factored in FP64 (App. C, "Constructing").
+ *   k       requested coarse dimension, 1 <= k <= 64.
+ *   bprime  device double[n] right-hand side of the first solve, or NULL for b' = the
+ *           b of the last mm_solve (MM_ERR_STATE if there was none).
+ * Errors: MM_ERR_NOT_SPD when E is not positive definite.
+ */
+mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bprime,
+                          double tol, int maxit);
+
+/* Kept coarse dimension and the k smallest Ritz values (host double[k], may be NULL). */
+mm_status mm_coarse_info(mm_plan_t plan, int32_t* k_kept, double* ritz_values);
+
+/* The orthonormal coarse basis Z (FP64), column j at Z[j*n .. j*n + n), host or device
+ * double[k_kept * n].  MM_ERR_STATE before mm_build_coarse. */
+mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
+
+/*
+ * Solve A m = P^T N^-1 d by PCG from m_0 = 0 (Sec. 3.1), stopping when the relative
+ * residual ||b - A m||_2 / ||b||_2 <= tol (the convergence measure of Sec. 5.1).
+ *   d       host or device double[nt] time-ordered data.
+ *   kind    MM_PREC_BD or MM_PREC_TWOLEVEL.
+ *   solver  MM_SOLVE_FP64: all arithmetic FP64, stopping on the recursive residual.
+ *           MM_SOLVE_MIXED: FP32 gather / Toeplitz / scatter and FP32 vectors with FP64
+ *           dot products and step scalars inside PCG, FP64 E factor and solve, and an
+ *           outer FP64 iterative-refinement loop m += A^-1 (b - A m) that stops on the
+ *           true FP64 residual.
+ *   m       host or device double[n] output map.
+ *   st      host stats (may be NULL).
+ * Returns MM_ERR_NOT_CONVERGED (m = last iterate, st filled) when maxit is reached.
+ */
+mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int kind,
+                   int solver, double* m, mm_stats* st);
+
+/* Human-readable description of the last error on this plan (never NULL). */
+const char* mm_last_error(mm_plan_t plan);
+
+/* Release every device and host buffer of the plan.  NULL is accepted. */
+void mm_destroy(mm_plan_t plan);
+
+/* Library version string. */
+const char* mm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

@@ -1,0 +1,939 @@
+// C-ABI entry points of libmm (declared in include/mm.h) and the host drivers behind
+// them: plan construction (Sec. 2 observed pixels, Eq. 4 / App. D Toeplitz rows,
+// overlap-save tiling, Eq. 10 M_BD), operator applications (Eq. 5-8), the PCG driver
+// (Sec. 3.1) with FP64 or mixed arithmetic plus iterative refinement, and the
+// a posteriori coarse space (Sec. 3.3.2, App. A, App. C).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "coarse.cuh"
+#include "coarse_host.h"
+#include "mm_internal.h"
+#include "pcg.cuh"
+
+namespace mm {
+
+static thread_local std::string g_last_error = "no error";
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        throw Error{MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+    }
+}
+
+void* dmalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error{e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e)};
+    }
+    return p;
+}
+
+void dfree(void* p) {
+    if (p != nullptr) (void)cudaFree(p);
+}
+
+template <typename T>
+static T* dalloc(size_t count) { return static_cast<T*>(dmalloc(count * sizeof(T))); }
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "memcpy H2D");
+}
+static void d2h(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "memcpy D2H");
+}
+static void sync(cudaStream_t s) { check_cuda(cudaStreamSynchronize(s), "stream synchronize"); }
+
+// ----------------------------------------------------------------------------- plan
+struct PlanHolder : Plan {
+    int* h_flags = nullptr;     // pinned
+    double* h_scal = nullptr;   // pinned
+    double* d_dot = nullptr;    // [DOT_BLOCKS + 2]
+    double* x64 = nullptr;      // [n] refinement iterate
+    double* r64 = nullptr;      // [n] refinement residual
+    double* ax64 = nullptr;     // [n]
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+static void free_tz(ToeplitzDev& t) {
+    dfree(t.tiles);
+    dfree(t.twiddle);
+    dfree(t.H);
+    t = ToeplitzDev{};
+}
+
+static void free_coarse(CoarseDev& c) {
+    dfree(c.Z64);
+    dfree(c.AZ64);
+    dfree(c.Z32);
+    dfree(c.AZ32);
+    dfree(c.L);
+    c = CoarseDev{};
+}
+
+static void destroy_plan(PlanHolder* P) {
+    if (P == nullptr) return;
+    for (void* p : {(void*)P->pixc, (void*)P->w64, (void*)P->w32, (void*)P->csr_off, (void*)P->tsort,
+                    (void*)P->wsort64, (void*)P->wsort32, (void*)P->ioff, (void*)P->ipsd, (void*)P->t0,
+                    (void*)P->bd64, (void*)P->bd32, (void*)P->tod64, (void*)P->tod32, (void*)P->dbuf,
+                    (void*)P->b64, (void*)P->d_dot, (void*)P->x64, (void*)P->r64, (void*)P->ax64})
+        dfree(p);
+    free_tz(P->tz64);
+    free_tz(P->tz32);
+    free_coarse(P->coarse);
+    PcgDev& g = P->pcg;
+    for (void* p : {(void*)g.partial, (void*)g.scal, (void*)g.flags, (void*)g.barrier, g.x, g.r, g.p, g.q, g.z,
+                    (void*)g.hist_alpha, (void*)g.hist_beta, (void*)g.hist_rz, (void*)g.hist_rr})
+        dfree(p);
+    if (P->h_flags) (void)cudaFreeHost(P->h_flags);
+    if (P->h_scal) (void)cudaFreeHost(P->h_scal);
+    if (P->ev0) (void)cudaEventDestroy(P->ev0);
+    if (P->ev1) (void)cudaEventDestroy(P->ev1);
+    if (P->ev2) (void)cudaEventDestroy(P->ev2);
+    delete P;
+}
+
+// Overlap-save block choice: minimise (tiles x B log2 B) over admissible blocks.
+template <typename T>
+static int choose_logn(const Plan& P, int forced_log2B) {
+    const int maxl = toeplitz_max_logn<T>();
+    if (forced_log2B > 0) {
+        const int logn = forced_log2B - 1;
+        if (logn < 8 || logn > maxl) throw Error{MM_ERR_ARG, "fft block size out of range"};
+        if ((int64_t(2) << logn) - 2 * (int64_t)P.lambda < 1) throw Error{MM_ERR_ARG, "fft block too short for lambda"};
+        return logn;
+    }
+    int best = -1;
+    double best_cost = 0.0;
+    for (int logn = 8; logn <= maxl; ++logn) {
+        const int64_t B = int64_t(2) << logn;
+        const int64_t Lv = B - 2 * (int64_t)P.lambda;
+        if (Lv < 1) continue;
+        int64_t tiles = 0;
+        for (int i = 0; i < P.K; ++i) {
+            const int64_t len = P.h_ioff[i + 1] - P.h_ioff[i];
+            tiles += (len + Lv - 1) / Lv;
+        }
+        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0);
+        if (best < 0 || cost < best_cost) {
+            best = logn;
+            best_cost = cost;
+        }
+    }
+    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the shared-memory FFT block"};
+    return best;
+}
+
+template <typename T>
+static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
+    tz.logn = choose_logn<T>(P, forced_log2B);
+    const int64_t N = int64_t(1) << tz.logn;
+    const int64_t B = 2 * N;
+    const int64_t Lv = B - 2 * (int64_t)P.lambda;
+    std::vector<Tile> tiles;
+    for (int i = 0; i < P.K; ++i) {
+        const int64_t a = P.h_ioff[i], b = P.h_ioff[i + 1];
+        for (int64_t s = a; s < b; s += Lv) {
+            Tile t;
+            t.out0 = s;
+            t.ibeg = a;
+            t.iend = b;
+            t.nout = (int32_t)std::min<int64_t>(Lv, b - s);
+            t.psd = P.h_ipsd[i];
+            tiles.push_back(t);
+        }
+    }
+    tz.ntiles = (int)tiles.size();
+    tz.tiles = dalloc<Tile>(tiles.size());
+    h2d(tz.tiles, tiles.data(), tiles.size() * sizeof(Tile), P.stream);
+    std::vector<T> tw((size_t)(B / 4 + 1));
+    for (int64_t k = 0; k <= B / 4; ++k) tw[(size_t)k] = (T)std::cos(2.0 * 3.14159265358979323846 * (double)k / (double)B);
+    tz.twiddle = dalloc<T>(tw.size());
+    h2d(tz.twiddle, tw.data(), tw.size() * sizeof(T), P.stream);
+    std::vector<T> H((size_t)P.npsd * (N + 1));
+    for (int p = 0; p < P.npsd; ++p) {
+        const std::vector<double> h = overlap_save_spectrum(P.rows[(size_t)p], N);
+        for (int64_t k = 0; k <= N; ++k) H[(size_t)p * (N + 1) + k] = (T)h[(size_t)k];
+    }
+    tz.H = dalloc<T>(H.size());
+    h2d(tz.H, H.data(), H.size() * sizeof(T), P.stream);
+    sync(P.stream);   // host vectors go out of scope
+}
+
+static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t npix_sky, const double* weights,
+                       const int64_t* ioff, int32_t K, const int32_t* ipsd, const mm_psd* psd, int32_t npsd,
+                       const mm_opts* o) {
+    if (o == nullptr || pix == nullptr || ioff == nullptr || ipsd == nullptr || psd == nullptr)
+        throw Error{MM_ERR_ARG, "null argument"};
+    if (o->ncomp != 1 && o->ncomp != 3) throw Error{MM_ERR_ARG, "ncomp must be 1 or 3"};
+    if ((o->ncomp == 3) != (weights != nullptr)) throw Error{MM_ERR_ARG, "weights required iff ncomp == 3"};
+    if (nt < 1 || nt >= (int64_t(1) << 31)) throw Error{MM_ERR_ARG, "nt out of range"};
+    if (npix_sky < 1 || K < 1 || npsd < 1) throw Error{MM_ERR_ARG, "npix_sky, K and npsd must be >= 1"};
+    if (!(o->fsamp > 0.0)) throw Error{MM_ERR_ARG, "fsamp must be > 0"};
+    if (o->window != MM_WINDOW_GAUSS && o->window != MM_WINDOW_RECT) throw Error{MM_ERR_ARG, "bad window"};
+    if (o->lambda < 0) throw Error{MM_ERR_ARG, "lambda must be >= 0"};
+    P.nt = nt;
+    P.npix_sky = npix_sky;
+    P.ncomp = o->ncomp;
+    P.K = K;
+    P.npsd = npsd;
+    P.lambda = o->lambda;
+    P.window = o->window;
+    P.fsamp = o->fsamp;
+    P.rcond_min = o->rcond_min > 0.0 ? o->rcond_min : 1e-6;
+    P.stream = static_cast<cudaStream_t>(o->stream);
+    P.h_ioff.assign(ioff, ioff + K + 1);
+    P.h_ipsd.assign(ipsd, ipsd + K);
+    if (P.h_ioff[0] != 0 || P.h_ioff[(size_t)K] != nt) throw Error{MM_ERR_ARG, "interval offsets must span [0, nt)"};
+    int64_t minlen = nt, maxlen = 0;
+    for (int i = 0; i < K; ++i) {
+        const int64_t len = P.h_ioff[i + 1] - P.h_ioff[i];
+        if (len <= 0) throw Error{MM_ERR_ARG, "interval offsets must increase strictly"};
+        minlen = std::min(minlen, len);
+        maxlen = std::max(maxlen, len);
+        if (P.h_ipsd[i] < 0 || P.h_ipsd[i] >= npsd) throw Error{MM_ERR_ARG, "interval psd id out of range"};
+    }
+    if ((int64_t)P.lambda >= minlen) throw Error{MM_ERR_ARG, "lambda must be < the shortest interval"};
+    for (int p = 0; p < npsd; ++p) {
+        if (!(psd[p].sigma > 0.0) || !(psd[p].fknee >= 0.0) || !(psd[p].alpha > 0.0) || !std::isfinite(psd[p].sigma) ||
+            !std::isfinite(psd[p].fknee) || !std::isfinite(psd[p].alpha))
+            throw Error{MM_ERR_ARG, "psd parameters must be sigma > 0, fknee >= 0, alpha > 0"};
+    }
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+
+    // --- host copies of the pointing
+    std::vector<int32_t> hpix((size_t)nt);
+    std::vector<double> hw;
+    if (is_device_ptr(pix)) {
+        check_cuda(cudaMemcpy(hpix.data(), pix, (size_t)nt * 4, cudaMemcpyDeviceToHost), "copy pix");
+    } else {
+        std::memcpy(hpix.data(), pix, (size_t)nt * 4);
+    }
+    if (P.ncomp == 3) {
+        hw.resize((size_t)nt * 2);
+        if (is_device_ptr(weights))
+            check_cuda(cudaMemcpy(hw.data(), weights, (size_t)nt * 16, cudaMemcpyDeviceToHost), "copy weights");
+        else
+            std::memcpy(hw.data(), weights, (size_t)nt * 16);
+    }
+    // --- observed pixels (reading: hits >= 1, or hits >= 3 and well-conditioned I/Q/U block)
+    std::vector<int32_t> hits_sky((size_t)npix_sky, 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t p = hpix[(size_t)t];
+        if (p < 0 || p >= npix_sky) throw Error{MM_ERR_ARG, "pixel index out of range"};
+        ++hits_sky[(size_t)p];
+    }
+    std::vector<char> obs((size_t)npix_sky, 0);
+    if (P.ncomp == 1) {
+        for (int32_t p = 0; p < npix_sky; ++p) obs[(size_t)p] = hits_sky[(size_t)p] >= 1;
+    } else {
+        std::vector<double> Bs((size_t)npix_sky * 6, 0.0);
+        for (int64_t t = 0; t < nt; ++t) {
+            double* b = &Bs[(size_t)hpix[(size_t)t] * 6];
+            const double c = hw[(size_t)t * 2], s = hw[(size_t)t * 2 + 1];
+            b[0] += 1.0;
+            b[1] += c;
+            b[2] += s;
+            b[3] += c * c;
+            b[4] += c * s;
+            b[5] += s * s;
+        }
+        for (int32_t p = 0; p < npix_sky; ++p)
+            obs[(size_t)p] = hits_sky[(size_t)p] >= 3 && rcond_sym3(&Bs[(size_t)p * 6]) >= P.rcond_min;
+    }
+    std::vector<int32_t> sky2obs((size_t)npix_sky, -1);
+    for (int32_t p = 0; p < npix_sky; ++p) {
+        if (obs[(size_t)p]) {
+            sky2obs[(size_t)p] = (int32_t)P.h_obs2sky.size();
+            P.h_obs2sky.push_back(p);
+            P.h_hits.push_back(hits_sky[(size_t)p]);
+        }
+    }
+    P.npix_obs = (int32_t)P.h_obs2sky.size();
+    P.n = (int64_t)P.npix_obs * P.ncomp;
+    std::vector<int32_t> pixc((size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) pixc[(size_t)t] = sky2obs[(size_t)hpix[(size_t)t]];
+    // --- pixel-sorted CSR (stable: ascending sample index inside each pixel)
+    std::vector<int32_t> off((size_t)P.npix_obs + 1, 0);
+    for (int32_t q = 0; q < P.npix_obs; ++q) off[(size_t)q + 1] = off[(size_t)q] + P.h_hits[(size_t)q];
+    P.nkept = off[(size_t)P.npix_obs];
+    std::vector<int32_t> tsort((size_t)P.nkept);
+    std::vector<double> wsort(P.ncomp == 3 ? (size_t)P.nkept * 2 : 0);
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (int64_t t = 0; t < nt; ++t) {
+            const int32_t q = pixc[(size_t)t];
+            if (q < 0) continue;
+            const int32_t j = pos[(size_t)q]++;
+            tsort[(size_t)j] = (int32_t)t;
+            if (P.ncomp == 3) {
+                wsort[(size_t)j * 2] = hw[(size_t)t * 2];
+                wsort[(size_t)j * 2 + 1] = hw[(size_t)t * 2 + 1];
+            }
+        }
+    }
+    // --- Toeplitz rows (reading R1-R4)
+    int64_t L = 1;
+    while (L < maxlen) L *= 2;
+    if (L < 2) L = 2;
+    P.L_grid = L;
+    P.rows.resize((size_t)npsd);
+    std::vector<double> t0((size_t)npsd);
+    for (int p = 0; p < npsd; ++p) {
+        P.rows[(size_t)p] = toeplitz_row(psd[p].sigma, psd[p].fknee, psd[p].alpha, L, P.fsamp, P.lambda, P.window);
+        if (!symbol_positive(P.rows[(size_t)p])) throw Error{MM_ERR_NOT_SPD, "Toeplitz row " + std::to_string(p) + " is not positive definite"};
+        t0[(size_t)p] = P.rows[(size_t)p][0];
+    }
+    // --- device buffers
+    cudaStream_t s = P.stream;
+    P.pixc = dalloc<int32_t>((size_t)nt);
+    h2d(P.pixc, pixc.data(), (size_t)nt * 4, s);
+    P.csr_off = dalloc<int32_t>(off.size());
+    h2d(P.csr_off, off.data(), off.size() * 4, s);
+    P.tsort = dalloc<int32_t>((size_t)P.nkept);
+    h2d(P.tsort, tsort.data(), (size_t)P.nkept * 4, s);
+    if (P.ncomp == 3) {
+        P.w64 = dalloc<double2>((size_t)nt);
+        h2d(P.w64, hw.data(), (size_t)nt * 16, s);
+        P.w32 = dalloc<float2>((size_t)nt);
+        launch_convert_f64_to_f32(reinterpret_cast<const double*>(P.w64), reinterpret_cast<float*>(P.w32), nt * 2, s);
+        P.wsort64 = dalloc<double2>((size_t)P.nkept);
+        h2d(P.wsort64, wsort.data(), (size_t)P.nkept * 16, s);
+        P.wsort32 = dalloc<float2>((size_t)P.nkept);
+        launch_convert_f64_to_f32(reinterpret_cast<const double*>(P.wsort64), reinterpret_cast<float*>(P.wsort32),
+                                  P.nkept * 2, s);
+    }
+    P.ioff = dalloc<int64_t>((size_t)K + 1);
+    h2d(P.ioff, P.h_ioff.data(), ((size_t)K + 1) * 8, s);
+    P.ipsd = dalloc<int32_t>((size_t)K);
+    h2d(P.ipsd, P.h_ipsd.data(), (size_t)K * 4, s);
+    P.t0 = dalloc<double>((size_t)npsd);
+    h2d(P.t0, t0.data(), (size_t)npsd * 8, s);
+    build_toeplitz<double>(P, P.tz64, o->fft_log2_f64);
+    build_toeplitz<float>(P, P.tz32, o->fft_log2_f32);
+    // M_BD (Eq. 10)
+    const size_t bdn = (size_t)P.npix_obs * (P.ncomp == 3 ? 6 : 1);
+    P.bd64 = dalloc<double>(bdn);
+    P.bd32 = dalloc<float>(bdn);
+    launch_bd_build(P, P.bd64, P.bd32, s);
+    // scratch
+    P.tod64 = dalloc<double>((size_t)nt);
+    P.tod32 = dalloc<float>((size_t)nt);
+    P.dbuf = dalloc<double>((size_t)nt);
+    P.b64 = dalloc<double>((size_t)P.n);
+    P.x64 = dalloc<double>((size_t)P.n);
+    P.r64 = dalloc<double>((size_t)P.n);
+    P.ax64 = dalloc<double>((size_t)P.n);
+    P.d_dot = dalloc<double>(DOT_BLOCKS + 4);
+    // PCG state
+    PcgDev& g = P.pcg;
+    g.n = P.n;
+    g.nblocks = std::max(1, std::min(pcg_max_blocks(P.num_sms), (P.npix_obs + 31) / 32));
+    g.partial = dalloc<double>((size_t)g.nblocks * PSTRIDE);
+    g.scal = dalloc<double>(16);
+    g.flags = dalloc<int>(8);
+    g.barrier = dalloc<unsigned>(4);
+    check_cuda(cudaMemsetAsync(g.barrier, 0, 16, s), "memset");
+    check_cuda(cudaMemsetAsync(g.flags, 0, 32, s), "memset");
+    for (void** v : {&g.x, &g.r, &g.p, &g.q, &g.z}) *v = dmalloc((size_t)P.n * 8);
+    check_cuda(cudaMallocHost(&P.h_flags, 64), "cudaMallocHost");
+    check_cuda(cudaMallocHost(&P.h_scal, 16 * 8), "cudaMallocHost");
+    check_cuda(cudaEventCreate(&P.ev0), "event");
+    check_cuda(cudaEventCreate(&P.ev1), "event");
+    check_cuda(cudaEventCreate(&P.ev2), "event");
+    sync(s);
+}
+
+// -------------------------------------------------------------------- operators
+template <typename T> static const ToeplitzDev& tz_of(const Plan& P);
+template <> const ToeplitzDev& tz_of<double>(const Plan& P) { return P.tz64; }
+template <> const ToeplitzDev& tz_of<float>(const Plan& P) { return P.tz32; }
+template <typename T> static T* tod_of(Plan& P);
+template <> double* tod_of<double>(Plan& P) { return P.tod64; }
+template <> float* tod_of<float>(Plan& P) { return P.tod32; }
+template <typename T> static const T* bd_ptr(const Plan& P);
+template <> const double* bd_ptr<double>(const Plan& P) { return P.bd64; }
+template <> const float* bd_ptr<float>(const Plan& P) { return P.bd32; }
+
+// y = A x = P^T N^-1 P x, de-pointing fused into the Toeplitz tile load (Eq. 8).
+template <typename T>
+static void apply_A(Plan& P, const T* x, T* y, const int* done) {
+    launch_toeplitz<T>(P, tz_of<T>(P), nullptr, x, tod_of<T>(P), done, P.stream);
+    launch_scatter<T>(P, tod_of<T>(P), y, done, P.stream);
+}
+
+// ---------------------------------------------------------------------------- PCG
+struct PcgOutcome {
+    int iters = 0;
+    int status = MM_OK;
+    double rr = 0.0, bb = 0.0;
+};
+
+template <typename T>
+static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
+    PcgArgs<T> a{};
+    PcgDev& g = P.pcg;
+    a.n = P.n;
+    a.npix = P.npix_obs;
+    a.maxit = maxit;
+    a.x = static_cast<T*>(g.x);
+    a.r = static_cast<T*>(g.r);
+    a.p = static_cast<T*>(g.p);
+    a.q = static_cast<T*>(g.q);
+    a.z = static_cast<T*>(g.z);
+    a.bd = bd_ptr<T>(P);
+    if (two) {
+        a.k = P.coarse.k;
+        if constexpr (sizeof(T) == 8) {
+            a.Z = reinterpret_cast<const T*>(P.coarse.Z64);
+            a.AZ = reinterpret_cast<const T*>(P.coarse.AZ64);
+        } else {
+            a.Z = reinterpret_cast<const T*>(P.coarse.Z32);
+            a.AZ = reinterpret_cast<const T*>(P.coarse.AZ32);
+        }
+        a.L = P.coarse.L;
+    }
+    a.partial = g.partial;
+    a.scal = g.scal;
+    a.flags = g.flags;
+    a.bar = g.barrier;
+    a.hist_alpha = g.hist_alpha;
+    a.hist_beta = g.hist_beta;
+    a.hist_rz = g.hist_rz;
+    a.hist_rr = g.hist_rr;
+    a.maxhist = g.maxhist;
+    return a;
+}
+
+// Runs PCG on the right-hand side already stored in pcg.r (as T); solution in pcg.x.
+template <typename T>
+static PcgOutcome run_pcg(PlanHolder& P, bool two, double tol, int maxit, T* zstore, int maxstore) {
+    cudaStream_t s = P.stream;
+    PcgArgs<T> a = pcg_args<T>(P, two, maxit);
+    a.zstore = zstore;
+    a.maxstore = maxstore;
+    P.h_scal[0] = tol * tol;
+    h2d(P.pcg.scal + SC_TOL2, P.h_scal, 8, s);
+    const int nb = P.pcg.nblocks;
+    launch_pcg<T>(0, P.ncomp, two, a, nb, s);
+    int launched = 0;
+    int chunk = 4;
+    PcgOutcome out;
+    while (true) {
+        d2h(P.h_flags, P.pcg.flags, 16, s);
+        sync(s);
+        if (P.h_flags[F_DONE]) break;
+        if (launched >= maxit) break;   // defensive: device counter stops at maxit
+        const int c = std::min(chunk, maxit - launched + 1);
+        for (int i = 0; i < c; ++i) {
+            apply_A<T>(P, a.p, static_cast<T*>(P.pcg.q), P.pcg.flags + F_DONE);
+            launch_pcg<T>(1, P.ncomp, two, a, nb, s);
+        }
+        launched += c;
+        chunk = std::min(chunk * 2, 16);
+    }
+    d2h(P.h_scal + 4, P.pcg.scal, 4 * 8, s);
+    sync(s);
+    out.iters = P.h_flags[F_ITER];
+    out.status = P.h_flags[F_STATUS];
+    out.rr = P.h_scal[4 + SC_RR];
+    out.bb = P.h_scal[4 + SC_BB];
+    if (out.status == MM_ERR_TIMEOUT) throw Error{MM_ERR_TIMEOUT, "grid barrier wait ran out"};
+    return out;
+}
+
+static double dot64(PlanHolder& P, const double* a, const double* b) {
+    launch_dot64(a, b, P.n, P.d_dot, P.d_dot + DOT_BLOCKS, P.stream);
+    d2h(P.h_scal + 8, P.d_dot + DOT_BLOCKS, 8, P.stream);
+    sync(P.stream);
+    return P.h_scal[8];
+}
+
+// ------------------------------------------------------------------- coarse space
+static void ensure_history(PlanHolder& P, int m) {
+    PcgDev& g = P.pcg;
+    if (g.maxhist >= m + 1) return;
+    dfree(g.hist_alpha);
+    dfree(g.hist_beta);
+    dfree(g.hist_rz);
+    dfree(g.hist_rr);
+    g.hist_alpha = g.hist_beta = g.hist_rz = g.hist_rr = nullptr;
+    g.maxhist = 0;
+    g.hist_alpha = dalloc<double>((size_t)m + 1);
+    g.hist_beta = dalloc<double>((size_t)m + 1);
+    g.hist_rz = dalloc<double>((size_t)m + 1);
+    g.hist_rr = dalloc<double>((size_t)m + 1);
+    g.maxhist = m + 1;
+}
+
+static std::vector<double> gram_host(PlanHolder& P, const double* A, int ka, const double* B, int kb) {
+    double* part = dalloc<double>((size_t)GRAM_BLOCKS * ka * kb);
+    std::vector<double> hp((size_t)GRAM_BLOCKS * ka * kb);
+    try {
+        const int nb = launch_gram(A, ka, B, kb, P.n, part, P.stream);
+        d2h(hp.data(), part, hp.size() * 8, P.stream);
+        sync(P.stream);
+        dfree(part);
+        std::vector<double> G((size_t)ka * kb, 0.0);
+        for (int b = 0; b < nb; ++b)
+            for (int i = 0; i < ka * kb; ++i) G[(size_t)i] += hp[(size_t)b * ka * kb + i];
+        return G;
+    } catch (...) {
+        dfree(part);
+        throw;
+    }
+}
+
+template <typename T>
+static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol, int maxit) {
+    cudaStream_t s = P.stream;
+    if (k < 1 || k > KMAX) throw Error{MM_ERR_ARG, "k must be in [1, 64]"};
+    if (maxit < 1) throw Error{MM_ERR_ARG, "maxit must be >= 1"};
+    const double* bsrc = bprime;
+    if (bsrc == nullptr) {
+        if (!P.have_b) throw Error{MM_ERR_STATE, "no right-hand side: pass bprime or call mm_solve first"};
+        bsrc = P.b64;
+    }
+    // first solve with M_BD, keeping z_j and the step scalars (Sec. 3.3.2 step 1)
+    if constexpr (sizeof(T) == 8) {
+        check_cuda(cudaMemcpyAsync(P.pcg.r, bsrc, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b'");
+    } else {
+        launch_convert_f64_to_f32(bsrc, static_cast<float*>(P.pcg.r), P.n, s);
+    }
+    ensure_history(P, maxit);
+    T* zstore = static_cast<T*>(dmalloc((size_t)(maxit + 1) * P.n * sizeof(T)));
+    double* Y = nullptr;
+    double* Y2 = nullptr;
+    double* C = nullptr;
+    try {
+        const PcgOutcome o = run_pcg<T>(P, false, tol, maxit, zstore, maxit + 1);
+        if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED)
+            throw Error{(mm_status)o.status, "first solve of the coarse construction failed"};
+        const int m = o.iters;   // alphas 0..m-1, betas 0..m-2, z_0..z_{m-1}
+        if (m < 1) throw Error{MM_ERR_STATE, "first solve took no step"};
+        std::vector<double> al((size_t)m), be((size_t)std::max(m - 1, 1)), rz((size_t)m);
+        d2h(al.data(), P.pcg.hist_alpha, (size_t)m * 8, s);
+        if (m > 1) d2h(be.data(), P.pcg.hist_beta, (size_t)(m - 1) * 8, s);
+        d2h(rz.data(), P.pcg.hist_rz, (size_t)m * 8, s);
+        sync(s);
+        // Lanczos tridiagonal of M_BD A (App. A, CG form)
+        std::vector<double> d((size_t)m), e((size_t)std::max(m - 1, 0));
+        for (int j = 0; j < m; ++j) d[(size_t)j] = 1.0 / al[(size_t)j] + (j > 0 ? be[(size_t)j - 1] / al[(size_t)j - 1] : 0.0);
+        for (int j = 0; j + 1 < m; ++j) e[(size_t)j] = std::sqrt(be[(size_t)j]) / al[(size_t)j];
+        std::vector<double> theta, S;
+        const int kk = std::min(k, m);
+        tridiag_smallest(d, e, kk, theta, S);
+        // Ritz vectors Y = sum_j (-1)^j z_j / sqrt(r_j^T z_j) S_j  (step 2-4)
+        std::vector<double> Cs((size_t)m * kk);
+        for (int j = 0; j < m; ++j) {
+            const double f = ((j & 1) ? -1.0 : 1.0) / std::sqrt(rz[(size_t)j]);
+            for (int c = 0; c < kk; ++c) Cs[(size_t)j * kk + c] = f * S[(size_t)j * kk + c];
+        }
+        C = dalloc<double>(Cs.size());
+        h2d(C, Cs.data(), Cs.size() * 8, s);
+        Y = dalloc<double>((size_t)kk * P.n);
+        launch_lincomb<T>(zstore, m, P.n, C, kk, Y, s);
+        sync(s);
+        dfree(zstore);
+        zstore = nullptr;
+        dfree(C);
+        C = nullptr;
+        // Euclidean orthonormalisation, twice (CholQR2); drop dependent columns first pass
+        int kcur = kk;
+        for (int pass = 0; pass < 2; ++pass) {
+            const std::vector<double> G = gram_host(P, Y, kcur, Y, kcur);
+            std::vector<double> W;
+            std::vector<int> kept;
+            if (!cholesky_drop(G, kcur, pass == 0 ? 1e-10 : 0.0, W, kept))
+                throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
+            const int knew = (int)kept.size();
+            C = dalloc<double>(W.size());
+            h2d(C, W.data(), W.size() * 8, s);
+            Y2 = dalloc<double>((size_t)knew * P.n);
+            launch_lincomb<double>(Y, kcur, P.n, C, knew, Y2, s);
+            sync(s);
+            dfree(C);
+            C = nullptr;
+            dfree(Y);
+            Y = Y2;
+            Y2 = nullptr;
+            kcur = knew;
+        }
+        free_coarse(P.coarse);
+        CoarseDev& cd = P.coarse;
+        cd.k = kcur;
+        cd.ritz = theta;
+        cd.Z64 = Y;
+        Y = nullptr;
+        cd.AZ64 = dalloc<double>((size_t)kcur * P.n);
+        for (int j = 0; j < kcur; ++j) apply_A<double>(P, cd.Z64 + (size_t)j * P.n, cd.AZ64 + (size_t)j * P.n, nullptr);
+        // E = Z^T A Z, symmetrised, Cholesky in FP64 (App. C)
+        std::vector<double> E = gram_host(P, cd.Z64, kcur, cd.AZ64, kcur);
+        for (int i = 0; i < kcur; ++i)
+            for (int j = 0; j < i; ++j) {
+                const double v = 0.5 * (E[(size_t)i * kcur + j] + E[(size_t)j * kcur + i]);
+                E[(size_t)i * kcur + j] = E[(size_t)j * kcur + i] = v;
+            }
+        std::vector<double> Lf;
+        if (!cholesky_lower(E, kcur, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
+        cd.L = dalloc<double>(Lf.size());
+        h2d(cd.L, Lf.data(), Lf.size() * 8, s);
+        cd.Z32 = dalloc<float>((size_t)kcur * P.n);
+        cd.AZ32 = dalloc<float>((size_t)kcur * P.n);
+        launch_convert_f64_to_f32(cd.Z64, cd.Z32, (int64_t)kcur * P.n, s);
+        launch_convert_f64_to_f32(cd.AZ64, cd.AZ32, (int64_t)kcur * P.n, s);
+        sync(s);
+    } catch (...) {
+        dfree(zstore);
+        dfree(Y);
+        dfree(Y2);
+        dfree(C);
+        throw;
+    }
+}
+
+// -------------------------------------------------------------------------- solve
+static void solve(PlanHolder& P, const double* d, double tol, int maxit, int kind, int solver, double* m,
+                  mm_stats* st) {
+    cudaStream_t s = P.stream;
+    if (!(tol >= 0.0) || maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
+    if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
+    if (solver != MM_SOLVE_FP64 && solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
+    const bool two = kind == MM_PREC_TWOLEVEL;
+    if (two && P.coarse.k == 0) throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
+    mm_stats stats{};
+    check_cuda(cudaEventRecord(P.ev0, s), "event");
+    const double* dd = d;
+    if (!is_device_ptr(d)) {
+        h2d(P.dbuf, d, (size_t)P.nt * 8, s);
+        dd = P.dbuf;
+    }
+    // b = P^T N^-1 d (Eq. 7)
+    launch_toeplitz<double>(P, P.tz64, dd, nullptr, P.tod64, nullptr, s);
+    launch_scatter<double>(P, P.tod64, P.b64, nullptr, s);
+    P.have_b = true;
+    check_cuda(cudaEventRecord(P.ev1, s), "event");
+    const bool m_dev = is_device_ptr(m);
+    double* xout = m_dev ? m : P.x64;
+    int status = MM_OK;
+    const double bb = dot64(P, P.b64, P.b64);
+    const double bn = std::sqrt(bb);
+    if (solver == MM_SOLVE_FP64) {
+        check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+        const PcgOutcome o = run_pcg<double>(P, two, tol, maxit, nullptr, 0);
+        if (o.status != MM_OK) status = o.status;
+        check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
+        stats.iters = o.iters;
+        stats.outer = 1;
+        stats.rel_resid_rec = bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
+        // true residual of the returned map
+        apply_A<double>(P, xout, P.ax64, nullptr);
+        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+        const double rr = dot64(P, P.r64, P.r64);
+        stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        stats.fp64_products = 1;
+        stats.converged = status == MM_OK;
+    } else {
+        // iterative refinement: FP64 residual, FP32 inner PCG on the scaled residual
+        check_cuda(cudaMemsetAsync(xout, 0, (size_t)P.n * 8, s), "memset x");
+        check_cuda(cudaMemcpyAsync(P.r64, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+        double rr = bb;
+        int total = 0;
+        int outer = 0;
+        int fp64 = 0;
+        double last_rec = 1.0;
+        status = MM_ERR_NOT_CONVERGED;
+        while (true) {
+            if (std::sqrt(rr) <= tol * bn || bb == 0.0) {
+                status = MM_OK;
+                break;
+            }
+            if (total >= maxit || outer >= 20) break;
+            // r32 = r / ||r||  (the norm^2 stays in device memory for the update)
+            launch_dot64(P.r64, P.r64, P.n, P.d_dot, P.d_dot + DOT_BLOCKS, s);
+            launch_scale_to_f32(P.r64, P.d_dot + DOT_BLOCKS, static_cast<float*>(P.pcg.r), P.n, s);
+            double tol_in = 0.5 * tol * bn / std::sqrt(rr);
+            tol_in = std::min(0.5, std::max(tol_in, 1e-5));
+            const PcgOutcome o = run_pcg<float>(P, two, tol_in, maxit - total, nullptr, 0);
+            if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
+                status = o.status;
+                break;
+            }
+            total += o.iters;
+            last_rec = o.bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
+            launch_axpy_f32(xout, static_cast<const float*>(P.pcg.x), P.d_dot + DOT_BLOCKS, P.n, s);
+            apply_A<double>(P, xout, P.ax64, nullptr);
+            launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+            ++fp64;
+            rr = dot64(P, P.r64, P.r64);
+            ++outer;
+            if (!std::isfinite(rr)) {
+                status = MM_ERR_NUMERIC;
+                break;
+            }
+        }
+        stats.iters = total;
+        stats.outer = outer;
+        stats.fp64_products = fp64;
+        stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        stats.rel_resid_rec = last_rec;
+        stats.converged = status == MM_OK;
+    }
+    if (!m_dev) d2h(m, xout, (size_t)P.n * 8, s);
+    check_cuda(cudaEventRecord(P.ev2, s), "event");
+    sync(s);
+    float ms = 0.f, ms_rhs = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, P.ev0, P.ev2), "event time");
+    check_cuda(cudaEventElapsedTime(&ms_rhs, P.ev0, P.ev1), "event time");
+    stats.ms_total = ms;
+    stats.ms_rhs = ms_rhs;
+    if (st != nullptr) *st = stats;
+    if (status != MM_OK) throw Error{(mm_status)status, status == MM_ERR_NOT_CONVERGED ? "maxit reached before tol" : "solve failed"};
+}
+
+}  // namespace mm
+
+// ================================================================== C entry points
+using namespace mm;
+
+namespace {
+template <typename F>
+mm_status guarded(mm_plan_t plan, F&& f) {
+    PlanHolder* P = reinterpret_cast<PlanHolder*>(plan);
+    try {
+        f();
+        return MM_OK;
+    } catch (const Error& e) {
+        if (P) P->err = e.msg;
+        g_last_error = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        if (P) P->err = "host allocation failed";
+        g_last_error = "host allocation failed";
+        return MM_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (P) P->err = e.what();
+        g_last_error = e.what();
+        return MM_ERR_ARG;
+    }
+}
+
+PlanHolder* get(mm_plan_t p) {
+    if (p == nullptr) throw Error{MM_ERR_ARG, "null plan"};
+    return reinterpret_cast<PlanHolder*>(p);
+}
+
+int prec_ok(int precision) {
+    if (precision != MM_FP64 && precision != MM_FP32) throw Error{MM_ERR_ARG, "precision must be MM_FP64 or MM_FP32"};
+    return precision;
+}
+}  // namespace
+
+extern "C" {
+
+mm_status mm_plan(mm_plan_t* out, const int32_t* pix, int64_t nt, int32_t npix_sky, const double* weights,
+                  const int64_t* interval_off, int32_t K, const int32_t* interval_psd, const mm_psd* psd,
+                  int32_t npsd, const mm_opts* opts) {
+    if (out == nullptr) return MM_ERR_ARG;
+    *out = nullptr;
+    PlanHolder* P = nullptr;
+    try {
+        P = new PlanHolder();
+        build_plan(*P, pix, nt, npix_sky, weights, interval_off, K, interval_psd, psd, npsd, opts);
+        *out = reinterpret_cast<mm_plan_t>(P);
+        return MM_OK;
+    } catch (const Error& e) {
+        g_last_error = e.msg;
+        destroy_plan(P);
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        destroy_plan(P);
+        return MM_ERR_OOM;
+    }
+}
+
+mm_status mm_plan_info(mm_plan_t plan, int32_t* npix_obs, int64_t* n, int64_t* nkept, int32_t* fft_block_f64,
+                       int32_t* fft_block_f32) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (npix_obs) *npix_obs = P->npix_obs;
+        if (n) *n = P->n;
+        if (nkept) *nkept = P->nkept;
+        if (fft_block_f64) *fft_block_f64 = 2 << P->tz64.logn;
+        if (fft_block_f32) *fft_block_f32 = 2 << P->tz32.logn;
+    });
+}
+
+mm_status mm_plan_pixels(mm_plan_t plan, int32_t* obs2sky, int32_t* hits) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        const size_t bytes = (size_t)P->npix_obs * 4;
+        for (auto pr : {std::make_pair(obs2sky, &P->h_obs2sky), std::make_pair(hits, &P->h_hits)}) {
+            if (pr.first == nullptr) continue;
+            if (is_device_ptr(pr.first))
+                check_cuda(cudaMemcpy(pr.first, pr.second->data(), bytes, cudaMemcpyHostToDevice), "copy");
+            else
+                std::memcpy(pr.first, pr.second->data(), bytes);
+        }
+    });
+}
+
+mm_status mm_plan_row(mm_plan_t plan, int32_t psd_id, double* row) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (row == nullptr || psd_id < 0 || psd_id >= P->npsd) throw Error{MM_ERR_ARG, "bad psd id or null row"};
+        std::memcpy(row, P->rows[(size_t)psd_id].data(), ((size_t)P->lambda + 1) * 8);
+    });
+}
+
+mm_status mm_gather(mm_plan_t plan, int precision, const void* x, void* y) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!x || !y) throw Error{MM_ERR_ARG, "null vector"};
+        if (prec_ok(precision) == MM_FP64)
+            launch_gather<double>(*P, static_cast<const double*>(x), static_cast<double*>(y), P->stream);
+        else
+            launch_gather<float>(*P, static_cast<const float*>(x), static_cast<float*>(y), P->stream);
+        sync(P->stream);
+    });
+}
+
+mm_status mm_apply_ninv(mm_plan_t plan, int precision, const void* y, void* z) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!y || !z) throw Error{MM_ERR_ARG, "null vector"};
+        if (prec_ok(precision) == MM_FP64)
+            launch_toeplitz<double>(*P, P->tz64, static_cast<const double*>(y), nullptr, static_cast<double*>(z), nullptr,
+                                    P->stream);
+        else
+            launch_toeplitz<float>(*P, P->tz32, static_cast<const float*>(y), nullptr, static_cast<float*>(z), nullptr,
+                                   P->stream);
+        sync(P->stream);
+    });
+}
+
+mm_status mm_scatter(mm_plan_t plan, int precision, const void* z, void* w) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!z || !w) throw Error{MM_ERR_ARG, "null vector"};
+        if (prec_ok(precision) == MM_FP64)
+            launch_scatter<double>(*P, static_cast<const double*>(z), static_cast<double*>(w), nullptr, P->stream);
+        else
+            launch_scatter<float>(*P, static_cast<const float*>(z), static_cast<float*>(w), nullptr, P->stream);
+        sync(P->stream);
+    });
+}
+
+mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!x || !y) throw Error{MM_ERR_ARG, "null vector"};
+        if (prec_ok(precision) == MM_FP64)
+            apply_A<double>(*P, static_cast<const double*>(x), static_cast<double*>(y), nullptr);
+        else
+            apply_A<float>(*P, static_cast<const float*>(x), static_cast<float*>(y), nullptr);
+        sync(P->stream);
+    });
+}
+
+mm_status mm_rhs(mm_plan_t plan, const double* d, double* b) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!d || !b) throw Error{MM_ERR_ARG, "null vector"};
+        launch_toeplitz<double>(*P, P->tz64, d, nullptr, P->tod64, nullptr, P->stream);
+        launch_scatter<double>(*P, P->tod64, b, nullptr, P->stream);
+        sync(P->stream);
+    });
+}
+
+mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, void* z) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!r || !z) throw Error{MM_ERR_ARG, "null vector"};
+        if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
+        const bool two = kind == MM_PREC_TWOLEVEL;
+        if (two && P->coarse.k == 0) throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
+        if (prec_ok(precision) == MM_FP64) {
+            PcgArgs<double> a = pcg_args<double>(*P, two, 0);
+            a.r = const_cast<double*>(static_cast<const double*>(r));
+            a.z = static_cast<double*>(z);
+            launch_pcg<double>(2, P->ncomp, two, a, P->pcg.nblocks, P->stream);
+        } else {
+            PcgArgs<float> a = pcg_args<float>(*P, two, 0);
+            a.r = const_cast<float*>(static_cast<const float*>(r));
+            a.z = static_cast<float*>(z);
+            launch_pcg<float>(2, P->ncomp, two, a, P->pcg.nblocks, P->stream);
+        }
+        sync(P->stream);
+    });
+}
+
+mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bprime, double tol, int maxit) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (prec_ok(precision) == MM_FP64)
+            build_coarse<double>(*P, k, bprime, tol, maxit);
+        else
+            build_coarse<float>(*P, k, bprime, tol, maxit);
+    });
+}
+
+mm_status mm_coarse_info(mm_plan_t plan, int32_t* k_kept, double* ritz_values) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (k_kept) *k_kept = P->coarse.k;
+        if (ritz_values) std::copy(P->coarse.ritz.begin(), P->coarse.ritz.end(), ritz_values);
+    });
+}
+
+mm_status mm_coarse_vectors(mm_plan_t plan, double* Z) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (P->coarse.k == 0) throw Error{MM_ERR_STATE, "no coarse space"};
+        if (Z == nullptr) throw Error{MM_ERR_ARG, "null output"};
+        check_cuda(cudaMemcpy(Z, P->coarse.Z64, (size_t)P->coarse.k * P->n * 8, cudaMemcpyDefault), "copy Z");
+    });
+}
+
+mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int kind, int solver, double* m,
+                   mm_stats* st) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!d || !m) throw Error{MM_ERR_ARG, "null vector"};
+        solve(*P, d, tol, maxit, kind, solver, m, st);
+    });
+}
+
+const char* mm_last_error(mm_plan_t plan) {
+    if (plan != nullptr) {
+        const PlanHolder* P = reinterpret_cast<const PlanHolder*>(plan);
+        if (!P->err.empty()) return P->err.c_str();
+    }
+    return g_last_error.c_str();
+}
+
+void mm_destroy(mm_plan_t plan) { destroy_plan(reinterpret_cast<PlanHolder*>(plan)); }
+
+const char* mm_version(void) { return "libmm 0.1 (sm_103a)"; }
+
+}  // extern "C"

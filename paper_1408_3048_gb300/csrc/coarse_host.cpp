@@ -1,0 +1,190 @@
+// Host FP64 dense helpers for the a posteriori coarse space (Sec. 3.3.2, App. A):
+//   * the k smallest eigenpairs of the symmetric tridiagonal Lanczos matrix T_m, by
+//     Sturm-sequence bisection (eigenvalues) and inverse iteration with
+//     re-orthogonalisation inside clusters (eigenvectors);
+//   * Cholesky factorisation with column dropping (orthonormalisation of the Ritz
+//     vectors and the factor of the coarse operator E = Z^T A Z, App. C).
+#include <algorithm>
+#include <cmath>
+
+#include "coarse_host.h"
+
+namespace mm {
+
+// number of eigenvalues of T (diag d, off-diag e) strictly smaller than x
+static int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    const int m = (int)d.size();
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < m; ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e, int k,
+                      std::vector<double>& theta, std::vector<double>& S) {
+    const int m = (int)d.size();
+    k = std::min(k, m);
+    // Gershgorin bounds
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+    }
+    const double scale = std::max(std::fabs(lo), std::fabs(hi));
+    theta.assign(k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        double a = lo, b = hi;   // count(a) <= j < count(b)
+        for (int it = 0; it < 200; ++it) {
+            const double c = 0.5 * (a + b);
+            if (c <= a || c >= b) break;
+            if (sturm_count(d, e, c) > j) b = c; else a = c;
+            if (b - a <= 4e-16 * scale) break;
+        }
+        theta[j] = 0.5 * (a + b);
+    }
+    // inverse iteration: (T - mu I) x = y by Gaussian elimination with partial pivoting
+    S.assign((size_t)m * k, 0.0);
+    const double eps = 2.2e-16 * scale;
+    for (int j = 0; j < k; ++j) {
+        const double mu = theta[j] + eps * 0.5;
+        std::vector<double> x(m);
+        uint64_t st = 0x9E3779B97F4A7C15ull ^ (uint64_t)(j + 1) * 0xBF58476D1CE4E5B9ull;
+        for (int i = 0; i < m; ++i) {
+            st ^= st >> 31; st *= 0x94D049BB133111EBull; st ^= st >> 29;
+            x[i] = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+        }
+        for (int iter = 0; iter < 4; ++iter) {
+            // tridiagonal LU with pivoting: rows carry (a, b, c) band + fill
+            std::vector<double> dd(m), du(m, 0.0), du2(m, 0.0), dl(m, 0.0), rhs = x;
+            std::vector<int> piv(m, 0);
+            for (int i = 0; i < m; ++i) dd[i] = d[i] - mu;
+            for (int i = 0; i + 1 < m; ++i) {
+                du[i] = e[i];
+                dl[i] = e[i];
+            }
+            for (int i = 0; i + 1 < m; ++i) {
+                if (std::fabs(dd[i]) >= std::fabs(dl[i])) {
+                    if (dd[i] == 0.0) dd[i] = eps;
+                    const double f = dl[i] / dd[i];
+                    dl[i] = f;
+                    dd[i + 1] -= f * du[i];
+                    piv[i] = 0;
+                } else {
+                    const double f = dd[i] / dl[i];
+                    dd[i] = dl[i];
+                    dl[i] = f;
+                    const double t = du[i];
+                    du[i] = dd[i + 1];
+                    dd[i + 1] = t - f * dd[i + 1];
+                    if (i + 2 < m) {
+                        du2[i] = du[i + 1];
+                        du[i + 1] = -f * du[i + 1];
+                    }
+                    piv[i] = 1;
+                }
+            }
+            if (dd[m - 1] == 0.0) dd[m - 1] = eps;
+            // forward: apply L^-1
+            for (int i = 0; i + 1 < m; ++i) {
+                if (piv[i] == 0) {
+                    rhs[i + 1] -= dl[i] * rhs[i];
+                } else {
+                    const double t = rhs[i];
+                    rhs[i] = rhs[i + 1];
+                    rhs[i + 1] = t - dl[i] * rhs[i + 1];
+                }
+            }
+            // backward: U x = rhs
+            for (int i = m - 1; i >= 0; --i) {
+                double v = rhs[i];
+                if (i + 1 < m) v -= du[i] * rhs[i + 1];
+                if (i + 2 < m) v -= du2[i] * rhs[i + 2];
+                rhs[i] = v / dd[i];
+            }
+            // re-orthogonalise against earlier vectors of the same cluster
+            for (int jj = 0; jj < j; ++jj) {
+                if (std::fabs(theta[jj] - theta[j]) > 1e-3 * scale) continue;
+                double dot = 0.0;
+                for (int i = 0; i < m; ++i) dot += rhs[i] * S[(size_t)i * k + jj];
+                for (int i = 0; i < m; ++i) rhs[i] -= dot * S[(size_t)i * k + jj];
+            }
+            double nrm = 0.0;
+            for (int i = 0; i < m; ++i) nrm += rhs[i] * rhs[i];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) break;
+            for (int i = 0; i < m; ++i) x[i] = rhs[i] / nrm;
+        }
+        for (int i = 0; i < m; ++i) S[(size_t)i * k + j] = x[i];
+    }
+}
+
+// Cholesky G = R^T R (G k x k row-major, symmetric).  Column j is dropped (keep[j] =
+// false) when its pivot sqrt(g_jj - ...) is < drop_rtol * max kept pivot so far
+// (drop_rtol = 0: never drop; a non-positive pivot then fails).  Returns the inverse
+// factor Rinv restricted to kept columns as a k x kk matrix W with Y_kept = Y W.
+bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
+                   std::vector<int>& kept) {
+    std::vector<double> R((size_t)k * k, 0.0);   // upper, only kept rows/cols filled
+    kept.clear();
+    double maxpiv = 0.0;
+    for (int j = 0; j < k; ++j) {
+        // r_ij for kept i
+        std::vector<double> col(kept.size());
+        double s = G[(size_t)j * k + j];
+        for (size_t a = 0; a < kept.size(); ++a) {
+            const int i = kept[a];
+            double v = G[(size_t)i * k + j];
+            for (size_t b = 0; b < a; ++b) v -= R[(size_t)kept[b] * k + i] * col[b];
+            v /= R[(size_t)i * k + i];
+            col[a] = v;
+            s -= v * v;
+        }
+        const double piv = s > 0.0 ? std::sqrt(s) : 0.0;
+        if (drop_rtol > 0.0 && (piv < drop_rtol * maxpiv || piv == 0.0)) continue;
+        if (!(piv > 0.0)) return false;
+        for (size_t a = 0; a < kept.size(); ++a) R[(size_t)kept[a] * k + j] = col[a];
+        R[(size_t)j * k + j] = piv;
+        kept.push_back(j);
+        maxpiv = std::max(maxpiv, piv);
+    }
+    // W = R_kept^-1 (upper triangular inverse), as k x kk: W[i][c] for kept col c
+    const int kk = (int)kept.size();
+    W.assign((size_t)k * kk, 0.0);
+    for (int c = 0; c < kk; ++c) {
+        // solve R_kept w = e_c (upper triangular in kept indices)
+        std::vector<double> w(kk, 0.0);
+        for (int a = kk - 1; a >= 0; --a) {
+            double v = (a == c) ? 1.0 : 0.0;
+            for (int b = a + 1; b < kk; ++b) v -= R[(size_t)kept[a] * k + kept[b]] * w[b];
+            w[a] = v / R[(size_t)kept[a] * k + kept[a]];
+        }
+        for (int a = 0; a < kk; ++a) W[(size_t)kept[a] * kk + c] = w[a];
+    }
+    return true;
+}
+
+// Plain Cholesky E = L L^T (row-major lower); false when E is not positive definite.
+bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L) {
+    L.assign((size_t)k * k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        double s = E[(size_t)j * k + j];
+        for (int p = 0; p < j; ++p) s -= L[(size_t)j * k + p] * L[(size_t)j * k + p];
+        if (!(s > 0.0)) return false;
+        const double ljj = std::sqrt(s);
+        L[(size_t)j * k + j] = ljj;
+        for (int i = j + 1; i < k; ++i) {
+            double v = E[(size_t)i * k + j];
+            for (int p = 0; p < j; ++p) v -= L[(size_t)i * k + p] * L[(size_t)j * k + p];
+            L[(size_t)i * k + j] = v / ljj;
+        }
+    }
+    return true;
+}
+
+}  // namespace mm

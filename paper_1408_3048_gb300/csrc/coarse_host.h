@@ -1,0 +1,22 @@
+// Host FP64 dense helpers of the coarse-space construction (see coarse_host.cpp).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+namespace mm {
+
+// k smallest eigenpairs of the symmetric tridiagonal matrix (diag d[m], off-diag e[m-1]):
+// theta[k] ascending, S row-major m x k (unit eigenvectors).
+void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e, int k,
+                      std::vector<double>& theta, std::vector<double>& S);
+
+// Cholesky of a Gram matrix with column dropping; W (k x kept) maps Y to orthonormal Y W.
+bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
+                   std::vector<int>& kept);
+
+// E = L L^T, row-major lower L; false if E is not positive definite.
+bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L);
+
+}  // namespace mm

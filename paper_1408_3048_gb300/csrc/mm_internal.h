@@ -1,0 +1,157 @@
+// Internal declarations shared by the translation units of libmm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+
+namespace mm {
+
+// ---------------------------------------------------------------------------------
+// Overlap-save tile: block of B real samples [in0, in0 + B) producing the valid outputs
+// [out0, out0 + nout) (out0 = in0 + lambda); samples outside [ibeg, iend) read as 0.
+struct Tile {
+    int64_t out0;
+    int64_t ibeg;
+    int64_t iend;
+    int32_t nout;
+    int32_t psd;
+};
+
+// Device tables of one arithmetic precision (T = double or float).
+struct ToeplitzDev {
+    int logn = 0;            // complex FFT length N = 2^logn, real block B = 2N
+    int ntiles = 0;
+    Tile* tiles = nullptr;   // [ntiles]
+    void* twiddle = nullptr; // T[B/4 + 1]: cos(2 pi k / B)
+    void* H = nullptr;       // T[npsd][N + 1]: kernel spectrum / N (real, even kernel)
+};
+
+struct CoarseDev {
+    int k = 0;                   // kept dimension
+    double* Z64 = nullptr;       // [k][n]
+    double* AZ64 = nullptr;      // [k][n]
+    float* Z32 = nullptr;        // [k][n]
+    float* AZ32 = nullptr;       // [k][n]
+    double* L = nullptr;         // [k][k] lower Cholesky factor of E (row-major)
+    std::vector<double> ritz;    // k smallest Ritz values
+};
+
+// Scratch and state of the PCG driver.
+struct PcgDev {
+    int64_t n = 0;
+    int nblocks = 0;             // cooperative grid size
+    double* partial = nullptr;   // [nblocks][2 + KMAX] block partial sums
+    double* scal = nullptr;      // [16] device scalars (see pcg.cu)
+    int* flags = nullptr;        // [8] done / status / iteration / barrier words
+    unsigned* barrier = nullptr; // grid barrier word
+    void* x = nullptr;           // vectors, sized for double
+    void* r = nullptr;
+    void* p = nullptr;
+    void* q = nullptr;
+    void* z = nullptr;
+    double* hist_alpha = nullptr;  // [maxhist]
+    double* hist_beta = nullptr;   // [maxhist]
+    double* hist_rz = nullptr;     // [maxhist]
+    double* hist_rr = nullptr;     // [maxhist]
+    int maxhist = 0;
+};
+
+struct Plan {
+    // problem
+    int64_t nt = 0;
+    int32_t npix_sky = 0;
+    int32_t ncomp = 1;
+    int32_t K = 0;
+    int32_t npsd = 0;
+    int32_t lambda = 0;
+    int32_t window = MM_WINDOW_GAUSS;
+    double fsamp = 100.0;
+    double rcond_min = 1e-6;
+    cudaStream_t stream = 0;
+    int num_sms = 0;
+    int64_t L_grid = 0;
+
+    // observed pixels
+    int32_t npix_obs = 0;
+    int64_t n = 0;
+    int64_t nkept = 0;
+    std::vector<int32_t> h_obs2sky, h_hits;
+    std::vector<std::vector<double>> rows;   // [npsd][lambda+1]
+    std::vector<int64_t> h_ioff;
+    std::vector<int32_t> h_ipsd;
+
+    // device pointing (time order) and pixel-sorted CSR
+    int32_t* pixc = nullptr;       // [nt] observed index or -1
+    double2* w64 = nullptr;        // [nt] (cos, sin), pol only
+    float2* w32 = nullptr;         // [nt]
+    int32_t* csr_off = nullptr;    // [npix_obs + 1]
+    int32_t* tsort = nullptr;      // [nkept] sample index, pixel-major, ascending t
+    double2* wsort64 = nullptr;    // [nkept] weights in sorted order (pol)
+    float2* wsort32 = nullptr;     // [nkept]
+    int64_t* ioff = nullptr;       // [K+1]
+    int32_t* ipsd = nullptr;       // [K]
+    double* t0 = nullptr;          // [npsd] diagonal of each row
+
+    ToeplitzDev tz64, tz32;
+
+    // block-Jacobi: inverse blocks, symmetric packed (a00 a01 a02 a11 a12 a22) or 1
+    double* bd64 = nullptr;        // [npix_obs][ncomp == 3 ? 6 : 1]
+    float* bd32 = nullptr;
+
+    // time-domain scratch
+    double* tod64 = nullptr;       // [nt]
+    float* tod32 = nullptr;        // [nt]
+    double* dbuf = nullptr;        // [nt] staging for host data
+    double* b64 = nullptr;         // [n] last right-hand side
+    bool have_b = false;
+
+    CoarseDev coarse;
+    PcgDev pcg;
+
+    std::string err;
+};
+
+// error helpers ----------------------------------------------------------------------
+struct Error {
+    mm_status st;
+    std::string msg;
+};
+
+void check_cuda(cudaError_t e, const char* what);   // throws Error{MM_ERR_CUDA}
+void* dmalloc(size_t bytes);                         // throws Error{MM_ERR_OOM}
+void dfree(void* p);
+
+// host numerics (plan.cpp) -------------------------------------------------------------
+void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);
+std::vector<double> toeplitz_row(double sigma, double fknee, double alpha, int64_t L,
+                                 double fsamp, int lam, int window);
+bool symbol_positive(const std::vector<double>& t);
+std::vector<double> overlap_save_spectrum(const std::vector<double>& t, int64_t N);
+double rcond_sym3(const double B[6]);
+
+// kernels (launchers) --------------------------------------------------------------------
+// Toeplitz overlap-save (toeplitz_f64.cu / toeplitz_f32.cu)
+template <typename T>
+void launch_toeplitz(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const T* x_map,
+                     T* z, const int* done, cudaStream_t s);
+template <typename T>
+size_t toeplitz_smem_bytes(int logn);
+template <typename T>
+int toeplitz_max_logn();
+
+// pointing (pointing.cu)
+template <typename T>
+void launch_gather(const Plan& P, const T* x, T* y, cudaStream_t s);
+template <typename T>
+void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream_t s);
+void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
+template <typename T>
+void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);
+void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+
+}  // namespace mm

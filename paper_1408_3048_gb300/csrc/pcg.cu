@@ -1,0 +1,439 @@
+// Preconditioned CG (Sec. 3.1) -- everything except the product q = A p runs in one
+// persistent cooperative kernel per iteration:
+//
+//   alpha = rho / p^T q;  x += alpha p;  r -= alpha q;  stop if ||r|| <= tol ||b||
+//   z = M r  (M_BD of Eq. 10, or M_2lvl of Eq. 12 applied as in App. C:
+//             v = E^-1 Z^T r by the FP64 Cholesky factor of E, z = M_BD (r - AZ v) + Z v)
+//   rho' = r^T z;  beta = rho' / rho;  p = z + beta p
+//
+// Dot products are accumulated in FP64 per block (fixed thread order), written as block
+// partials and summed by every block in block order after a grid barrier, so every block
+// sees the same scalars and the result is bit-reproducible.  The grid barrier is a
+// counter whose top bit flips once all blocks arrived; each wait is bounded in time
+// (2 s on the global timer), after which the kernel records MM_ERR_TIMEOUT and returns.
+// The iteration count, stopping decision and scalar history live in device memory; the
+// host only polls a done flag every few iterations.
+#include "pcg.cuh"
+
+namespace mm {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false when this block gave up waiting (timeout recorded in flags).
+__device__ bool grid_sync(unsigned* bar, int* flags) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned nb = gridDim.x;
+        const unsigned inc = blockIdx.x == 0 ? (0x80000000u - (nb - 1u)) : 1u;
+        __threadfence();
+        const unsigned old = atomicAdd(bar, inc);
+        const unsigned long long t0 = global_ns();
+        while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0u) {
+            if (global_ns() - t0 > 2000000000ull) {
+                atomicExch(&flags[F_STATUS], (int)MM_ERR_TIMEOUT);
+                atomicExch(&flags[F_DONE], 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Block-wide FP64 sum (fixed order); result valid in every thread.
+__device__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sh[i];
+    return s;
+}
+
+// Sum of slot `slot` over all block partials, in block order.
+__device__ __forceinline__ double sum_partials(const double* part, int slot) {
+    double s = 0.0;
+    const volatile double* p = part;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)b * PSTRIDE + slot];
+    return s;
+}
+
+// Pixel range of this block.
+__device__ __forceinline__ void block_pixels(int npix, int& lo, int& hi) {
+    const int chunk = (npix + gridDim.x - 1) / gridDim.x;
+    lo = blockIdx.x * chunk;
+    hi = min(npix, lo + chunk);
+    if (lo > hi) lo = hi;
+}
+
+// Z^T r over this block's elements -> part[blk][S_COARSE + j]
+template <typename T>
+__device__ void coarse_partials(const PcgArgs<T>& a, const T* r, int64_t e0, int64_t e1) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = w; j < a.k; j += nw) {
+        const T* zj = a.Z + (size_t)j * a.n;
+        double s = 0.0;
+        for (int64_t i = e0 + l; i < e1; i += 32) s += (double)zj[i] * (double)r[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (l == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_COARSE + j] = s;
+    }
+}
+
+// v = E^-1 u with E = L L^T (L row-major k x k), by warp 0; u from the partials.
+template <typename T>
+__device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        double u0 = 0.0, u1 = 0.0;   // rows l and l + 32
+        if (l < a.k) u0 = sum_partials(a.partial, S_COARSE + l);
+        if (l + 32 < a.k) u1 = sum_partials(a.partial, S_COARSE + l + 32);
+        // forward: L y = u
+        for (int j = 0; j < a.k; ++j) {
+            const double uj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
+            const double yj = uj / a.L[(size_t)j * a.k + j];
+            if (l == (j & 31)) {
+                if (j < 32) u0 = yj; else u1 = yj;
+            }
+            if (l > j && l < a.k) u0 -= a.L[(size_t)l * a.k + j] * yj;
+            if (l + 32 > j && l + 32 < a.k) u1 -= a.L[(size_t)(l + 32) * a.k + j] * yj;
+        }
+        // backward: L^T v = y
+        for (int j = a.k - 1; j >= 0; --j) {
+            const double yj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
+            const double vj = yj / a.L[(size_t)j * a.k + j];
+            if (l == (j & 31)) {
+                if (j < 32) u0 = vj; else u1 = vj;
+            }
+            if (l < j && l < a.k) u0 -= a.L[(size_t)j * a.k + l] * vj;
+            if (l + 32 < j && l + 32 < a.k) u1 -= a.L[(size_t)j * a.k + l + 32] * vj;
+        }
+        if (l < a.k) v_sh[l] = u0;
+        if (l + 32 < a.k) v_sh[l + 32] = u1;
+    }
+    __syncthreads();
+}
+
+// z = M_BD (r - AZ v) + Z v (or M_BD r) on this block's pixels; returns partial r^T z.
+template <typename T, int NC, bool TWO>
+__device__ double apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0, int p1) {
+    double rz = 0.0;
+    for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+        const int64_t e = (int64_t)q * NC;
+        T t[NC], zc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            t[c] = a.r[e + c];
+            zc[c] = (T)0;
+        }
+        if constexpr (TWO) {
+            for (int j = 0; j < a.k; ++j) {
+                const T vj = (T)v_sh[j];
+                const T* az = a.AZ + (size_t)j * a.n + e;
+                const T* zz = a.Z + (size_t)j * a.n + e;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    t[c] -= az[c] * vj;
+                    zc[c] += zz[c] * vj;
+                }
+            }
+        }
+        T out[NC];
+        if constexpr (NC == 1) {
+            out[0] = a.bd[q] * t[0] + zc[0];
+        } else {
+            const T* m = a.bd + 6 * (int64_t)q;
+            out[0] = m[0] * t[0] + m[1] * t[1] + m[2] * t[2] + zc[0];
+            out[1] = m[1] * t[0] + m[3] * t[1] + m[4] * t[2] + zc[1];
+            out[2] = m[2] * t[0] + m[4] * t[1] + m[5] * t[2] + zc[2];
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            a.z[e + c] = out[c];
+            rz += (double)a.r[e + c] * (double)out[c];
+        }
+    }
+    return rz;
+}
+
+// ------------------------------------------------------------------------ init kernel
+// r = b is already in a.r.  x = 0, z = M r, p = z, rho = r^T z, bb = r^T r.
+template <typename T, int NC, bool TWO>
+__global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
+    __shared__ double sh[32];
+    __shared__ double v_sh[KMAX];
+    int p0, p1;
+    block_pixels(a.npix, p0, p1);
+    const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
+    double bb = 0.0;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+        a.x[i] = (T)0;
+        bb += (double)a.r[i] * (double)a.r[i];
+    }
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = bb;
+    if constexpr (TWO) coarse_partials(a, a.r, e0, e1);
+    if (!grid_sync(a.bar, a.flags)) return;
+    const double bbt = sum_partials(a.partial, S_RR);
+    if constexpr (TWO) coarse_solve(a, v_sh);
+    double rz = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    __syncthreads();
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+        a.p[i] = a.z[i];
+        if (a.zstore != nullptr) a.zstore[i] = a.z[i];
+    }
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
+    if (!grid_sync(a.bar, a.flags)) return;
+    const double rho = sum_partials(a.partial, S_RZ);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[SC_RHO] = rho;
+        a.scal[SC_BB] = bbt;
+        a.scal[SC_RR] = bbt;
+        a.flags[F_ITER] = 0;
+        if (a.hist_rz != nullptr) a.hist_rz[0] = rho;
+        if (a.hist_rr != nullptr) a.hist_rr[0] = bbt;
+        if (!(bbt > 0.0)) {
+            a.flags[F_DONE] = 1;
+            a.flags[F_STATUS] = isfinite(bbt) ? (int)MM_OK : (int)MM_ERR_NUMERIC;
+        } else if (!isfinite(rho) || !(rho > 0.0)) {
+            a.flags[F_DONE] = 1;
+            a.flags[F_STATUS] = isfinite(rho) ? (int)MM_ERR_NOT_SPD : (int)MM_ERR_NUMERIC;
+        } else {
+            a.flags[F_DONE] = 0;
+            a.flags[F_STATUS] = (int)MM_OK;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- iteration kernel
+template <typename T, int NC, bool TWO>
+__global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
+    __shared__ double sh[32];
+    __shared__ double v_sh[KMAX];
+    if (*(volatile int*)&a.flags[F_DONE]) return;
+    int p0, p1;
+    block_pixels(a.npix, p0, p1);
+    const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
+    // phase A: p^T q
+    double pq = 0.0;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) pq += (double)a.p[i] * (double)a.q[i];
+    pq = block_sum(pq, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_PQ] = pq;
+    if (!grid_sync(a.bar, a.flags)) return;
+    const double pqt = sum_partials(a.partial, S_PQ);
+    const double rho = a.scal[SC_RHO];
+    if (!(pqt > 0.0) || !isfinite(pqt)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.flags[F_STATUS] = isfinite(pqt) ? (int)MM_ERR_NOT_SPD : (int)MM_ERR_NUMERIC;
+            a.flags[F_DONE] = 1;
+        }
+        return;
+    }
+    const double alpha = rho / pqt;
+    // phase B: x += alpha p, r -= alpha q, r^T r, Z^T r
+    const T al = (T)alpha;
+    double rr = 0.0;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+        a.x[i] += al * a.p[i];
+        const T ri = a.r[i] - al * a.q[i];
+        a.r[i] = ri;
+        rr += (double)ri * (double)ri;
+    }
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = rr;
+    if constexpr (TWO) {
+        __syncthreads();
+        coarse_partials(a, a.r, e0, e1);
+    }
+    if (!grid_sync(a.bar, a.flags)) return;
+    const double rrt = sum_partials(a.partial, S_RR);
+    const int it = a.flags[F_ITER] + 1;     // every block reads the same value here
+    bool stop = false;
+    int status = MM_OK;
+    if (!isfinite(rrt)) {
+        stop = true;
+        status = MM_ERR_NUMERIC;
+    } else if (rrt <= a.scal[SC_TOL2] * a.scal[SC_BB]) {
+        stop = true;
+    } else if (it >= a.maxit) {
+        stop = true;
+        status = MM_ERR_NOT_CONVERGED;
+    }
+    if (stop) {
+        // every block has read F_ITER above; wait for all before block 0 updates it
+        if (!grid_sync(a.bar, a.flags)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.flags[F_ITER] = it;
+            a.scal[SC_RR] = rrt;
+            if (a.hist_alpha != nullptr && it - 1 < a.maxhist) a.hist_alpha[it - 1] = alpha;
+            if (a.hist_rr != nullptr && it < a.maxhist) a.hist_rr[it] = rrt;
+            a.flags[F_STATUS] = status;
+            a.flags[F_DONE] = 1;
+        }
+        return;
+    }
+    // phase C: z = M r, r^T z
+    if constexpr (TWO) coarse_solve(a, v_sh);
+    double rz = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
+    if (!grid_sync(a.bar, a.flags)) return;
+    const double rzt = sum_partials(a.partial, S_RZ);
+    const double beta = rzt / rho;
+    const T be = (T)beta;
+    T* zs = (a.zstore != nullptr && it < a.maxstore) ? a.zstore + (size_t)it * a.n : nullptr;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+        const T zi = a.z[i];
+        a.p[i] = zi + be * a.p[i];
+        if (zs != nullptr) zs[i] = zi;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.flags[F_ITER] = it;
+        a.scal[SC_RHO] = rzt;
+        a.scal[SC_RR] = rrt;
+        if (a.hist_alpha != nullptr && it - 1 < a.maxhist) a.hist_alpha[it - 1] = alpha;
+        if (a.hist_beta != nullptr && it - 1 < a.maxhist) a.hist_beta[it - 1] = beta;
+        if (a.hist_rz != nullptr && it < a.maxhist) a.hist_rz[it] = rzt;
+        if (a.hist_rr != nullptr && it < a.maxhist) a.hist_rr[it] = rrt;
+        if (!isfinite(rzt) || !(rzt > 0.0)) {
+            a.flags[F_STATUS] = isfinite(rzt) ? (int)MM_ERR_NOT_SPD : (int)MM_ERR_NUMERIC;
+            a.flags[F_DONE] = 1;
+        }
+    }
+}
+
+// --------------------------------------------------------------- stand-alone M_2lvl
+// Used by mm_precond: the same device functions as in PCG, launched cooperatively.
+template <typename T, int NC, bool TWO>
+__global__ void __launch_bounds__(PCG_THREADS) precond_kernel(PcgArgs<T> a) {
+    __shared__ double v_sh[KMAX];
+    int p0, p1;
+    block_pixels(a.npix, p0, p1);
+    const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
+    if constexpr (TWO) {
+        coarse_partials(a, a.r, e0, e1);
+        if (!grid_sync(a.bar, a.flags)) return;
+        coarse_solve(a, v_sh);
+    }
+    (void)apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+}
+
+// ----------------------------------------------------------------------- launchers
+template <typename T, int NC, bool TWO>
+static void coop(void (*kern)(PcgArgs<T>), const PcgArgs<T>& a, int nblocks, cudaStream_t s) {
+    void* args[] = {(void*)&a};
+    check_cuda(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblocks), dim3(PCG_THREADS), args,
+                                           0, s),
+               "cooperative PCG launch");
+}
+
+template <typename T>
+void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks, cudaStream_t s) {
+#define MM_PCG_CASE(NC, TWO)                                                       \
+    if (ncomp == NC && two == TWO) {                                               \
+        if (which == 0) coop<T, NC, TWO>(pcg_init_kernel<T, NC, TWO>, a, nblocks, s); \
+        else if (which == 1) coop<T, NC, TWO>(pcg_iter_kernel<T, NC, TWO>, a, nblocks, s); \
+        else coop<T, NC, TWO>(precond_kernel<T, NC, TWO>, a, nblocks, s);          \
+        return;                                                                    \
+    }
+    MM_PCG_CASE(1, false)
+    MM_PCG_CASE(1, true)
+    MM_PCG_CASE(3, false)
+    MM_PCG_CASE(3, true)
+#undef MM_PCG_CASE
+    throw Error{MM_ERR_ARG, "launch_pcg: bad ncomp"};
+}
+template void launch_pcg<double>(int, int, bool, const PcgArgs<double>&, int, cudaStream_t);
+template void launch_pcg<float>(int, int, bool, const PcgArgs<float>&, int, cudaStream_t);
+
+int pcg_max_blocks(int num_sms) {
+    int per_sm = 0;
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_iter_kernel<double, 3, true>,
+                                                             PCG_THREADS, 0),
+               "occupancy");
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    return per_sm * num_sms;
+}
+
+// ------------------------------------------------------------------ vector helpers
+// Deterministic FP64 dot: per-block partials then one block sums them in order.
+template <typename TA, typename TB>
+__global__ void dot_partial_kernel(const TA* a, const TB* b, int64_t n, double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_kernel(const double* part, int m, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+void launch_dot64(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t s) {
+    const int g = DOT_BLOCKS;
+    dot_partial_kernel<double, double><<<g, 256, 0, s>>>(a, b, n, part);
+    sum_kernel<<<1, 32, 0, s>>>(part, g, out);
+    check_cuda(cudaGetLastError(), "dot launch");
+}
+
+__global__ void scale_to_f32_kernel(const double* a, const double* scale, float* b, int64_t n) {
+    const double sc = 1.0 / sqrt(*scale);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)(a[i] * sc);
+}
+
+// b = (float)(a / sqrt(*sq))
+void launch_scale_to_f32(const double* a, const double* sq, float* b, int64_t n, cudaStream_t s) {
+    scale_to_f32_kernel<<<DOT_BLOCKS, 256, 0, s>>>(a, sq, b, n);
+    check_cuda(cudaGetLastError(), "scale launch");
+}
+
+__global__ void axpy_f32_kernel(double* x, const float* d, const double* sq, int64_t n) {
+    const double sc = sqrt(*sq);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += sc * (double)d[i];
+}
+
+// x += sqrt(*sq) * d
+void launch_axpy_f32(double* x, const float* d, const double* sq, int64_t n, cudaStream_t s) {
+    axpy_f32_kernel<<<DOT_BLOCKS, 256, 0, s>>>(x, d, sq, n);
+    check_cuda(cudaGetLastError(), "axpy launch");
+}
+
+__global__ void sub_kernel(const double* b, const double* ax, double* r, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = b[i] - ax[i];
+}
+
+void launch_sub(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s) {
+    sub_kernel<<<DOT_BLOCKS, 256, 0, s>>>(b, ax, r, n);
+    check_cuda(cudaGetLastError(), "sub launch");
+}
+
+}  // namespace mm

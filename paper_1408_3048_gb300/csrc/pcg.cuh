@@ -1,0 +1,58 @@
+// PCG kernel arguments and launchers (see pcg.cu).
+#pragma once
+
+#include "mm_internal.h"
+
+namespace mm {
+
+constexpr int PCG_THREADS = 256;
+constexpr int KMAX = 64;          // largest coarse dimension
+constexpr int DOT_BLOCKS = 304;   // blocks of the stand-alone dot / vector kernels
+
+// partial-sum slots per block
+constexpr int S_PQ = 0, S_RR = 1, S_RZ = 2, S_COARSE = 3;
+constexpr int PSTRIDE = S_COARSE + KMAX;
+
+// device scalars
+constexpr int SC_RHO = 0, SC_BB = 1, SC_RR = 2, SC_TOL2 = 3;
+// device flags
+constexpr int F_DONE = 0, F_STATUS = 1, F_ITER = 2;
+
+template <typename T>
+struct PcgArgs {
+    int64_t n;
+    int npix;
+    int maxit;
+    T* x;
+    T* r;
+    T* p;
+    const T* q;
+    T* z;
+    const T* bd;         // M_BD inverse blocks
+    int k;               // coarse dimension (TWOLEVEL)
+    const T* Z;          // [k][n]
+    const T* AZ;         // [k][n]
+    const double* L;     // Cholesky factor of E, row-major [k][k]
+    double* partial;     // [grid][PSTRIDE]
+    double* scal;
+    int* flags;
+    unsigned* bar;
+    double* hist_alpha;  // optional, [maxhist]
+    double* hist_beta;
+    double* hist_rz;
+    double* hist_rr;
+    int maxhist;
+    T* zstore;           // optional [maxstore][n]: z_j of every step (Ritz construction)
+    int maxstore;
+};
+
+template <typename T>
+void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks, cudaStream_t s);
+int pcg_max_blocks(int num_sms);
+
+void launch_dot64(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t s);
+void launch_scale_to_f32(const double* a, const double* sq, float* b, int64_t n, cudaStream_t s);
+void launch_axpy_f32(double* x, const float* d, const double* sq, int64_t n, cudaStream_t s);
+void launch_sub(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
+
+}  // namespace mm

@@ -1,0 +1,264 @@
+// Pointing operators and the block-Jacobi preconditioner.
+//
+//   gather   y = P x        (Eq. 2: y_t = x_I + cos 2phi_t x_Q + sin 2phi_t x_U)
+//   scatter  w = P^T z      segmented, warp-reduced sum over the pixel-sorted samples of
+//                           each observed pixel (CSR built at plan time); no atomics, so
+//                           the result is bit-reproducible
+//   M_BD     Eq. 10: B_p = sum_{t in p} t^(i(t))_0 w_t w_t^T, stored inverted
+//                           (symmetric, packed a00 a01 a02 a11 a12 a22)
+#include "mm_internal.h"
+
+namespace mm {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+
+// ----------------------------------------------------------------------------- gather
+template <typename T, int NC>
+__global__ void gather_kernel(const int32_t* __restrict__ pixc,
+                              const typename V2<T>::type* __restrict__ w,
+                              const T* __restrict__ x, T* __restrict__ y, int64_t nt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = pixc[t];
+        T v = (T)0;
+        if (q >= 0) {
+            if constexpr (NC == 1) {
+                v = __ldg(x + q);
+            } else {
+                const typename V2<T>::type ww = w[t];
+                const T* xq = x + 3 * (int64_t)q;
+                v = __ldg(xq) + ww.x * __ldg(xq + 1) + ww.y * __ldg(xq + 2);
+            }
+        }
+        y[t] = v;
+    }
+}
+
+template <typename T>
+static const typename V2<T>::type* weights_time(const Plan& P);
+template <>
+const double2* weights_time<double>(const Plan& P) { return P.w64; }
+template <>
+const float2* weights_time<float>(const Plan& P) { return P.w32; }
+
+template <typename T>
+static const typename V2<T>::type* weights_sorted(const Plan& P);
+template <>
+const double2* weights_sorted<double>(const Plan& P) { return P.wsort64; }
+template <>
+const float2* weights_sorted<float>(const Plan& P) { return P.wsort32; }
+
+static int grid_for(int64_t n, int threads, int num_sms) {
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+void launch_gather(const Plan& P, const T* x, T* y, cudaStream_t s) {
+    const int th = 256;
+    const int g = grid_for(P.nt, th, P.num_sms);
+    if (P.ncomp == 1)
+        gather_kernel<T, 1><<<g, th, 0, s>>>(P.pixc, nullptr, x, y, P.nt);
+    else
+        gather_kernel<T, 3><<<g, th, 0, s>>>(P.pixc, weights_time<T>(P), x, y, P.nt);
+    check_cuda(cudaGetLastError(), "gather launch");
+}
+template void launch_gather<double>(const Plan&, const double*, double*, cudaStream_t);
+template void launch_gather<float>(const Plan&, const float*, float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------- scatter
+// One warp per observed pixel.  Lanes stride over the pixel's sorted samples and keep
+// per-lane partial sums in T; the warp tree (xor shuffles, fixed order) runs in double.
+template <typename T, int NC>
+__global__ void scatter_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ tsort,
+                               const typename V2<T>::type* __restrict__ ws,
+                               const T* __restrict__ z, T* __restrict__ w, int npix,
+                               const int* done) {
+    if (done != nullptr && *(volatile const int*)done) return;
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (int q = blockIdx.x * warps + (threadIdx.x >> 5); q < npix; q += gridDim.x * warps) {
+        const int b = off[q];
+        const int e = off[q + 1];
+        T a0 = 0, a1 = 0, a2 = 0;
+        for (int j = b + lane; j < e; j += 32) {
+            const T v = z[tsort[j]];
+            a0 += v;
+            if constexpr (NC == 3) {
+                const typename V2<T>::type ww = ws[j];
+                a1 += ww.x * v;
+                a2 += ww.y * v;
+            }
+        }
+        double s0 = a0, s1 = a1, s2 = a2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            if constexpr (NC == 3) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+        }
+        if (lane == 0) {
+            if constexpr (NC == 1) {
+                w[q] = (T)s0;
+            } else {
+                w[3 * (int64_t)q] = (T)s0;
+                w[3 * (int64_t)q + 1] = (T)s1;
+                w[3 * (int64_t)q + 2] = (T)s2;
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream_t s) {
+    if (P.npix_obs == 0) return;
+    const int th = 256;
+    const int64_t warps_needed = P.npix_obs;
+    int g = (int)((warps_needed + (th / 32) - 1) / (th / 32));
+    if (g > P.num_sms * 32) g = P.num_sms * 32;
+    if (P.ncomp == 1)
+        scatter_kernel<T, 1><<<g, th, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs, done);
+    else
+        scatter_kernel<T, 3><<<g, th, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z, w,
+                                               P.npix_obs, done);
+    check_cuda(cudaGetLastError(), "scatter launch");
+}
+template void launch_scatter<double>(const Plan&, const double*, double*, const int*, cudaStream_t);
+template void launch_scatter<float>(const Plan&, const float*, float*, const int*, cudaStream_t);
+
+// ------------------------------------------------------------------------ M_BD build
+__device__ __forceinline__ int interval_of(const int64_t* ioff, int K, int64_t t) {
+    int lo = 0, hi = K;   // ioff[lo] <= t < ioff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ioff[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int NC>
+__global__ void bd_build_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ tsort,
+                                const double2* __restrict__ ws, const int64_t* __restrict__ ioff,
+                                const int32_t* __restrict__ ipsd, const double* __restrict__ t0,
+                                int K, int npix, double* __restrict__ bd64, float* __restrict__ bd32) {
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (int q = blockIdx.x * warps + (threadIdx.x >> 5); q < npix; q += gridDim.x * warps) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = off[q] + lane; j < off[q + 1]; j += 32) {
+            const int t = tsort[j];
+            const double d = t0[ipsd[interval_of(ioff, K, t)]];
+            s[0] += d;
+            if constexpr (NC == 3) {
+                const double2 w = ws[j];
+                s[1] += d * w.x;
+                s[2] += d * w.y;
+                s[3] += d * w.x * w.x;
+                s[4] += d * w.x * w.y;
+                s[5] += d * w.y * w.y;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < (NC == 3 ? 6 : 1); ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        if (lane == 0) {
+            if constexpr (NC == 1) {
+                const double inv = 1.0 / s[0];
+                bd64[q] = inv;
+                bd32[q] = (float)inv;
+            } else {
+                // B = [[s0 s1 s2][s1 s3 s4][s2 s4 s5]]; inverse by cofactors (B is SPD and
+                // well conditioned for every observed pixel)
+                const double a = s[0], b = s[1], c = s[2], d = s[3], e = s[4], f = s[5];
+                const double c00 = d * f - e * e;
+                const double c01 = c * e - b * f;
+                const double c02 = b * e - c * d;
+                const double c11 = a * f - c * c;
+                const double c12 = b * c - a * e;
+                const double c22 = a * d - b * b;
+                const double det = a * c00 + b * c01 + c * c02;
+                const double id = 1.0 / det;
+                const double v[6] = {c00 * id, c01 * id, c02 * id, c11 * id, c12 * id, c22 * id};
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    bd64[6 * (int64_t)q + i] = v[i];
+                    bd32[6 * (int64_t)q + i] = (float)v[i];
+                }
+            }
+        }
+    }
+}
+
+void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s) {
+    if (P.npix_obs == 0) return;
+    const int th = 256;
+    int g = (P.npix_obs + 7) / 8;
+    if (g > P.num_sms * 32) g = P.num_sms * 32;
+    if (P.ncomp == 1)
+        bd_build_kernel<1><<<g, th, 0, s>>>(P.csr_off, P.tsort, nullptr, P.ioff, P.ipsd, P.t0, P.K,
+                                             P.npix_obs, bd64, bd32);
+    else
+        bd_build_kernel<3><<<g, th, 0, s>>>(P.csr_off, P.tsort, P.wsort64, P.ioff, P.ipsd, P.t0, P.K,
+                                             P.npix_obs, bd64, bd32);
+    check_cuda(cudaGetLastError(), "bd build launch");
+}
+
+// ------------------------------------------------------------------------ M_BD apply
+template <typename T, int NC>
+__global__ void bd_apply_kernel(const T* __restrict__ bd, const T* __restrict__ r, T* __restrict__ z,
+                                int npix) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npix; q += gridDim.x * blockDim.x) {
+        if constexpr (NC == 1) {
+            z[q] = bd[q] * r[q];
+        } else {
+            const T* m = bd + 6 * (int64_t)q;
+            const T r0 = r[3 * (int64_t)q], r1 = r[3 * (int64_t)q + 1], r2 = r[3 * (int64_t)q + 2];
+            z[3 * (int64_t)q] = m[0] * r0 + m[1] * r1 + m[2] * r2;
+            z[3 * (int64_t)q + 1] = m[1] * r0 + m[3] * r1 + m[4] * r2;
+            z[3 * (int64_t)q + 2] = m[2] * r0 + m[4] * r1 + m[5] * r2;
+        }
+    }
+}
+
+template <typename T>
+static const T* bd_of(const Plan& P);
+template <>
+const double* bd_of<double>(const Plan& P) { return P.bd64; }
+template <>
+const float* bd_of<float>(const Plan& P) { return P.bd32; }
+
+template <typename T>
+void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s) {
+    if (P.npix_obs == 0) return;
+    const int th = 256;
+    const int g = grid_for(P.npix_obs, th, P.num_sms);
+    if (P.ncomp == 1)
+        bd_apply_kernel<T, 1><<<g, th, 0, s>>>(bd_of<T>(P), r, z, P.npix_obs);
+    else
+        bd_apply_kernel<T, 3><<<g, th, 0, s>>>(bd_of<T>(P), r, z, P.npix_obs);
+    check_cuda(cudaGetLastError(), "bd apply launch");
+}
+template void launch_bd_apply<double>(const Plan&, const double*, double*, cudaStream_t);
+template void launch_bd_apply<float>(const Plan&, const float*, float*, cudaStream_t);
+
+// -------------------------------------------------------------------------- helpers
+__global__ void convert_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    convert_kernel<<<grid_for(n, 256, 160), 256, 0, s>>>(a, b, n);
+    check_cuda(cudaGetLastError(), "convert launch");
+}
+
+}  // namespace mm

@@ -1,0 +1,325 @@
+// Banded block-Toeplitz N^-1 by overlap-save FFT in shared memory (Eq. 4; band of
+// Sec. 4.1.4; FFT product of Sec. 2.1).  Included by toeplitz_f64.cu / toeplitz_f32.cu.
+//
+// One CTA per overlap-save tile.  A tile reads B = 2N real samples
+// [out0 - lambda, out0 - lambda + B) of one stationary interval (zero outside it),
+// packs them as N complex values u_m = y_2m + i y_2m+1, runs an N-point complex FFT,
+// turns that into the spectrum of the real block (real-FFT post-processing), multiplies
+// by the real spectrum H of the even kernel (t_|k| for |k| <= lambda, laid out
+// circularly over B), converts back to the packed N-point form and inverts with the
+// same forward FFT (conjugation trick).  Outputs [lambda, lambda + nout) of the block
+// equal the truncated band product exactly (no wrap-around reaches them when
+// nout <= B - 2 lambda).
+//
+// FFT: Stockham autosort, radix 8 passes (+ one radix 2/4 pass), data in shared memory
+// with one padding slot every 128 bytes so that strided stores of a pass are free of
+// bank conflicts, butterflies of a pass held in registers (in-place with barriers).
+// Twiddles from a quarter-wave cosine table cos(2 pi k / B), k = 0..B/4, in shared
+// memory (host-computed in FP64).
+//
+// The tile load can evaluate y = P x on the fly from the map (fused de-pointing).
+#pragma once
+
+#include "mm_internal.h"
+
+namespace mm {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <typename T>
+struct TzArgs {
+    const Tile* tiles;
+    const T* twiddle;      // [N/2 + 1]
+    const T* H;            // [npsd][N + 1]
+    const T* y;            // time-domain input (mode 0)
+    const T* x;            // map (gather modes)
+    const int32_t* pixc;   // [nt]
+    const typename Cx<T>::type* w;  // [nt] (cos, sin) for ncomp = 3
+    T* z;                  // [nt] output
+    const int* done;       // early-exit flag (PCG) or nullptr
+    int lambda;
+};
+
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::type cmul(typename Cx<T>::type a, T c, T s) {
+    // a * (c - i s)
+    typename Cx<T>::type r;
+    r.x = a.x * c + a.y * s;
+    r.y = a.y * c - a.x * s;
+    return r;
+}
+
+// cos / sin of 2 pi m / B from the quarter table (Q = B/4 entries + 1).
+template <typename T, int LOGQ>
+__device__ __forceinline__ void twiddle(const T* tab, int m, T& c, T& s) {
+    constexpr int Q = 1 << LOGQ;
+    const int q = (m >> LOGQ) & 3;
+    const int r = m & (Q - 1);
+    const T cr = tab[r];
+    const T sr = tab[Q - r];
+    switch (q) {
+        case 0: c = cr; s = sr; break;
+        case 1: c = -sr; s = cr; break;
+        case 2: c = -cr; s = -sr; break;
+        default: c = sr; s = -cr; break;
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft(typename Cx<T>::type* v);
+
+template <typename T>
+__device__ __forceinline__ void bfly2(typename Cx<T>::type& a, typename Cx<T>::type& b) {
+    typename Cx<T>::type t = a;
+    a.x = t.x + b.x; a.y = t.y + b.y;
+    b.x = t.x - b.x; b.y = t.y - b.y;
+}
+
+template <>
+__device__ __forceinline__ void dft<double, 2>(double2* v) { bfly2<double>(v[0], v[1]); }
+template <>
+__device__ __forceinline__ void dft<float, 2>(float2* v) { bfly2<float>(v[0], v[1]); }
+
+template <typename T>
+__device__ __forceinline__ void dft4(typename Cx<T>::type& a0, typename Cx<T>::type& a1,
+                                     typename Cx<T>::type& a2, typename Cx<T>::type& a3) {
+    // forward 4-point DFT, outputs in natural order in (a0, a1, a2, a3)
+    typename Cx<T>::type t0, t1, t2, t3;
+    t0.x = a0.x + a2.x; t0.y = a0.y + a2.y;
+    t1.x = a0.x - a2.x; t1.y = a0.y - a2.y;
+    t2.x = a1.x + a3.x; t2.y = a1.y + a3.y;
+    // (a1 - a3) * (-i)
+    t3.x = a1.y - a3.y; t3.y = a3.x - a1.x;
+    a0.x = t0.x + t2.x; a0.y = t0.y + t2.y;
+    a2.x = t0.x - t2.x; a2.y = t0.y - t2.y;
+    a1.x = t1.x + t3.x; a1.y = t1.y + t3.y;
+    a3.x = t1.x - t3.x; a3.y = t1.y - t3.y;
+}
+
+template <>
+__device__ __forceinline__ void dft<double, 4>(double2* v) { dft4<double>(v[0], v[1], v[2], v[3]); }
+template <>
+__device__ __forceinline__ void dft<float, 4>(float2* v) { dft4<float>(v[0], v[1], v[2], v[3]); }
+
+template <typename T>
+__device__ __forceinline__ void dft8(typename Cx<T>::type* v) {
+    using C2 = typename Cx<T>::type;
+    const T h = (T)0.70710678118654752440084436210484903928;  // sqrt(1/2)
+    C2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<T>(e0, e1, e2, e3);
+    dft4<T>(o0, o1, o2, o3);
+    // o_k *= W8^k, W8 = exp(-2 pi i / 8)
+    C2 t;
+    t.x = h * (o1.x + o1.y); t.y = h * (o1.y - o1.x); o1 = t;        // (1 - i)/sqrt2
+    t.x = o2.y; t.y = -o2.x; o2 = t;                                   // -i
+    t.x = h * (o3.y - o3.x); t.y = -h * (o3.x + o3.y); o3 = t;        // (-1 - i)/sqrt2
+    v[0].x = e0.x + o0.x; v[0].y = e0.y + o0.y;
+    v[4].x = e0.x - o0.x; v[4].y = e0.y - o0.y;
+    v[1].x = e1.x + o1.x; v[1].y = e1.y + o1.y;
+    v[5].x = e1.x - o1.x; v[5].y = e1.y - o1.y;
+    v[2].x = e2.x + o2.x; v[2].y = e2.y + o2.y;
+    v[6].x = e2.x - o2.x; v[6].y = e2.y - o2.y;
+    v[3].x = e3.x + o3.x; v[3].y = e3.y + o3.y;
+    v[7].x = e3.x - o3.x; v[7].y = e3.y - o3.y;
+}
+
+template <>
+__device__ __forceinline__ void dft<double, 8>(double2* v) { dft8<double>(v); }
+template <>
+__device__ __forceinline__ void dft<float, 8>(float2* v) { dft8<float>(v); }
+
+// padding: one slot every 128 bytes
+template <typename T> struct PadLog;
+template <> struct PadLog<double> { static constexpr int v = 3; };   // 8 x 16 B
+template <> struct PadLog<float> { static constexpr int v = 4; };    // 16 x 8 B
+
+template <typename T>
+__device__ __forceinline__ int pad(int i) { return i + (i >> PadLog<T>::v); }
+
+// One in-place Stockham pass of radix R on N = 2^LOGN points (Ns = 2^LOGNS).
+template <typename T, int LOGN, int NT, int LOGR, int LOGNS>
+__device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) {
+    using C2 = typename Cx<T>::type;
+    constexpr int N = 1 << LOGN;
+    constexpr int R = 1 << LOGR;
+    constexpr int NB = N >> LOGR;
+    constexpr int BPT = NB / NT;
+    constexpr int Ns = 1 << LOGNS;
+    static_assert(BPT >= 1 && NB % NT == 0, "butterflies per thread");
+    C2 v[BPT][R];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = tid + b * NT;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = a[pad<T>(j + r * NB)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = tid + b * NT;
+        const int k = j & (Ns - 1);
+        if (LOGNS > 0) {
+            // v[r] *= W_{Ns R}^{r k} = W_B^{r k (B / (Ns R))}, B = 2N
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const int m = (r * k) << (LOGN + 1 - LOGNS - LOGR);
+                T c, s;
+                twiddle<T, LOGN - 1>(tab, m, c, s);
+                v[b][r] = cmul<T>(v[b][r], c, s);
+            }
+        }
+        dft<T, R>(v[b]);
+        const int idx = ((j - k) << LOGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[pad<T>(idx + r * Ns)] = v[b][r];
+    }
+    __syncthreads();
+}
+
+template <typename T, int LOGN, int NT, int LOGNS>
+__device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const T* tab) {
+    if constexpr (LOGNS < LOGN) {
+        constexpr int REM = LOGN - LOGNS;
+        constexpr int LOGR = REM >= 3 ? 3 : REM;
+        fft_pass<T, LOGN, NT, LOGR, LOGNS>(a, tab);
+        fft_all<T, LOGN, NT, LOGNS + LOGR>(a, tab);
+    }
+}
+
+// MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map.
+template <typename T, int MODE>
+__device__ __forceinline__ T load_sample(const TzArgs<T>& A, int64_t t) {
+    if constexpr (MODE == 0) {
+        return A.y[t];
+    } else {
+        const int q = __ldg(A.pixc + t);
+        if (q < 0) return (T)0;
+        if constexpr (MODE == 1) {
+            return __ldg(A.x + q);
+        } else {
+            const typename Cx<T>::type w = A.w[t];
+            const T* xq = A.x + 3 * (int64_t)q;
+            return __ldg(xq) + w.x * __ldg(xq + 1) + w.y * __ldg(xq + 2);
+        }
+    }
+}
+
+template <typename T, int LOGN, int NT, int MODE>
+__global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
+    using C2 = typename Cx<T>::type;
+    constexpr int N = 1 << LOGN;
+    constexpr int Q = N / 2;             // B/4
+    if (A.done != nullptr && *(volatile const int*)A.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* a = reinterpret_cast<C2*>(smem_raw);
+    T* tab = reinterpret_cast<T*>(smem_raw + sizeof(C2) * (N + (N >> PadLog<T>::v)));
+    const Tile tile = A.tiles[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
+    const int64_t ws = tile.out0 - A.lambda;
+    for (int m = tid; m < N; m += NT) {
+        const int64_t t0 = ws + 2 * m;
+        C2 u;
+        u.x = (t0 >= tile.ibeg && t0 < tile.iend) ? load_sample<T, MODE>(A, t0) : (T)0;
+        u.y = (t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend) ? load_sample<T, MODE>(A, t0 + 1) : (T)0;
+        a[pad<T>(m)] = u;
+    }
+    __syncthreads();
+    fft_all<T, LOGN, NT, 0>(a, tab);
+    // real-FFT post-processing, spectrum product, pre-processing for the inverse.
+    const T* H = A.H + (int64_t)tile.psd * (N + 1);
+    for (int k = tid; k <= N / 2; k += NT) {
+        const int k2 = (N - k) & (N - 1);
+        const C2 u1 = a[pad<T>(k)];
+        const C2 u2 = a[pad<T>(k2)];
+        T cw, sw;                         // W = cw - i sw = exp(-2 pi i k / B)
+        twiddle<T, LOGN - 1>(tab, k, cw, sw);
+        // E = (u1 + conj u2)/2, O = -i (u1 - conj u2)/2
+        C2 E, O;
+        E.x = (T)0.5 * (u1.x + u2.x); E.y = (T)0.5 * (u1.y - u2.y);
+        O.x = (T)0.5 * (u1.y + u2.y); O.y = (T)-0.5 * (u1.x - u2.x);
+        const C2 WO = cmul<T>(O, cw, sw);
+        C2 X1, X2;                         // X_k = E + W O, X_{N-k} = conj(E - W O)
+        X1.x = E.x + WO.x; X1.y = E.y + WO.y;
+        X2.x = E.x - WO.x; X2.y = -(E.y - WO.y);
+        const T h1 = H[k];
+        const T h2 = H[N - k];
+        C2 Z1, Z2;
+        Z1.x = h1 * X1.x; Z1.y = h1 * X1.y;
+        Z2.x = h2 * X2.x; Z2.y = h2 * X2.y;
+        // V1 = (Z1 + conj Z2)/2 + i conj(W) (Z1 - conj Z2)/2
+        // V2 = (Z2 + conj Z1)/2 - i W (Z2 - conj Z1)/2
+        C2 S1, D1, S2, D2;
+        S1.x = (T)0.5 * (Z1.x + Z2.x); S1.y = (T)0.5 * (Z1.y - Z2.y);
+        D1.x = (T)0.5 * (Z1.x - Z2.x); D1.y = (T)0.5 * (Z1.y + Z2.y);
+        S2.x = S1.x; S2.y = -S1.y;
+        D2.x = -D1.x; D2.y = D1.y;
+        // conj(W) = cw + i sw ; i conj(W) D1
+        C2 V1, V2;
+        {
+            const T px = cw * D1.x - sw * D1.y;   // conj(W) * D1
+            const T py = cw * D1.y + sw * D1.x;
+            V1.x = S1.x - py; V1.y = S1.y + px;   // + i (px + i py)
+        }
+        {
+            const T px = cw * D2.x + sw * D2.y;   // W * D2
+            const T py = cw * D2.y - sw * D2.x;
+            V2.x = S2.x + py; V2.y = S2.y - px;   // - i (px + i py)
+        }
+        // store conjugates: the forward FFT of conj(V) is conj of N * IFFT(V)
+        V1.y = -V1.y;
+        V2.y = -V2.y;
+        a[pad<T>(k)] = V1;
+        if (k2 != k) a[pad<T>(k2)] = V2;
+    }
+    __syncthreads();
+    fft_all<T, LOGN, NT, 0>(a, tab);
+    // outputs: real samples lambda .. lambda + nout - 1 of the block
+    T* zo = A.z + tile.out0;
+    for (int n = tid; n < tile.nout; n += NT) {
+        const int i = n + A.lambda;
+        const C2 v = a[pad<T>(i >> 1)];
+        zo[n] = (i & 1) ? -v.y : v.x;
+    }
+}
+
+template <typename T, int LOGN>
+constexpr int tz_threads() {
+    return (1 << LOGN) / 8 >= 512 ? 512 : ((1 << LOGN) / 8 < 32 ? 32 : (1 << LOGN) / 8);
+}
+
+template <typename T>
+size_t toeplitz_smem_bytes_impl(int logn) {
+    const size_t N = size_t(1) << logn;
+    return sizeof(typename Cx<T>::type) * (N + (N >> PadLog<T>::v)) + sizeof(T) * (N / 2 + 1);
+}
+
+template <typename T, int LOGN, int MODE>
+void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
+    constexpr int NT = tz_threads<T, LOGN>();
+    const size_t smem = toeplitz_smem_bytes_impl<T>(LOGN);
+    auto kern = toeplitz_os_kernel<T, LOGN, NT, MODE>;
+    static bool attr_set = false;   // per instantiation; set once per process
+    if (!attr_set) {
+        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(toeplitz)");
+        attr_set = true;
+    }
+    kern<<<ntiles, NT, smem, s>>>(A);
+    check_cuda(cudaGetLastError(), "toeplitz kernel launch");
+}
+
+template <typename T, int LOGN>
+void launch_mode(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
+    switch (mode) {
+        case 0: launch_one<T, LOGN, 0>(A, ntiles, s); break;
+        case 1: launch_one<T, LOGN, 1>(A, ntiles, s); break;
+        default: launch_one<T, LOGN, 3>(A, ntiles, s); break;
+    }
+}
+
+}  // namespace mm

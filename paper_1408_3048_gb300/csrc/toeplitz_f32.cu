@@ -1,0 +1,40 @@
+// float instantiations of the overlap-save Toeplitz kernel (see toeplitz.cuh).
+#include "toeplitz.cuh"
+
+namespace mm {
+
+template <>
+size_t toeplitz_smem_bytes<float>(int logn) { return toeplitz_smem_bytes_impl<float>(logn); }
+
+template <>
+int toeplitz_max_logn<float>() { return 14; }
+
+template <>
+void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y, const float* x,
+                          float* z, const int* done, cudaStream_t s) {
+    if (tz.ntiles == 0) return;
+    TzArgs<float> A;
+    A.tiles = tz.tiles;
+    A.twiddle = static_cast<const float*>(tz.twiddle);
+    A.H = static_cast<const float*>(tz.H);
+    A.y = y;
+    A.x = x;
+    A.pixc = P.pixc;
+    A.w = P.w32;
+    A.z = z;
+    A.done = done;
+    A.lambda = P.lambda;
+    const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
+    switch (tz.logn) {
+        case 8: launch_mode<float, 8>(A, tz.ntiles, mode, s); break;
+        case 9: launch_mode<float, 9>(A, tz.ntiles, mode, s); break;
+        case 10: launch_mode<float, 10>(A, tz.ntiles, mode, s); break;
+        case 11: launch_mode<float, 11>(A, tz.ntiles, mode, s); break;
+        case 12: launch_mode<float, 12>(A, tz.ntiles, mode, s); break;
+        case 13: launch_mode<float, 13>(A, tz.ntiles, mode, s); break;
+        case 14: launch_mode<float, 14>(A, tz.ntiles, mode, s); break;
+        default: throw Error{MM_ERR_ARG, "unsupported FFT length"};
+    }
+}
+
+}  // namespace mm

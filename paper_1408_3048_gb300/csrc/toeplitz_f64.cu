@@ -1,0 +1,39 @@
+// double instantiations of the overlap-save Toeplitz kernel (see toeplitz.cuh).
+#include "toeplitz.cuh"
+
+namespace mm {
+
+template <>
+size_t toeplitz_smem_bytes<double>(int logn) { return toeplitz_smem_bytes_impl<double>(logn); }
+
+template <>
+int toeplitz_max_logn<double>() { return 13; }
+
+template <>
+void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x,
+                          double* z, const int* done, cudaStream_t s) {
+    if (tz.ntiles == 0) return;
+    TzArgs<double> A;
+    A.tiles = tz.tiles;
+    A.twiddle = static_cast<const double*>(tz.twiddle);
+    A.H = static_cast<const double*>(tz.H);
+    A.y = y;
+    A.x = x;
+    A.pixc = P.pixc;
+    A.w = P.w64;
+    A.z = z;
+    A.done = done;
+    A.lambda = P.lambda;
+    const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
+    switch (tz.logn) {
+        case 8: launch_mode<double, 8>(A, tz.ntiles, mode, s); break;
+        case 9: launch_mode<double, 9>(A, tz.ntiles, mode, s); break;
+        case 10: launch_mode<double, 10>(A, tz.ntiles, mode, s); break;
+        case 11: launch_mode<double, 11>(A, tz.ntiles, mode, s); break;
+        case 12: launch_mode<double, 12>(A, tz.ntiles, mode, s); break;
+        case 13: launch_mode<double, 13>(A, tz.ntiles, mode, s); break;
+        default: throw Error{MM_ERR_ARG, "unsupported FFT length"};
+    }
+}
+
+}  // namespace mm

@@ -1,0 +1,324 @@
+"""Thin ctypes binding of libmm (include/mm.h): argument marshalling only.
+
+Every ``mm_*`` function here has the same name and arguments as its C counterpart;
+arrays may be torch tensors (device or host) or numpy arrays (host), passed by pointer.
+All arithmetic runs in the library's CUDA kernels.  There is no fallback: if libmm.so
+is missing or fails to load, the first call raises.
+
+``Plan`` wraps one ``mm_plan_t`` with torch tensors for the common calls.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libmm.so")
+
+MM_OK, MM_ERR_ARG, MM_ERR_CUDA, MM_ERR_OOM, MM_ERR_NOT_SPD = 0, 1, 2, 3, 4
+MM_ERR_NOT_CONVERGED, MM_ERR_NUMERIC, MM_ERR_TIMEOUT, MM_ERR_STATE = 5, 6, 7, 8
+MM_FP64, MM_FP32 = 0, 1
+MM_WINDOW_GAUSS, MM_WINDOW_RECT = 0, 1
+MM_PREC_BD, MM_PREC_TWOLEVEL = 0, 1
+MM_SOLVE_FP64, MM_SOLVE_MIXED = 0, 1
+
+STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 4: "MM_ERR_NOT_SPD",
+                5: "MM_ERR_NOT_CONVERGED", 6: "MM_ERR_NUMERIC", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_STATE"}
+
+# every symbol include/mm.h declares (checked by the CPU tests)
+EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
+           "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
+           "mm_coarse_vectors", "mm_solve", "mm_last_error", "mm_destroy", "mm_version"]
+
+
+class mm_psd(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("fknee", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+class mm_opts(ctypes.Structure):
+    _fields_ = [("ncomp", ctypes.c_int32), ("lambda_", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("fft_log2_f64", ctypes.c_int32), ("fft_log2_f32", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fsamp", ctypes.c_double), ("rcond_min", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class mm_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("fp64_products", ctypes.c_int32), ("rel_resid", ctypes.c_double),
+                ("rel_resid_rec", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_rhs", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "mm_plan": (I32, [PP, P, I64, I32, P, P, I32, P, P, I32, ctypes.POINTER(mm_opts)]),
+    "mm_plan_info": (I32, [P, P, P, P, P, P]),
+    "mm_plan_pixels": (I32, [P, P, P]),
+    "mm_plan_row": (I32, [P, I32, P]),
+    "mm_gather": (I32, [P, ctypes.c_int, P, P]),
+    "mm_apply_ninv": (I32, [P, ctypes.c_int, P, P]),
+    "mm_scatter": (I32, [P, ctypes.c_int, P, P]),
+    "mm_apply_A": (I32, [P, ctypes.c_int, P, P]),
+    "mm_rhs": (I32, [P, P, P]),
+    "mm_precond": (I32, [P, ctypes.c_int, ctypes.c_int, P, P]),
+    "mm_build_coarse": (I32, [P, ctypes.c_int, ctypes.c_int, P, D, ctypes.c_int]),
+    "mm_coarse_info": (I32, [P, P, P]),
+    "mm_coarse_vectors": (I32, [P, P]),
+    "mm_solve": (I32, [P, P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(mm_stats)]),
+    "mm_last_error": (ctypes.c_char_p, [P]),
+    "mm_destroy": (None, [P]),
+    "mm_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libmm.so (built in-tree by ``paper_1408_3048_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"libmm.so is not built ({LIBPATH}); run paper_1408_3048_gb300.build.build()")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(status, plan=None):
+    if status != MM_OK:
+        msg = lib().mm_last_error(plan).decode()
+        raise MMError(status, msg)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def mm_version():
+    return lib().mm_version().decode()
+
+
+def mm_last_error(plan):
+    return lib().mm_last_error(plan).decode()
+
+
+def mm_plan(pix, nt, npix_sky, weights, interval_off, K, interval_psd, psd, npsd, opts):
+    h = ctypes.c_void_p()
+    st = lib().mm_plan(ctypes.byref(h), _ptr(pix), int(nt), int(npix_sky), _ptr(weights), _ptr(interval_off),
+                       int(K), _ptr(interval_psd), ctypes.cast(psd, ctypes.c_void_p), int(npsd), ctypes.byref(opts))
+    _check(st, None)
+    return h.value
+
+
+def mm_plan_info(plan):
+    npix = ctypes.c_int32()
+    n = ctypes.c_int64()
+    nk = ctypes.c_int64()
+    b64 = ctypes.c_int32()
+    b32 = ctypes.c_int32()
+    _check(lib().mm_plan_info(plan, ctypes.byref(npix), ctypes.byref(n), ctypes.byref(nk), ctypes.byref(b64),
+                              ctypes.byref(b32)), plan)
+    return {"npix_obs": npix.value, "n": n.value, "nkept": nk.value, "fft_block_f64": b64.value,
+            "fft_block_f32": b32.value}
+
+
+def mm_plan_pixels(plan, obs2sky, hits):
+    _check(lib().mm_plan_pixels(plan, _ptr(obs2sky), _ptr(hits)), plan)
+
+
+def mm_plan_row(plan, psd_id, row):
+    _check(lib().mm_plan_row(plan, int(psd_id), _ptr(row)), plan)
+
+
+def mm_gather(plan, precision, x, y):
+    _check(lib().mm_gather(plan, precision, _ptr(x), _ptr(y)), plan)
+
+
+def mm_apply_ninv(plan, precision, y, z):
+    _check(lib().mm_apply_ninv(plan, precision, _ptr(y), _ptr(z)), plan)
+
+
+def mm_scatter(plan, precision, z, w):
+    _check(lib().mm_scatter(plan, precision, _ptr(z), _ptr(w)), plan)
+
+
+def mm_apply_A(plan, precision, x, y):
+    _check(lib().mm_apply_A(plan, precision, _ptr(x), _ptr(y)), plan)
+
+
+def mm_rhs(plan, d, b):
+    _check(lib().mm_rhs(plan, _ptr(d), _ptr(b)), plan)
+
+
+def mm_precond(plan, kind, precision, r, z):
+    _check(lib().mm_precond(plan, kind, precision, _ptr(r), _ptr(z)), plan)
+
+
+def mm_build_coarse(plan, k, precision, bprime, tol, maxit):
+    _check(lib().mm_build_coarse(plan, int(k), precision, _ptr(bprime), float(tol), int(maxit)), plan)
+
+
+def mm_coarse_info(plan):
+    k = ctypes.c_int32()
+    _check(lib().mm_coarse_info(plan, ctypes.byref(k), None), plan)
+    vals = np.zeros(max(k.value, 1), dtype=np.float64)
+    _check(lib().mm_coarse_info(plan, None, vals.ctypes.data), plan)
+    return k.value, vals[: k.value]
+
+
+def mm_coarse_vectors(plan, Z):
+    _check(lib().mm_coarse_vectors(plan, _ptr(Z)), plan)
+
+
+def mm_solve(plan, d, tol, maxit, kind, solver, m, raise_on_error=True):
+    st = mm_stats()
+    status = lib().mm_solve(plan, _ptr(d), float(tol), int(maxit), kind, solver, _ptr(m), ctypes.byref(st))
+    if raise_on_error:
+        _check(status, plan)
+    return status, st
+
+
+def mm_destroy(plan):
+    lib().mm_destroy(plan)
+
+
+# ------------------------------------------------------------------------ Plan class
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """One map-making problem on the current CUDA device (torch tensors in and out)."""
+
+    def __init__(self, pix, npix_sky, weights, offsets, interval_psd, psds, lam, fsamp=100.0, ncomp=None,
+                 window=MM_WINDOW_GAUSS, rcond_min=1e-6, fft_log2=(0, 0), stream=None):
+        torch = _torch()
+        self._torch = torch
+        pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32))
+        if ncomp is None:
+            ncomp = 1 if weights is None else 3
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1, 2))
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        ipsd = np.ascontiguousarray(np.asarray(interval_psd, dtype=np.int32))
+        ps = np.asarray(psds, dtype=np.float64).reshape(-1, 3)
+        arr = (mm_psd * len(ps))(*[mm_psd(*map(float, p)) for p in ps])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o = mm_opts(ncomp=ncomp, lambda_=int(lam), window=window, fft_log2_f64=int(fft_log2[0]),
+                    fft_log2_f32=int(fft_log2[1]), reserved=0, fsamp=float(fsamp), rcond_min=float(rcond_min),
+                    stream=stream.cuda_stream)
+        self.handle = mm_plan(pix, pix.size, npix_sky, w, off, off.size - 1, ipsd, arr, len(ps), o)
+        info = mm_plan_info(self.handle)
+        self.npix_obs = info["npix_obs"]
+        self.n = info["n"]
+        self.nkept = info["nkept"]
+        self.fft_block_f64 = info["fft_block_f64"]
+        self.fft_block_f32 = info["fft_block_f32"]
+        self.nt = int(pix.size)
+        self.ncomp = ncomp
+        self.lam = int(lam)
+        self.npsd = len(ps)
+
+    # helpers
+    def _dtype(self, precision):
+        return self._torch.float64 if precision == MM_FP64 else self._torch.float32
+
+    def _new(self, size, precision):
+        return self._torch.empty(size, dtype=self._dtype(precision), device="cuda")
+
+    def pixels(self):
+        o2s = np.zeros(self.npix_obs, dtype=np.int32)
+        hits = np.zeros(self.npix_obs, dtype=np.int32)
+        mm_plan_pixels(self.handle, o2s, hits)
+        return o2s, hits
+
+    def row(self, psd_id):
+        r = np.zeros(self.lam + 1, dtype=np.float64)
+        mm_plan_row(self.handle, psd_id, r)
+        return r
+
+    def gather(self, x, precision=MM_FP64):
+        y = self._new(self.nt, precision)
+        mm_gather(self.handle, precision, x, y)
+        return y
+
+    def apply_ninv(self, y, precision=MM_FP64):
+        z = self._new(self.nt, precision)
+        mm_apply_ninv(self.handle, precision, y, z)
+        return z
+
+    def scatter(self, z, precision=MM_FP64):
+        w = self._new(self.n, precision)
+        mm_scatter(self.handle, precision, z, w)
+        return w
+
+    def apply_A(self, x, precision=MM_FP64, out=None):
+        y = self._new(self.n, precision) if out is None else out
+        mm_apply_A(self.handle, precision, x, y)
+        return y
+
+    def rhs(self, d):
+        b = self._new(self.n, MM_FP64)
+        mm_rhs(self.handle, d, b)
+        return b
+
+    def precond(self, r, kind=MM_PREC_BD, precision=MM_FP64):
+        z = self._new(self.n, precision)
+        mm_precond(self.handle, kind, precision, r, z)
+        return z
+
+    def build_coarse(self, k, precision=MM_FP64, bprime=None, tol=1e-6, maxit=1000):
+        mm_build_coarse(self.handle, k, precision, bprime, tol, maxit)
+        return mm_coarse_info(self.handle)
+
+    def coarse_vectors(self):
+        k, _ = mm_coarse_info(self.handle)
+        Z = np.zeros(k * self.n, dtype=np.float64)
+        mm_coarse_vectors(self.handle, Z)
+        return Z.reshape(k, self.n).T.copy()
+
+    def solve(self, d, tol=1e-6, maxit=1000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, out=None,
+              raise_on_error=True):
+        m = self._new(self.n, MM_FP64) if out is None else out
+        status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
+        return m, st.as_dict(), status
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C-ABI) against the FP64 oracle -- needs a GPU.
+
+Tolerances: integer outputs (observed pixels, hits) bit-exact; FP64 operators to
+1e-12 relative L2 (the FFT Toeplitz product and the oracle's direct sum differ only by
+rounding, ~log2(B) * 1e-16 relative to the band norm); FP32 operators to 2e-5 relative
+L2 (FP32 FFT rounding, ~log2(B) * 6e-8, times the dynamic range of the 1/f band); maps
+to 1e-6 relative L2 with PCG iteration counts within 2 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import precond as oprec
+from oracle.pcg import pcg
+from paper_1408_3048_gb300 import mm, synth
+from problems import oracle_problem, tiny_scan
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(scan, **kw):
+    return mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
+                   scan.lam, scan.fsamp, **kw)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+SCANS = {
+    "T_tiny": lambda: tiny_scan(ncomp=1),
+    "P_tiny": lambda: tiny_scan(ncomp=3),
+    "T_ragged": lambda: synth.raster_scan(24, 20, 3, 20000, 1, 3, 300, [(1.0, 1.0, 1.0), (0.7, 2.0, 1.7), (1.3, 0.3, 1.2)],
+                                          det_psd=[0, 1, 2], uneven=(2000, 12000), seed=4),
+    "P_ragged": lambda: synth.raster_scan(24, 24, 4, 24000, 3, 4, 500, [(1.0, 1.0, 1.0), (0.8, 1.5, 1.5)],
+                                          det_psd=[0, 1, 0, 1], uneven=(3000, 9000), seed=5),
+    "c2_small": lambda: synth.config(2, scale=64),
+}
+
+
+@pytest.fixture(scope="module", params=list(SCANS))
+def case(request):
+    scan = SCANS[request.param]()
+    pr = oracle_problem(scan)
+    plan = _plan(scan)
+    yield request.param, scan, pr, plan
+    plan.close()
+
+
+def test_pixels_and_hits_bit_exact(case):
+    _, scan, pr, plan = case
+    o2s, hits = plan.pixels()
+    assert plan.npix_obs == pr.npix_obs and plan.n == pr.n
+    assert np.array_equal(o2s, pr.obs2sky)
+    assert np.array_equal(hits, pr.hits)
+
+
+def test_rows_match(case):
+    _, scan, pr, plan = case
+    for p in range(plan.npsd):
+        r = plan.row(p)
+        assert np.abs(r - pr.rows[p]).max() <= 1e-13 * np.abs(pr.rows[p]).max()
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32])
+def test_gather_ninv_scatter(case, prec):
+    _, scan, pr, plan = case
+    rng = np.random.default_rng(1)
+    dt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+    tol = 1e-12 if prec == mm.MM_FP64 else 2e-5
+    x = rng.standard_normal(pr.n)
+    xc = _cuda(x, dt)
+    y = plan.gather(xc, prec).cpu().numpy()
+    assert _rel(y, pr.P(xc.double().cpu().numpy())) <= (1e-15 if prec == mm.MM_FP64 else 1e-7)
+    t = rng.standard_normal(pr.nt)
+    tc = _cuda(t, dt)
+    z = plan.apply_ninv(tc, prec).cpu().numpy()
+    zr = pr.Ninv(tc.double().cpu().numpy())
+    assert _rel(z, zr) <= tol
+    # element-wise: every output within tol of the band norm scale
+    scale = np.abs(pr.rows[0]).sum() * np.abs(t).max()
+    assert np.abs(z - zr).max() <= tol * scale * 10
+    w = plan.scatter(tc, prec).cpu().numpy()
+    assert _rel(w, pr.PT(tc.double().cpu().numpy())) <= (1e-14 if prec == mm.MM_FP64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32])
+def test_apply_A(case, prec):
+    _, scan, pr, plan = case
+    dt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+    x = np.random.default_rng(2).standard_normal(pr.n)
+    xc = _cuda(x, dt)
+    y = plan.apply_A(xc, prec).cpu().numpy()
+    assert _rel(y, pr.A(xc.double().cpu().numpy())) <= (1e-12 if prec == mm.MM_FP64 else 3e-5)
+
+
+def test_A_symmetric_deterministic(case):
+    _, scan, pr, plan = case
+    rng = np.random.default_rng(3)
+    x, y = _cuda(rng.standard_normal(pr.n)), _cuda(rng.standard_normal(pr.n))
+    Ax1 = plan.apply_A(x)
+    Ax2 = plan.apply_A(x)
+    assert torch.equal(Ax1, Ax2)                     # bit-reproducible (no atomics)
+    Ay = plan.apply_A(y)
+    a, b = float(y @ Ax1), float(x @ Ay)
+    assert abs(a - b) <= 1e-12 * float(torch.linalg.norm(Ax1) * torch.linalg.norm(y))
+    assert float(x @ Ax1) > 0
+
+
+def test_rhs_and_bd(case):
+    _, scan, pr, plan = case
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal(pr.nt)
+    b = plan.rhs(_cuda(d)).cpu().numpy()
+    assert _rel(b, pr.rhs(d)) <= 1e-12
+    bd = oprec.BlockJacobi(pr)
+    r = rng.standard_normal(pr.n)
+    for prec, tol in ((mm.MM_FP64, 1e-12), (mm.MM_FP32, 1e-5)):
+        dt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+        z = plan.precond(_cuda(r, dt), mm.MM_PREC_BD, prec).cpu().numpy()
+        assert _rel(z, bd.apply(r)) <= tol
+
+
+def _data(scan, real=0):
+    sky = synth.sky_map(scan.npix_sky, scan.ncomp, 1000)
+    n = synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds, scan.fsamp, 2000 + real)
+    return synth.tod(scan, sky, n)
+
+
+def test_solve_fp64_bd_matches_oracle(case):
+    name, scan, pr, plan = case
+    d = _data(scan)
+    bd = oprec.BlockJacobi(pr)
+    ref = pcg(pr.A, bd.apply, pr.rhs(d), 1e-6, 3000)
+    m, st, status = plan.solve(_cuda(d), tol=1e-6, maxit=3000)
+    assert status == mm.MM_OK and st["converged"] == 1
+    assert abs(st["iters"] - ref.iters) <= 2, (st["iters"], ref.iters)
+    assert _rel(m.cpu().numpy(), ref.x) <= 1e-6
+    assert st["rel_resid"] <= 1.5e-6
+
+
+def test_solve_mixed_reaches_tolerance(case):
+    name, scan, pr, plan = case
+    d = _data(scan)
+    ref = pcg(pr.A, oprec.BlockJacobi(pr).apply, pr.rhs(d), 1e-10, 5000)
+    m, st, status = plan.solve(_cuda(d), tol=1e-6, maxit=5000, solver=mm.MM_SOLVE_MIXED)
+    assert status == mm.MM_OK
+    # true FP64 residual of the returned map, recomputed by the oracle
+    b = pr.rhs(d)
+    mm_ = m.cpu().numpy()
+    assert np.linalg.norm(b - pr.A(mm_)) / np.linalg.norm(b) <= 1e-6
+    assert st["rel_resid"] <= 1e-6
+
+
+def test_two_level(case):
+    name, scan, pr, plan = case
+    k = 8 if pr.n < 2000 else 16
+    d0, d1 = _data(scan, 0), _data(scan, 1)
+    b0 = pr.rhs(d0)
+    bd = oprec.BlockJacobi(pr)
+    r0 = pcg(pr.A, bd.apply, b0, 1e-6, 3000, record=True)
+    Zo, th = oprec.ritz_coarse_space(r0.alphas, r0.betas, r0.zs, r0.rzs, k)
+    tl = oprec.TwoLevel(pr, bd, Zo)
+    kk, ritz = plan.build_coarse(k, mm.MM_FP64, bprime=_cuda(b0), tol=1e-6, maxit=3000)
+    assert kk >= 1
+    # converged (smallest) Ritz values agree with the oracle's Lanczos
+    np.testing.assert_allclose(ritz[:3], th[:3], rtol=1e-6)
+    ref = pcg(pr.A, tl.apply, pr.rhs(d1), 1e-6, 3000)
+    m, st, status = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL)
+    assert status == mm.MM_OK
+    assert abs(st["iters"] - ref.iters) <= 2, (st["iters"], ref.iters)
+    assert _rel(m.cpu().numpy(), ref.x) <= 1e-6
+    # M_2lvl application (Eq. 12) against the oracle's operator built on the library's Z
+    Zl = plan.coarse_vectors()
+    assert np.allclose(Zl.T @ Zl, np.eye(kk), atol=1e-10)
+    tl_lib = oprec.TwoLevel(pr, bd, Zl)
+    r = np.random.default_rng(5).standard_normal(pr.n)
+    z = plan.precond(_cuda(r), mm.MM_PREC_TWOLEVEL, mm.MM_FP64).cpu().numpy()
+    assert _rel(z, tl_lib.apply(r)) <= 1e-9
+    z32 = plan.precond(_cuda(r, torch.float32), mm.MM_PREC_TWOLEVEL, mm.MM_FP32).cpu().numpy()
+    assert _rel(z32, tl_lib.apply(r)) <= 1e-4
+    # T5 on the library operator: M_2lvl A Z = Z
+    AZ0 = plan.apply_A(_cuda(Zl[:, 0]))
+    mz = plan.precond(AZ0, mm.MM_PREC_TWOLEVEL, mm.MM_FP64).cpu().numpy()
+    assert _rel(mz, Zl[:, 0]) <= 1e-8
+    # mixed two-level reaches the tolerance in the true residual
+    m2, st2, status2 = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL,
+                                  solver=mm.MM_SOLVE_MIXED)
+    assert status2 == mm.MM_OK
+    b1 = pr.rhs(d1)
+    assert np.linalg.norm(b1 - pr.A(m2.cpu().numpy())) / np.linalg.norm(b1) <= 1e-6
+
+
+def test_errors_are_reported():
+    scan = tiny_scan()
+    with pytest.raises(mm.MMError) as e:
+        mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
+                10 ** 6, scan.fsamp)
+    assert e.value.status == mm.MM_ERR_ARG
+    bad = scan.pix.copy()
+    bad[3] = scan.npix_sky
+    with pytest.raises(mm.MMError) as e:
+        mm.Plan(bad, scan.npix_sky, None, scan.offsets, scan.interval_psd, scan.psds, scan.lam)
+    assert e.value.status == mm.MM_ERR_ARG
+    # a hard-truncated steep spectrum has a negative symbol (the oracle's noise pin)
+    s2 = synth.raster_scan(8, 8, 1, 8192, 1, 2, 64, [(1.0, 1.0, 4.0)], seed=1)
+    with pytest.raises(mm.MMError) as e:
+        mm.Plan(s2.pix, s2.npix_sky, None, s2.offsets, s2.interval_psd, s2.psds, 64, window=mm.MM_WINDOW_RECT)
+    assert e.value.status == mm.MM_ERR_NOT_SPD
+    plan = _plan(scan)
+    with pytest.raises(mm.MMError) as e:
+        plan.precond(_cuda(np.ones(plan.n)), mm.MM_PREC_TWOLEVEL)
+    assert e.value.status == mm.MM_ERR_STATE
+    d = _data(scan)
+    m, st, status = plan.solve(_cuda(d), tol=1e-12, maxit=2, raise_on_error=False)
+    assert status == mm.MM_ERR_NOT_CONVERGED and st["iters"] == 2
+    plan.close()
+
+
+def test_host_buffers_e2e():
+    scan = tiny_scan(ncomp=3)
+    pr = oracle_problem(scan)
+    plan = _plan(scan)
+    d = _data(scan)
+    out = np.zeros(plan.n)
+    st = mm.mm_solve(plan.handle, d, 1e-8, 1000, mm.MM_PREC_BD, mm.MM_SOLVE_FP64, out)[1]
+    ref = pcg(pr.A, oprec.BlockJacobi(pr).apply, pr.rhs(d), 1e-8, 1000)
+    assert _rel(out, ref.x) <= 1e-6 and st.converged == 1
+    plan.close()
