@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: GLS map-making time-to-solution on one GB300.
+
+Workload (one "step" = one full map solve): the polarised I/Q/U raster scan of
+paper_1408_3048_gb300.synth.config(2) -- 256 x 256 patch, 16 detectors x 2^20 = 2^24
+samples, 256 stationary intervals of uneven length, per-detector 1/f noise
+(f_knee in [0.1, 2] Hz, alpha in [1, 2]), Toeplitz half bandwidth lambda = 4096.
+
+A step computes b = P^T N^-1 d and solves (P^T N^-1 P) m = b to relative residual 1e-6
+with the two-level preconditioner (32 Ritz vectors of M_BD A, built once from another
+noise realisation and reported separately) in mixed precision (FP32 operators inside
+PCG, FP64 dots, E factor and iterative-refinement residual).  The FP64 block-Jacobi
+solve of the same data is timed beside it (``fp64_bj``).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload and extrapolates to a full solve (see "cpu_baseline" in the output).
+N > 1 (torchrun): every rank solves its own noise realisation on its own GPU (replicas,
+no collective on the data path); the time is the max over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-6
+K_COARSE = 32
+CONFIG = 2
+GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
+WORKLOAD = ("polarised I/Q/U raster, 256x256 patch, 16 detectors x 2^20 = 2^24 samples, 256 uneven "
+            "intervals, 1/f noise fknee U[0.1,2] Hz alpha U[1,2], lambda=4096, tol 1e-6, two-level k=32")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="build, warm up, then run one step between cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off); prints a one-line JSON summary only")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------- inputs
+def make_inputs(realisations):
+    from paper_1408_3048_gb300 import synth
+    scan = synth.config(CONFIG)
+    sky = synth.sky_map(scan.npix_sky, scan.ncomp, 1000 + CONFIG)
+    ds = [synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds, scan.fsamp,
+                                                       2000 + 100 * CONFIG + r)) for r in realisations]
+    return scan, ds
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from paper_1408_3048_gb300 import synth
+from oracle.system import Problem
+from oracle.precond import BlockJacobi
+from oracle.pcg import pcg
+steps, iters = {steps}, {iters}
+scan = synth.config({cfg})
+sky = synth.sky_map(scan.npix_sky, scan.ncomp, {sky_seed})
+d = synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds, scan.fsamp, {noise_seed}))
+t = time.perf_counter()
+pr = Problem(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds, scan.fsamp,
+             scan.lam, scan.ncomp)
+bd = BlockJacobi(pr)
+t_plan = time.perf_counter() - t
+rng = np.random.default_rng(0)
+Z = np.linalg.qr(rng.standard_normal((pr.n, {k})))[0]
+AZ = rng.standard_normal((pr.n, {k}))
+import scipy.linalg
+lu = scipy.linalg.lu_factor(Z.T @ AZ + {k} * np.eye({k}))
+A = lambda x: pr.A(x, route="fft")
+def m2(r):
+    v = scipy.linalg.lu_solve(lu, Z.T @ r)
+    return bd.apply(r - AZ @ v) + Z @ v
+out = []
+for s in range(steps):
+    t0 = time.perf_counter()
+    b = pr.rhs(d, route="fft")
+    t1 = time.perf_counter()
+    res = pcg(A, m2, b, 0.0, {sample_iters})
+    t2 = time.perf_counter()
+    per_it = (t2 - t1) / {sample_iters}
+    out.append((t1 - t0) + iters * per_it)
+print(json.dumps({{"values": out, "t_plan": t_plan, "per_iter": per_it, "rhs": t1 - t0}}))
+"""
+
+
+def oracle_time_to_solution(steps, iters, sample_iters=2):
+    """Run the oracle in a fresh single-threaded process; return (values, info)."""
+    code = ORACLE_SNIPPET.format(root=ROOT, steps=steps, iters=iters, cfg=CONFIG, sky_seed=1000 + CONFIG,
+                                 noise_seed=2000 + 100 * CONFIG + 1, k=K_COARSE, sample_iters=sample_iters)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    j = json.loads(r.stdout.strip().splitlines()[-1])
+    return j["values"], j
+
+
+def oracle_iterations():
+    if os.path.exists(GOLDEN):
+        with open(GOLDEN) as f:
+            g = json.load(f)
+        return int(g["iters_2lvl"]), "oracle two-level PCG iteration count (tests/golden/c2_oracle.json)"
+    return None, None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    iters, src = oracle_iterations()
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count file missing"}))
+        return
+    vals, info = oracle_time_to_solution(a.warmup + a.steps, iters)
+    v = float(np.mean(vals[a.warmup:]))
+    line = {
+        "impl": "reference", "metric": "time-to-solution @1e-6 resid, two-level (FP64 CPU oracle)",
+        "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: b = P^T N^-1 d plus 2 two-level PCG iterations of the full "
+                                   f"workload, extrapolated to {iters} iterations ({src})"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# -------------------------------------------------------------------- GPU arm
+def run_ours(a, rank, world, local_rank):
+    import torch
+    from paper_1408_3048_gb300 import mm
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    scan, (d0, d1) = make_inputs([0, 1 + rank])
+    plan = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
+                   scan.lam, scan.fsamp, stream=stream)
+    dc0 = torch.from_numpy(d0).to(dev)
+    dc1 = torch.from_numpy(d1).to(dev)
+    m = torch.empty(plan.n, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # coarse space (a posteriori, from realisation 0), timed separately
+    b0 = plan.rhs(dc0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    kk, ritz = plan.build_coarse(K_COARSE, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)
+    torch.cuda.synchronize()
+    t_coarse = time.perf_counter() - t
+
+    def step():
+        return plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, out=m)[1]
+
+    if a.profile:
+        for _ in range(max(1, a.warmup)):
+            step()
+        torch.cuda.synchronize()
+        n0 = mm.mm_launch_count()
+        torch.cuda.profiler.start()
+        st = step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profiled_step": st, "gpu_launches": mm.mm_launch_count() - n0}))
+        plan.close()
+        return
+
+    # FP64 block-Jacobi and FP64 two-level references (one solve each)
+    _, st_bj, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_BD, mm.MM_SOLVE_FP64, out=m)
+    _, st_2f, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
+    m_ref64 = m.clone()
+
+    for _ in range(a.warmup):
+        step()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = mm.mm_launch_count()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step() for _ in range(a.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = (mm.mm_launch_count() - n0) // max(a.steps, 1)
+    clk = clocks.stop()
+    t_max = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms_step = float(t_max.item()) / a.steps
+    st = stats[-1]
+    err_vs_fp64 = float(torch.linalg.norm(m - m_ref64) / torch.linalg.norm(m_ref64))
+
+    # per-kernel profile of one more step (events around every launch)
+    plan.profile(True)
+    step()
+    prof = plan.profile_read()
+    plan.profile(False)
+    # A x alone, FP32 and FP64 (CUDA events, inputs already resident)
+    x32 = torch.randn(plan.n, dtype=torch.float32, device=dev)
+    x64 = x32.double()
+    y32 = torch.empty_like(x32)
+    y64 = torch.empty_like(x64)
+    ax = {}
+    for prec, x, y in ((mm.MM_FP32, x32, y32), (mm.MM_FP64, x64, y64)):
+        for _ in range(3):
+            plan.apply_A(x, prec, out=y)
+        plan.profile(True)
+        reps = 20 if prec == mm.MM_FP32 else 5
+        for _ in range(reps):
+            plan.apply_A(x, prec, out=y)
+        p = plan.profile_read()
+        plan.profile(False)
+        key = "f32" if prec == mm.MM_FP32 else "f64"
+        ax[key] = {"toeplitz_ms": p[f"toeplitz_{key}"][0] / reps, "scatter_ms": p[f"scatter_{key}"][0] / reps}
+
+    # e2e through the C-ABI with host buffers (pinned d in, host m out)
+    dh = torch.from_numpy(d1).pin_memory()
+    mh = torch.empty(plan.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        mm.mm_solve(plan.handle, dh, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, mh)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t) / a.steps
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel of the step
+    hbm, peak_src = peaks()
+    nt, n = plan.nt, plan.n
+    stages = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    s = 4 if dom.endswith("f32") else 8
+    if dom.startswith("toeplitz"):
+        # pointing (4 B) + weights (2 s) read, TOD written (s) per sample; map read
+        alg_bytes = nt * (4 + 2 * s + s) + n * s
+    elif dom.startswith("scatter"):
+        # sorted sample index (4 B) + weights (2 s) + TOD (s) per sample; map written
+        alg_bytes = nt * (4 + 2 * s + s) + n * s
+    else:
+        alg_bytes = 8 * n * s
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    # A x HBM GB/s (algorithmic bytes per A x: pointing + weights + x and y; TOD excluded)
+    axgbs = {}
+    for key, sz in (("f32", 4), ("f64", 8)):
+        t_ax = (ax[key]["toeplitz_ms"] + ax[key]["scatter_ms"]) * 1e-3
+        axgbs[key] = (nt * (4 + 2 * sz) + 2 * n * sz) / t_ax / 1e9
+    line = {
+        "metric": "time-to-solution @1e-6 resid (2-level mixed vs FP64 BJ, 1 GPU); A·x HBM GB/s",
+        "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nt": nt, "n": n, "npix_obs": plan.npix_obs, "k_kept": kk,
+                   "fft_block_f64": plan.fft_block_f64, "fft_block_f32": plan.fft_block_f32,
+                   "l2": "inputs larger than L2 (d 134 MB, pointing 335 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gpu_launches": int(launches),
+        "solve": {"iters": st["iters"], "outer": st["outer"], "fp64_products": st["fp64_products"],
+                  "rel_resid": st["rel_resid"], "map_rel_err_vs_fp64_2lvl": err_vs_fp64},
+        "fp64_bj": {"s": st_bj["ms_total"] / 1e3, "iters": st_bj["iters"], "rel_resid": st_bj["rel_resid"]},
+        "fp64_2lvl": {"s": st_2f["ms_total"] / 1e3, "iters": st_2f["iters"]},
+        "speedup_vs_fp64_bj": (st_bj["ms_total"] / 1e3) / (ms_step / 1e3),
+        "coarse_build_s": t_coarse,
+        "ax_gbs": {k: round(v, 1) for k, v in axgbs.items()},
+        "ax_ms": ax,
+        "profile_ms": {k: [round(v[0], 4), v[1]] for k, v in stages.items()},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": peak_src},
+        "clocks": clk,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(nt * 8), "d2h_bytes_per_step": int(n * 8)},
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        iters, src = oracle_iterations()
+        if iters is None:
+            iters, src = st_2f["iters"], "FP64 two-level PCG iteration count of this run"
+        try:
+            vals, info = oracle_time_to_solution(1, iters)
+            line["cpu_baseline"] = {"value": vals[0], "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"b = P^T N^-1 d plus 2 two-level PCG iterations of the full workload "
+                                              f"(FP64 NumPy/SciPy, 1 thread), extrapolated to {iters} iterations "
+                                              f"({src}); plan time {info['t_plan']:.1f} s excluded"}
+        except Exception as ex:  # the GPU number stands; say why the baseline is missing
+            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(ex)[:200]}"}
+    print(json.dumps(line))
+    plan.close()
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(a, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -207,6 +207,18 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
 mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int kind,
                    int solver, double* m, mm_stats* st);
 
+/*
+ * Per-stage device timers.  mm_profile(plan, 1) clears and enables them: every later
+ * launch of the Toeplitz kernel (stage 0 FP64, 1 FP32; de-pointing fused or not), the
+ * scatter kernel (2 FP64, 3 FP32) and the PCG vector kernel (4 FP64, 5 FP32) is
+ * bracketed by CUDA events on the plan's stream (stages 6-7 are reserved).
+ * mm_profile_read returns the summed milliseconds (host double[8]) and launch counts
+ * (host int64[8]); either may be NULL.
+ * The events add a few microseconds per launch; mm_profile(plan, 0) turns them off.
+ */
+mm_status mm_profile(mm_plan_t plan, int enable);
+mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
+
 /* Human-readable description of the last error on this plan (never NULL). */
 const char* mm_last_error(mm_plan_t plan);
 
@@ -215,6 +227,9 @@ void mm_destroy(mm_plan_t plan);
 
 /* Library version string. */
 const char* mm_version(void);
+
+/* Number of CUDA kernels this process has launched through the library so far. */
+int64_t mm_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 // (Sec. 3.1) with FP64 or mixed arithmetic plus iterative refinement, and the
 // a posteriori coarse space (Sec. 3.3.2, App. A, App. C).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -17,6 +18,9 @@
 namespace mm {
 
 static thread_local std::string g_last_error = "no error";
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
 
 void check_cuda(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
@@ -60,6 +64,44 @@ static void d2h(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "memcpy D2H");
 }
 static void sync(cudaStream_t s) { check_cuda(cudaStreamSynchronize(s), "stream synchronize"); }
+static void sync(Plan& P) {
+    sync(P.stream);
+    if (P.prof.on) prof_flush(P);
+}
+
+// ------------------------------------------------------------------------ profiling
+int prof_begin(Plan& P, int stage) {
+    if (!P.prof.on) return -1;
+    cudaEvent_t ev[2];
+    for (int i = 0; i < 2; ++i) {
+        if (!P.prof.pool.empty()) {
+            ev[i] = P.prof.pool.back();
+            P.prof.pool.pop_back();
+        } else {
+            check_cuda(cudaEventCreate(&ev[i]), "event");
+        }
+    }
+    check_cuda(cudaEventRecord(ev[0], P.stream), "event record");
+    P.prof.pending.push_back({stage, ev[0], ev[1]});
+    return (int)P.prof.pending.size() - 1;
+}
+
+void prof_end(Plan& P, int slot) {
+    if (slot < 0) return;
+    check_cuda(cudaEventRecord(P.prof.pending[(size_t)slot].b, P.stream), "event record");
+}
+
+void prof_flush(Plan& P) {
+    for (auto& e : P.prof.pending) {
+        float ms = 0.f;
+        check_cuda(cudaEventElapsedTime(&ms, e.a, e.b), "event elapsed");
+        P.prof.ms[e.stage] += ms;
+        P.prof.launches[e.stage] += 1;
+        P.prof.pool.push_back(e.a);
+        P.prof.pool.push_back(e.b);
+    }
+    P.prof.pending.clear();
+}
 
 // ----------------------------------------------------------------------------- plan
 struct PlanHolder : Plan {
@@ -107,6 +149,11 @@ static void destroy_plan(PlanHolder* P) {
     if (P->ev0) (void)cudaEventDestroy(P->ev0);
     if (P->ev1) (void)cudaEventDestroy(P->ev1);
     if (P->ev2) (void)cudaEventDestroy(P->ev2);
+    for (auto& e : P->prof.pending) {
+        (void)cudaEventDestroy(e.a);
+        (void)cudaEventDestroy(e.b);
+    }
+    for (auto e : P->prof.pool) (void)cudaEventDestroy(e);
     delete P;
 }
 
@@ -377,8 +424,13 @@ template <> const float* bd_ptr<float>(const Plan& P) { return P.bd32; }
 // y = A x = P^T N^-1 P x, de-pointing fused into the Toeplitz tile load (Eq. 8).
 template <typename T>
 static void apply_A(Plan& P, const T* x, T* y, const int* done) {
+    const bool f64 = sizeof(T) == 8;
+    int s0 = prof_begin(P, f64 ? ST_TZ64 : ST_TZ32);
     launch_toeplitz<T>(P, tz_of<T>(P), nullptr, x, tod_of<T>(P), done, P.stream);
+    prof_end(P, s0);
+    s0 = prof_begin(P, f64 ? ST_SC64 : ST_SC32);
     launch_scatter<T>(P, tod_of<T>(P), y, done, P.stream);
+    prof_end(P, s0);
 }
 
 // ---------------------------------------------------------------------------- PCG
@@ -440,19 +492,21 @@ static PcgOutcome run_pcg(PlanHolder& P, bool two, double tol, int maxit, T* zst
     PcgOutcome out;
     while (true) {
         d2h(P.h_flags, P.pcg.flags, 16, s);
-        sync(s);
+        sync(P);
         if (P.h_flags[F_DONE]) break;
         if (launched >= maxit) break;   // defensive: device counter stops at maxit
         const int c = std::min(chunk, maxit - launched + 1);
         for (int i = 0; i < c; ++i) {
             apply_A<T>(P, a.p, static_cast<T*>(P.pcg.q), P.pcg.flags + F_DONE);
+            const int sl = prof_begin(P, sizeof(T) == 8 ? ST_PCG64 : ST_PCG32);
             launch_pcg<T>(1, P.ncomp, two, a, nb, s);
+            prof_end(P, sl);
         }
         launched += c;
         chunk = std::min(chunk * 2, 16);
     }
     d2h(P.h_scal + 4, P.pcg.scal, 4 * 8, s);
-    sync(s);
+    sync(P);
     out.iters = P.h_flags[F_ITER];
     out.status = P.h_flags[F_STATUS];
     out.rr = P.h_scal[4 + SC_RR];
@@ -628,8 +682,12 @@ static void solve(PlanHolder& P, const double* d, double tol, int maxit, int kin
         dd = P.dbuf;
     }
     // b = P^T N^-1 d (Eq. 7)
+    int sl = prof_begin(P, ST_TZ64);
     launch_toeplitz<double>(P, P.tz64, dd, nullptr, P.tod64, nullptr, s);
+    prof_end(P, sl);
+    sl = prof_begin(P, ST_SC64);
     launch_scatter<double>(P, P.tod64, P.b64, nullptr, s);
+    prof_end(P, sl);
     P.have_b = true;
     check_cuda(cudaEventRecord(P.ev1, s), "event");
     const bool m_dev = is_device_ptr(m);
@@ -700,7 +758,7 @@ static void solve(PlanHolder& P, const double* d, double tol, int maxit, int kin
     }
     if (!m_dev) d2h(m, xout, (size_t)P.n * 8, s);
     check_cuda(cudaEventRecord(P.ev2, s), "event");
-    sync(s);
+    sync(P);
     float ms = 0.f, ms_rhs = 0.f;
     check_cuda(cudaEventElapsedTime(&ms, P.ev0, P.ev2), "event time");
     check_cuda(cudaEventElapsedTime(&ms_rhs, P.ev0, P.ev1), "event time");
@@ -852,7 +910,30 @@ mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y) {
             apply_A<double>(*P, static_cast<const double*>(x), static_cast<double*>(y), nullptr);
         else
             apply_A<float>(*P, static_cast<const float*>(x), static_cast<float*>(y), nullptr);
-        sync(P->stream);
+        sync(*P);
+    });
+}
+
+mm_status mm_profile(mm_plan_t plan, int enable) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        sync(*P);
+        P->prof.on = enable != 0;
+        for (int i = 0; i < ST_COUNT; ++i) {
+            P->prof.ms[i] = 0.0;
+            P->prof.launches[i] = 0;
+        }
+    });
+}
+
+mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        sync(*P);
+        for (int i = 0; i < ST_COUNT; ++i) {
+            if (ms) ms[i] = P->prof.ms[i];
+            if (launches) launches[i] = P->prof.launches[i];
+        }
     });
 }
 
@@ -935,5 +1016,7 @@ const char* mm_last_error(mm_plan_t plan) {
 void mm_destroy(mm_plan_t plan) { destroy_plan(reinterpret_cast<PlanHolder*>(plan)); }
 
 const char* mm_version(void) { return "libmm 0.1 (sm_103a)"; }
+
+int64_t mm_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -39,6 +39,7 @@ void launch_lincomb(const TIN* V, int m, int64_t n, const double* C, int kk, dou
     if (g > 4096) g = 4096;
     lincomb_kernel<TIN><<<(int)g, th, 0, s>>>(V, m, n, C, kk, out);
     check_cuda(cudaGetLastError(), "lincomb launch");
+    note_launch();
 }
 template void launch_lincomb<double>(const double*, int, int64_t, const double*, int, double*, cudaStream_t);
 template void launch_lincomb<float>(const float*, int, int64_t, const double*, int, double*, cudaStream_t);
@@ -92,6 +93,7 @@ int launch_gram(const double* A, int ka, const double* B, int kb, int64_t n, dou
     chunk = (chunk + 31) / 32 * 32;
     gram_kernel<<<nblk, 256, 0, s>>>(A, ka, B, kb, n, chunk, part);
     check_cuda(cudaGetLastError(), "gram launch");
+    note_launch();
     return nblk;
 }
 

@@ -61,6 +61,20 @@ struct PcgDev {
     int maxhist = 0;
 };
 
+// Per-stage CUDA-event timers (enabled by mm_profile).
+enum { ST_TZ64 = 0, ST_TZ32 = 1, ST_SC64 = 2, ST_SC32 = 3, ST_PCG64 = 4, ST_PCG32 = 5, ST_COUNT = 8 };
+struct Prof {
+    bool on = false;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[ST_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t launches[ST_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
 struct Plan {
     // problem
     int64_t nt = 0;
@@ -112,9 +126,15 @@ struct Plan {
 
     CoarseDev coarse;
     PcgDev pcg;
+    Prof prof;
 
     std::string err;
 };
+
+// profiling helpers (api.cu): begin returns a slot (or -1 when off), end closes it
+int prof_begin(Plan& P, int stage);
+void prof_end(Plan& P, int slot);
+void prof_flush(Plan& P);   // after a stream synchronisation
 
 // error helpers ----------------------------------------------------------------------
 struct Error {
@@ -123,6 +143,7 @@ struct Error {
 };
 
 void check_cuda(cudaError_t e, const char* what);   // throws Error{MM_ERR_CUDA}
+void note_launch(int kernels = 1);                   // process-wide kernel launch counter
 void* dmalloc(size_t bytes);                         // throws Error{MM_ERR_OOM}
 void dfree(void* p);
 

@@ -344,6 +344,7 @@ static void coop(void (*kern)(PcgArgs<T>), const PcgArgs<T>& a, int nblocks, cud
     check_cuda(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblocks), dim3(PCG_THREADS), args,
                                            0, s),
                "cooperative PCG launch");
+    note_launch();
 }
 
 template <typename T>
@@ -400,6 +401,7 @@ void launch_dot64(const double* a, const double* b, int64_t n, double* part, dou
     dot_partial_kernel<double, double><<<g, 256, 0, s>>>(a, b, n, part);
     sum_kernel<<<1, 32, 0, s>>>(part, g, out);
     check_cuda(cudaGetLastError(), "dot launch");
+    note_launch(2);
 }
 
 __global__ void scale_to_f32_kernel(const double* a, const double* scale, float* b, int64_t n) {
@@ -412,6 +414,7 @@ __global__ void scale_to_f32_kernel(const double* a, const double* scale, float*
 void launch_scale_to_f32(const double* a, const double* sq, float* b, int64_t n, cudaStream_t s) {
     scale_to_f32_kernel<<<DOT_BLOCKS, 256, 0, s>>>(a, sq, b, n);
     check_cuda(cudaGetLastError(), "scale launch");
+    note_launch();
 }
 
 __global__ void axpy_f32_kernel(double* x, const float* d, const double* sq, int64_t n) {
@@ -424,6 +427,7 @@ __global__ void axpy_f32_kernel(double* x, const float* d, const double* sq, int
 void launch_axpy_f32(double* x, const float* d, const double* sq, int64_t n, cudaStream_t s) {
     axpy_f32_kernel<<<DOT_BLOCKS, 256, 0, s>>>(x, d, sq, n);
     check_cuda(cudaGetLastError(), "axpy launch");
+    note_launch();
 }
 
 __global__ void sub_kernel(const double* b, const double* ax, double* r, int64_t n) {
@@ -434,6 +438,7 @@ __global__ void sub_kernel(const double* b, const double* ax, double* r, int64_t
 void launch_sub(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s) {
     sub_kernel<<<DOT_BLOCKS, 256, 0, s>>>(b, ax, r, n);
     check_cuda(cudaGetLastError(), "sub launch");
+    note_launch();
 }
 
 }  // namespace mm

@@ -66,6 +66,7 @@ void launch_gather(const Plan& P, const T* x, T* y, cudaStream_t s) {
     else
         gather_kernel<T, 3><<<g, th, 0, s>>>(P.pixc, weights_time<T>(P), x, y, P.nt);
     check_cuda(cudaGetLastError(), "gather launch");
+    note_launch();
 }
 template void launch_gather<double>(const Plan&, const double*, double*, cudaStream_t);
 template void launch_gather<float>(const Plan&, const float*, float*, cudaStream_t);
@@ -128,6 +129,7 @@ void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream
         scatter_kernel<T, 3><<<g, th, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z, w,
                                                P.npix_obs, done);
     check_cuda(cudaGetLastError(), "scatter launch");
+    note_launch();
 }
 template void launch_scatter<double>(const Plan&, const double*, double*, const int*, cudaStream_t);
 template void launch_scatter<float>(const Plan&, const float*, float*, const int*, cudaStream_t);
@@ -208,6 +210,7 @@ void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s) {
         bd_build_kernel<3><<<g, th, 0, s>>>(P.csr_off, P.tsort, P.wsort64, P.ioff, P.ipsd, P.t0, P.K,
                                              P.npix_obs, bd64, bd32);
     check_cuda(cudaGetLastError(), "bd build launch");
+    note_launch();
 }
 
 // ------------------------------------------------------------------------ M_BD apply
@@ -244,6 +247,7 @@ void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s) {
     else
         bd_apply_kernel<T, 3><<<g, th, 0, s>>>(bd_of<T>(P), r, z, P.npix_obs);
     check_cuda(cudaGetLastError(), "bd apply launch");
+    note_launch();
 }
 template void launch_bd_apply<double>(const Plan&, const double*, double*, cudaStream_t);
 template void launch_bd_apply<float>(const Plan&, const float*, float*, cudaStream_t);
@@ -259,6 +263,7 @@ void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_
     if (n == 0) return;
     convert_kernel<<<grid_for(n, 256, 160), 256, 0, s>>>(a, b, n);
     check_cuda(cudaGetLastError(), "convert launch");
+    note_launch();
 }
 
 }  // namespace mm

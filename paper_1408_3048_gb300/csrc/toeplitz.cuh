@@ -311,6 +311,7 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     }
     kern<<<ntiles, NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz kernel launch");
+    note_launch();
 }
 
 template <typename T, int LOGN>

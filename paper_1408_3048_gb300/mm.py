@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 # every symbol include/mm.h declares (checked by the CPU tests)
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
-           "mm_coarse_vectors", "mm_solve", "mm_last_error", "mm_destroy", "mm_version"]
+           "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
+           "mm_version", "mm_launch_count"]
 
 
 class mm_psd(ctypes.Structure):
@@ -79,9 +80,12 @@ _SIGS = {
     "mm_coarse_info": (I32, [P, P, P]),
     "mm_coarse_vectors": (I32, [P, P]),
     "mm_solve": (I32, [P, P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(mm_stats)]),
+    "mm_profile": (I32, [P, ctypes.c_int]),
+    "mm_profile_read": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
     "mm_destroy": (None, [P]),
     "mm_version": (ctypes.c_char_p, []),
+    "mm_launch_count": (I64, []),
 }
 
 
@@ -123,6 +127,10 @@ def _check(status, plan=None):
 # ---------------------------------------------------------------- C-named wrappers
 def mm_version():
     return lib().mm_version().decode()
+
+
+def mm_launch_count():
+    return int(lib().mm_launch_count())
 
 
 def mm_last_error(plan):
@@ -203,6 +211,17 @@ def mm_solve(plan, d, tol, maxit, kind, solver, m, raise_on_error=True):
     if raise_on_error:
         _check(status, plan)
     return status, st
+
+
+def mm_profile(plan, enable):
+    _check(lib().mm_profile(plan, int(enable)), plan)
+
+
+def mm_profile_read(plan):
+    ms = np.zeros(8, dtype=np.float64)
+    n = np.zeros(8, dtype=np.int64)
+    _check(lib().mm_profile_read(plan, ms.ctypes.data, n.ctypes.data), plan)
+    return ms, n
 
 
 def mm_destroy(plan):
@@ -311,6 +330,15 @@ class Plan:
         m = self._new(self.n, MM_FP64) if out is None else out
         status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
         return m, st.as_dict(), status
+
+    def profile(self, enable=True):
+        mm_profile(self.handle, enable)
+
+    def profile_read(self):
+        """{stage: (total ms, launches)} per kernel and precision."""
+        ms, n = mm_profile_read(self.handle)
+        names = ["toeplitz_f64", "toeplitz_f32", "scatter_f64", "scatter_f32", "pcg_f64", "pcg_f32"]
+        return {nm: (float(ms[i]), int(n[i])) for i, nm in enumerate(names)}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     with open(os.path.join(ROOT, "include", "mm.h")) as f:
         txt = f.read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\**\s+\**(mm_[a-z_A-Z0-9]+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(mm_[a-z_A-Z0-9]+)\s*\(", txt, re.M)))
 
 
 def test_header_declares_the_boundary():
