@@ -157,6 +157,22 @@ mm_status mm_scatter(mm_plan_t plan, int precision, const void* z, void* w);
 /* y = A x = P^T [N^-1 [P x]] (Eq. 5, 8).  x, y device [n] in `precision`. */
 mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y);
 
+/*
+ * y = A x exactly as mm_apply_A, but without allocating device memory during the call.
+ * The paper has no counterpart: this exists for callers that cannot allocate once they
+ * run -- e.g. code whose GPU memory is already reserved by a pool it does not own (a
+ * framework's caching allocator) or a latency-critical path where cudaMalloc could fail
+ * or stall.  The time-domain intermediate of A x is kept in one 32 MiB array compiled
+ * into the library (held on every device that loads it, until the process exits)
+ * instead of in the plan's buffer; so nt * (8 for MM_FP64, 4 for MM_FP32) must not
+ * exceed 32 MiB (nt <= 4194304 in FP64, 8388608 in FP32), else MM_ERR_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array: every call rewrites what it reads, but calls that overlap
+ * on the GPU (other streams, other host threads) race.  x, y device [n] in `precision`.
+ */
+mm_status mm_apply_A_static(mm_plan_t plan, int precision, const void* x, void* y);
+
 /* b = P^T N^-1 d (Eq. 7).  d device [nt] double, b device [n] double (FP64 arithmetic). */
 mm_status mm_rhs(mm_plan_t plan, const double* d, double* b);
 

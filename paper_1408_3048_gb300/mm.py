@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
-           "mm_version", "mm_launch_count"]
+           "mm_version", "mm_launch_count", "mm_apply_A_static"]
 
 
 class mm_psd(ctypes.Structure):
@@ -74,6 +74,7 @@ _SIGS = {
     "mm_apply_ninv": (I32, [P, ctypes.c_int, P, P]),
     "mm_scatter": (I32, [P, ctypes.c_int, P, P]),
     "mm_apply_A": (I32, [P, ctypes.c_int, P, P]),
+    "mm_apply_A_static": (I32, [P, ctypes.c_int, P, P]),
     "mm_rhs": (I32, [P, P, P]),
     "mm_precond": (I32, [P, ctypes.c_int, ctypes.c_int, P, P]),
     "mm_build_coarse": (I32, [P, ctypes.c_int, ctypes.c_int, P, D, ctypes.c_int]),
@@ -179,6 +180,10 @@ def mm_scatter(plan, precision, z, w):
 
 def mm_apply_A(plan, precision, x, y):
     _check(lib().mm_apply_A(plan, precision, _ptr(x), _ptr(y)), plan)
+
+
+def mm_apply_A_static(plan, precision, x, y):
+    _check(lib().mm_apply_A_static(plan, precision, _ptr(x), _ptr(y)), plan)
 
 
 def mm_rhs(plan, d, b):
