@@ -235,6 +235,22 @@ mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int k
 mm_status mm_profile(mm_plan_t plan, int enable);
 mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
 
+/* Options of mm_solve_ex.  Zero-initialise and set what you need; 0 selects the default. */
+typedef struct {
+    double tol;             /* relative residual target (required, >= 0)                  */
+    int32_t maxit;          /* total PCG iterations (required, >= 1)                      */
+    int32_t kind;           /* MM_PREC_BD or MM_PREC_TWOLEVEL                              */
+    int32_t solver;         /* MM_SOLVE_FP64 or MM_SOLVE_MIXED                             */
+    int32_t max_outer;      /* refinement steps (MIXED), default 20                        */
+    double inner_tol_min;   /* lower bound of the inner FP32 tolerance (MIXED), default 3e-7
+                               (FP32 PCG tracks the true residual down to ~2e-7 relative)    */
+    double first_inner_tol; /* inner tolerance of the first step (MIXED); default: the same
+                               rule as later steps, max(inner_tol_min, 0.5 tol ||b||/||r||) */
+} mm_solve_opts;
+
+/* mm_solve with explicit options (same semantics and errors). */
+mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts, double* m, mm_stats* st);
+
 /* Human-readable description of the last error on this plan (never NULL). */
 const char* mm_last_error(mm_plan_t plan);
 

@@ -127,6 +127,7 @@ static void free_coarse(CoarseDev& c) {
     dfree(c.Z32);
     dfree(c.AZ32);
     dfree(c.L);
+    dfree(c.Ld);
     c = CoarseDev{};
 }
 
@@ -463,6 +464,7 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
             a.AZ = reinterpret_cast<const T*>(P.coarse.AZ32);
         }
         a.L = P.coarse.L;
+        a.Ld = P.coarse.Ld;
     }
     a.partial = g.partial;
     a.scal = g.scal;
@@ -651,6 +653,10 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
         if (!cholesky_lower(E, kcur, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
         cd.L = dalloc<double>(Lf.size());
         h2d(cd.L, Lf.data(), Lf.size() * 8, s);
+        std::vector<double> Ld((size_t)kcur);
+        for (int j = 0; j < kcur; ++j) Ld[(size_t)j] = 1.0 / Lf[(size_t)j * kcur + j];
+        cd.Ld = dalloc<double>(Ld.size());
+        h2d(cd.Ld, Ld.data(), Ld.size() * 8, s);
         cd.Z32 = dalloc<float>((size_t)kcur * P.n);
         cd.AZ32 = dalloc<float>((size_t)kcur * P.n);
         launch_convert_f64_to_f32(cd.Z64, cd.Z32, (int64_t)kcur * P.n, s);
@@ -666,9 +672,14 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
 }
 
 // -------------------------------------------------------------------------- solve
-static void solve(PlanHolder& P, const double* d, double tol, int maxit, int kind, int solver, double* m,
-                  mm_stats* st) {
+static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, double* m, mm_stats* st) {
     cudaStream_t s = P.stream;
+    const double tol = so.tol;
+    const int maxit = so.maxit;
+    const int kind = so.kind;
+    const int solver = so.solver;
+    const int max_outer = so.max_outer > 0 ? so.max_outer : 20;
+    const double inner_min = so.inner_tol_min > 0.0 ? so.inner_tol_min : 3e-7;
     if (!(tol >= 0.0) || maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
     if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
     if (solver != MM_SOLVE_FP64 && solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
@@ -725,12 +736,13 @@ static void solve(PlanHolder& P, const double* d, double tol, int maxit, int kin
                 status = MM_OK;
                 break;
             }
-            if (total >= maxit || outer >= 20) break;
+            if (total >= maxit || outer >= max_outer) break;
             // r32 = r / ||r||  (the norm^2 stays in device memory for the update)
             launch_dot64(P.r64, P.r64, P.n, P.d_dot, P.d_dot + DOT_BLOCKS, s);
             launch_scale_to_f32(P.r64, P.d_dot + DOT_BLOCKS, static_cast<float*>(P.pcg.r), P.n, s);
             double tol_in = 0.5 * tol * bn / std::sqrt(rr);
-            tol_in = std::min(0.5, std::max(tol_in, 1e-5));
+            tol_in = std::min(0.5, std::max(tol_in, inner_min));
+            if (outer == 0 && so.first_inner_tol > 0.0) tol_in = so.first_inner_tol;
             const PcgOutcome o = run_pcg<float>(P, two, tol_in, maxit - total, nullptr, 0);
             if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
                 status = o.status;
@@ -1001,7 +1013,20 @@ mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int k
     return guarded(plan, [&] {
         PlanHolder* P = get(plan);
         if (!d || !m) throw Error{MM_ERR_ARG, "null vector"};
-        solve(*P, d, tol, maxit, kind, solver, m, st);
+        mm_solve_opts o{};
+        o.tol = tol;
+        o.maxit = maxit;
+        o.kind = kind;
+        o.solver = solver;
+        solve(*P, d, o, m, st);
+    });
+}
+
+mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts, double* m, mm_stats* st) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!d || !m || !opts) throw Error{MM_ERR_ARG, "null argument"};
+        solve(*P, d, *opts, m, st);
     });
 }
 

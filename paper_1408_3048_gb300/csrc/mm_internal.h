@@ -38,6 +38,7 @@ struct CoarseDev {
     float* Z32 = nullptr;        // [k][n]
     float* AZ32 = nullptr;       // [k][n]
     double* L = nullptr;         // [k][k] lower Cholesky factor of E (row-major)
+    double* Ld = nullptr;        // [k] reciprocal diagonal of L
     std::vector<double> ritz;    // k smallest Ritz values
 };
 

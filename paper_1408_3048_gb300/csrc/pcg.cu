@@ -68,12 +68,13 @@ __device__ double block_sum(double v, double* sh) {
     return s;
 }
 
-// Sum of slot `slot` over all block partials, in block order.
-__device__ __forceinline__ double sum_partials(const double* part, int slot) {
+// Sum of slot `slot` over all block partials: every thread reads at most a few partials
+// (L2 loads, bypassing L1) and the block reduces them in a fixed order, so every block
+// obtains the same value.  Must be called by all threads of the block.
+__device__ double grid_total(const double* part, int slot, double* sh) {
     double s = 0.0;
-    const volatile double* p = part;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)b * PSTRIDE + slot];
-    return s;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(part + (size_t)b * PSTRIDE + slot);
+    return block_sum(s, sh);
 }
 
 // Pixel range of this block.
@@ -84,32 +85,46 @@ __device__ __forceinline__ void block_pixels(int npix, int& lo, int& hi) {
     if (lo > hi) lo = hi;
 }
 
-// Z^T r over this block's elements -> part[blk][S_COARSE + j]
+// Z^T r over this block's elements -> part[blk][S_COARSE + j] (a preconditioner input,
+// not a CG dot product: lanes accumulate in T, the reductions above them in FP64)
 template <typename T>
 __device__ void coarse_partials(const PcgArgs<T>& a, const T* r, int64_t e0, int64_t e1) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < a.k; j += nw) {
         const T* zj = a.Z + (size_t)j * a.n;
-        double s = 0.0;
-        for (int64_t i = e0 + l; i < e1; i += 32) s += (double)zj[i] * (double)r[i];
+        // per-lane partial in T (a few dozen terms: for T = float this keeps the FP64 pipe,
+        // which GB300 runs at 1/64 of the FP32 rate, for the cross-lane / block sums)
+        T sl = (T)0;
+#pragma unroll 8
+        for (int64_t i = e0 + l; i < e1; i += 32) sl += __ldg(zj + i) * r[i];
+        double s = (double)sl;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (l == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_COARSE + j] = s;
     }
 }
 
-// v = E^-1 u with E = L L^T (L row-major k x k), by warp 0; u from the partials.
+// v = E^-1 u with E = L L^T (L row-major k x k, reciprocal diagonal in Ld), u = Z^T r
+// from the block partials.  Warps reduce the k coarse slots (lanes over blocks, fixed
+// order), then warp 0 runs the two triangular solves with lanes owning rows l, l + 32.
 template <typename T>
 __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = w; j < a.k; j += nw) {
+        double s = 0.0;
+        for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(a.partial + (size_t)b * PSTRIDE + S_COARSE + j);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (l == 0) v_sh[j] = s;
+    }
+    __syncthreads();
     if (threadIdx.x < 32) {
-        const int l = threadIdx.x;
-        double u0 = 0.0, u1 = 0.0;   // rows l and l + 32
-        if (l < a.k) u0 = sum_partials(a.partial, S_COARSE + l);
-        if (l + 32 < a.k) u1 = sum_partials(a.partial, S_COARSE + l + 32);
+        double u0 = l < a.k ? v_sh[l] : 0.0;
+        double u1 = l + 32 < a.k ? v_sh[l + 32] : 0.0;
         // forward: L y = u
         for (int j = 0; j < a.k; ++j) {
             const double uj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
-            const double yj = uj / a.L[(size_t)j * a.k + j];
+            const double yj = uj * a.Ld[j];
             if (l == (j & 31)) {
                 if (j < 32) u0 = yj; else u1 = yj;
             }
@@ -119,13 +134,14 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
         // backward: L^T v = y
         for (int j = a.k - 1; j >= 0; --j) {
             const double yj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
-            const double vj = yj / a.L[(size_t)j * a.k + j];
+            const double vj = yj * a.Ld[j];
             if (l == (j & 31)) {
                 if (j < 32) u0 = vj; else u1 = vj;
             }
             if (l < j && l < a.k) u0 -= a.L[(size_t)j * a.k + l] * vj;
             if (l + 32 < j && l + 32 < a.k) u1 -= a.L[(size_t)j * a.k + l + 32] * vj;
         }
+        __syncwarp();
         if (l < a.k) v_sh[l] = u0;
         if (l + 32 < a.k) v_sh[l + 32] = u1;
     }
@@ -145,14 +161,15 @@ __device__ double apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0,
             zc[c] = (T)0;
         }
         if constexpr (TWO) {
+#pragma unroll 8
             for (int j = 0; j < a.k; ++j) {
                 const T vj = (T)v_sh[j];
                 const T* az = a.AZ + (size_t)j * a.n + e;
                 const T* zz = a.Z + (size_t)j * a.n + e;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    t[c] -= az[c] * vj;
-                    zc[c] += zz[c] * vj;
+                    t[c] -= __ldg(az + c) * vj;
+                    zc[c] += __ldg(zz + c) * vj;
                 }
             }
         }
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = bb;
     if constexpr (TWO) coarse_partials(a, a.r, e0, e1);
     if (!grid_sync(a.bar, a.flags)) return;
-    const double bbt = sum_partials(a.partial, S_RR);
+    const double bbt = grid_total(a.partial, S_RR, sh);
     if constexpr (TWO) coarse_solve(a, v_sh);
     double rz = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
     __syncthreads();
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     rz = block_sum(rz, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags)) return;
-    const double rho = sum_partials(a.partial, S_RZ);
+    const double rho = grid_total(a.partial, S_RZ, sh);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.scal[SC_RHO] = rho;
         a.scal[SC_BB] = bbt;
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     pq = block_sum(pq, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_PQ] = pq;
     if (!grid_sync(a.bar, a.flags)) return;
-    const double pqt = sum_partials(a.partial, S_PQ);
+    const double pqt = grid_total(a.partial, S_PQ, sh);
     const double rho = a.scal[SC_RHO];
     if (!(pqt > 0.0) || !isfinite(pqt)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -265,7 +282,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
         coarse_partials(a, a.r, e0, e1);
     }
     if (!grid_sync(a.bar, a.flags)) return;
-    const double rrt = sum_partials(a.partial, S_RR);
+    const double rrt = grid_total(a.partial, S_RR, sh);
     const int it = a.flags[F_ITER] + 1;     // every block reads the same value here
     bool stop = false;
     int status = MM_OK;
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     rz = block_sum(rz, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags)) return;
-    const double rzt = sum_partials(a.partial, S_RZ);
+    const double rzt = grid_total(a.partial, S_RZ, sh);
     const double beta = rzt / rho;
     const T be = (T)beta;
     T* zs = (a.zstore != nullptr && it < a.maxstore) ? a.zstore + (size_t)it * a.n : nullptr;
@@ -366,14 +383,15 @@ void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks
 template void launch_pcg<double>(int, int, bool, const PcgArgs<double>&, int, cudaStream_t);
 template void launch_pcg<float>(int, int, bool, const PcgArgs<float>&, int, cudaStream_t);
 
+// One block per SM: enough threads for the map-sized vectors, and few block partials
+// for the reductions.
 int pcg_max_blocks(int num_sms) {
     int per_sm = 0;
     check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_iter_kernel<double, 3, true>,
                                                              PCG_THREADS, 0),
                "occupancy");
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;
-    return per_sm * num_sms;
+    if (per_sm < 1) throw Error{MM_ERR_CUDA, "PCG kernel does not fit on an SM"};
+    return num_sms;
 }
 
 // ------------------------------------------------------------------ vector helpers

@@ -5,7 +5,7 @@
 
 namespace mm {
 
-constexpr int PCG_THREADS = 256;
+constexpr int PCG_THREADS = 512;
 constexpr int KMAX = 64;          // largest coarse dimension
 constexpr int DOT_BLOCKS = 304;   // blocks of the stand-alone dot / vector kernels
 
@@ -33,6 +33,7 @@ struct PcgArgs {
     const T* Z;          // [k][n]
     const T* AZ;         // [k][n]
     const double* L;     // Cholesky factor of E, row-major [k][k]
+    const double* Ld;    // 1 / L_jj, [k]
     double* partial;     // [grid][PSTRIDE]
     double* scal;
     int* flags;

@@ -139,6 +139,46 @@ template <> struct PadLog<float> { static constexpr int v = 4; };    // 16 x 8 B
 template <typename T>
 __device__ __forceinline__ int pad(int i) { return i + (i >> PadLog<T>::v); }
 
+// v[r] *= W_{Ns R}^{r k}, r = 1..R-1 (W_M = exp(-2 pi i / M)).
+// FP64: every power read from the quarter-wave table (the FP64 pipe is the bottleneck of
+// the FP64 kernel, table reads go to the otherwise idle load/store unit).
+// FP32: one sincospif per butterfly and the powers by a multiplication tree of depth <= 3
+// (the FP32 kernel is shared-memory bound, and power-of-two strided table reads conflict).
+template <typename T, int LOGN, int LOGR, int LOGNS>
+__device__ __forceinline__ void pass_twiddles(typename Cx<T>::type* v, int k, const T* tab) {
+    constexpr int R = 1 << LOGR;
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            const int m = (r * k) << (LOGN + 1 - LOGNS - LOGR);
+            T c, s;
+            twiddle<T, LOGN - 1>(tab, m, c, s);
+            v[r] = cmul<T>(v[r], c, s);
+        }
+    } else {
+        float sn, cs;
+        // angle 2 pi k / (Ns R) = pi * x, x = 2k / 2^(LOGNS + LOGR) exactly representable
+        sincospif((float)(2 * k) * (1.0f / (float)(1 << (LOGNS + LOGR))), &sn, &cs);
+        float2 w[8];
+        w[1] = make_float2(cs, sn);   // (cos, sin) of theta; multiply uses c - i s
+        auto mulw = [](float2 a, float2 b) {   // (cos, sin) of the sum of the two angles
+            return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+        };
+        if constexpr (R >= 4) {
+            w[2] = mulw(w[1], w[1]);
+            w[3] = mulw(w[1], w[2]);
+        }
+        if constexpr (R >= 8) {
+            w[4] = mulw(w[2], w[2]);
+            w[5] = mulw(w[2], w[3]);
+            w[6] = mulw(w[3], w[3]);
+            w[7] = mulw(w[3], w[4]);
+        }
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul<T>(v[r], w[r].x, w[r].y);
+    }
+}
+
 // One in-place Stockham pass of radix R on N = 2^LOGN points (Ns = 2^LOGNS).
 template <typename T, int LOGN, int NT, int LOGR, int LOGNS>
 __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) {
@@ -162,16 +202,7 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) 
     for (int b = 0; b < BPT; ++b) {
         const int j = tid + b * NT;
         const int k = j & (Ns - 1);
-        if (LOGNS > 0) {
-            // v[r] *= W_{Ns R}^{r k} = W_B^{r k (B / (Ns R))}, B = 2N
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const int m = (r * k) << (LOGN + 1 - LOGNS - LOGR);
-                T c, s;
-                twiddle<T, LOGN - 1>(tab, m, c, s);
-                v[b][r] = cmul<T>(v[b][r], c, s);
-            }
-        }
+        if (LOGNS > 0) pass_twiddles<T, LOGN, LOGR, LOGNS>(v[b], k, tab);
         dft<T, R>(v[b]);
         const int idx = ((j - k) << LOGR) + k;
 #pragma unroll
@@ -191,23 +222,6 @@ __device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const T* tab) {
 }
 
 // MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map.
-template <typename T, int MODE>
-__device__ __forceinline__ T load_sample(const TzArgs<T>& A, int64_t t) {
-    if constexpr (MODE == 0) {
-        return A.y[t];
-    } else {
-        const int q = __ldg(A.pixc + t);
-        if (q < 0) return (T)0;
-        if constexpr (MODE == 1) {
-            return __ldg(A.x + q);
-        } else {
-            const typename Cx<T>::type w = A.w[t];
-            const T* xq = A.x + 3 * (int64_t)q;
-            return __ldg(xq) + w.x * __ldg(xq + 1) + w.y * __ldg(xq + 2);
-        }
-    }
-}
-
 template <typename T, int LOGN, int NT, int MODE>
 __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     using C2 = typename Cx<T>::type;
@@ -221,12 +235,63 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const int tid = threadIdx.x;
     for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     const int64_t ws = tile.out0 - A.lambda;
-    for (int m = tid; m < N; m += NT) {
-        const int64_t t0 = ws + 2 * m;
-        C2 u;
-        u.x = (t0 >= tile.ibeg && t0 < tile.iend) ? load_sample<T, MODE>(A, t0) : (T)0;
-        u.y = (t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend) ? load_sample<T, MODE>(A, t0 + 1) : (T)0;
-        a[pad<T>(m)] = u;
+    // Load the block in batches: all pointing / weight loads of a batch are issued before
+    // the dependent map gathers, so each thread keeps UNR pairs of samples in flight.
+    constexpr int PER = N / NT;                 // complex points per thread
+    constexpr int UMAX = MODE == 3 ? 4 : 8;
+    constexpr int UNR = PER < UMAX ? PER : UMAX;
+#pragma unroll 1
+    for (int base = 0; base < PER; base += UNR) {
+        T v0[UNR], v1[UNR];
+        if constexpr (MODE == 0) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int64_t t0 = ws + 2 * (int64_t)((base + u) * NT + tid);
+                v0[u] = (t0 >= tile.ibeg && t0 < tile.iend) ? A.y[t0] : (T)0;
+                v1[u] = (t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend) ? A.y[t0 + 1] : (T)0;
+            }
+        } else {
+            int q0[UNR], q1[UNR];
+            typename Cx<T>::type w0[UNR], w1[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int64_t t0 = ws + 2 * (int64_t)((base + u) * NT + tid);
+                const bool ok0 = t0 >= tile.ibeg && t0 < tile.iend;
+                const bool ok1 = t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend;
+                q0[u] = ok0 ? __ldg(A.pixc + t0) : -1;
+                q1[u] = ok1 ? __ldg(A.pixc + t0 + 1) : -1;
+                if constexpr (MODE == 3) {
+                    if (ok0) w0[u] = A.w[t0];
+                    if (ok1) w1[u] = A.w[t0 + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if constexpr (MODE == 1) {
+                    v0[u] = q0[u] >= 0 ? __ldg(A.x + q0[u]) : (T)0;
+                    v1[u] = q1[u] >= 0 ? __ldg(A.x + q1[u]) : (T)0;
+                } else {
+                    T r0 = (T)0, r1 = (T)0;
+                    if (q0[u] >= 0) {
+                        const T* xq = A.x + 3 * (int64_t)q0[u];
+                        r0 = __ldg(xq) + w0[u].x * __ldg(xq + 1) + w0[u].y * __ldg(xq + 2);
+                    }
+                    if (q1[u] >= 0) {
+                        const T* xq = A.x + 3 * (int64_t)q1[u];
+                        r1 = __ldg(xq) + w1[u].x * __ldg(xq + 1) + w1[u].y * __ldg(xq + 2);
+                    }
+                    v0[u] = r0;
+                    v1[u] = r1;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            C2 c;
+            c.x = v0[u];
+            c.y = v1[u];
+            a[pad<T>((base + u) * NT + tid)] = c;
+        }
     }
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, tab);
@@ -287,9 +352,12 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     }
 }
 
+// Threads per CTA: N/8 (one radix-8 butterfly per thread and pass), capped at
+// 512 (at 1024 threads the 64-register limit spills the butterflies), at least 32.
 template <typename T, int LOGN>
 constexpr int tz_threads() {
-    return (1 << LOGN) / 8 >= 512 ? 512 : ((1 << LOGN) / 8 < 32 ? 32 : (1 << LOGN) / 8);
+    constexpr int cap = 512;
+    return (1 << LOGN) / 8 >= cap ? cap : ((1 << LOGN) / 8 < 32 ? 32 : (1 << LOGN) / 8);
 }
 
 template <typename T>

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
-           "mm_version", "mm_launch_count", "mm_apply_A_static"]
+           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex"]
 
 
 class mm_psd(ctypes.Structure):
@@ -50,6 +50,12 @@ class mm_stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class mm_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("solver", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol_min", ctypes.c_double),
+                ("first_inner_tol", ctypes.c_double)]
 
 
 class MMError(RuntimeError):
@@ -81,6 +87,7 @@ _SIGS = {
     "mm_coarse_info": (I32, [P, P, P]),
     "mm_coarse_vectors": (I32, [P, P]),
     "mm_solve": (I32, [P, P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(mm_stats)]),
+    "mm_solve_ex": (I32, [P, P, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
@@ -229,6 +236,14 @@ def mm_profile_read(plan):
     return ms, n
 
 
+def mm_solve_ex(plan, d, opts, m, raise_on_error=True):
+    st = mm_stats()
+    status = lib().mm_solve_ex(plan, _ptr(d), ctypes.byref(opts), _ptr(m), ctypes.byref(st))
+    if raise_on_error:
+        _check(status, plan)
+    return status, st
+
+
 def mm_destroy(plan):
     lib().mm_destroy(plan)
 
@@ -331,9 +346,17 @@ class Plan:
         return Z.reshape(k, self.n).T.copy()
 
     def solve(self, d, tol=1e-6, maxit=1000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, out=None,
-              raise_on_error=True):
+              raise_on_error=True, **extra):
+        """extra: max_outer, inner_tol_min, first_inner_tol (mm_solve_opts)."""
         m = self._new(self.n, MM_FP64) if out is None else out
-        status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
+        if extra:
+            o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver,
+                              max_outer=int(extra.get("max_outer", 0)),
+                              inner_tol_min=float(extra.get("inner_tol_min", 0.0)),
+                              first_inner_tol=float(extra.get("first_inner_tol", 0.0)))
+            status, st = mm_solve_ex(self.handle, d, o, m, raise_on_error)
+        else:
+            status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
         return m, st.as_dict(), status
 
     def profile(self, enable=True):
