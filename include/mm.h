@@ -251,6 +251,23 @@ typedef struct {
 /* mm_solve with explicit options (same semantics and errors). */
 mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts, double* m, mm_stats* st);
 
+/*
+ * Gradients of a loss L(m) of the GLS map m = A^-1 P^T N^-1 d (Eq. 3, 5, 7), given
+ * g = dL/dm at the solution m of the data d.  The paper does not differentiate Eq. 3;
+ * with A symmetric one more PCG solve gives them:
+ *   mu = A^-1 g                                     (adjoint solve, `opts` as mm_solve_ex)
+ *   dL/dd = N^-1 P mu                               (dL_dd: host or device double[nt])
+ *   dL/dtheta_pc = (P mu)^T (dN^-1/dtheta_pc) (d - P m)   (dL_dpsd: host double[npsd][3],
+ *                                                    columns sigma, fknee, alpha)
+ * dN^-1/dtheta is block Toeplitz with the derivative rows: the row transform of mm_plan
+ * applied to d(1/S_j)/dtheta (analytic) times the window; the products u^T T v use the
+ * same overlap-save kernel.  d, m, g: host or device, double.  Either output may be NULL.
+ * The PSD gradient needs fknee > 0 for every PSD (MM_ERR_ARG otherwise).  All FP64
+ * except the adjoint solve, which follows opts->solver.  Krylov vectors are not kept.
+ */
+mm_status mm_grad(mm_plan_t plan, const double* d, const double* m, const double* g, double* dL_dd,
+                  double* dL_dpsd, const mm_solve_opts* opts, mm_stats* st);
+
 /* Human-readable description of the last error on this plan (never NULL). */
 const char* mm_last_error(mm_plan_t plan);
 

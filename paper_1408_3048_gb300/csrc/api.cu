@@ -105,6 +105,10 @@ void prof_flush(Plan& P) {
 
 // ----------------------------------------------------------------------------- plan
 struct PlanHolder : Plan {
+    std::vector<mm_psd> h_psd;
+    double* grad_H = nullptr;   // [3][npsd][N+1] derivative spectra (FP64 block)
+    double* grad_u = nullptr;   // [nt] P mu
+    double* grad_part = nullptr;  // [K]
     int* h_flags = nullptr;     // pinned
     double* h_scal = nullptr;   // pinned
     double* d_dot = nullptr;    // [DOT_BLOCKS + 2]
@@ -136,7 +140,8 @@ static void destroy_plan(PlanHolder* P) {
     for (void* p : {(void*)P->pixc, (void*)P->w64, (void*)P->w32, (void*)P->csr_off, (void*)P->tsort,
                     (void*)P->wsort64, (void*)P->wsort32, (void*)P->ioff, (void*)P->ipsd, (void*)P->t0,
                     (void*)P->bd64, (void*)P->bd32, (void*)P->tod64, (void*)P->tod32, (void*)P->dbuf,
-                    (void*)P->b64, (void*)P->d_dot, (void*)P->x64, (void*)P->r64, (void*)P->ax64})
+                    (void*)P->b64, (void*)P->d_dot, (void*)P->x64, (void*)P->r64, (void*)P->ax64,
+                    (void*)P->grad_H, (void*)P->grad_u, (void*)P->grad_part})
         dfree(p);
     free_tz(P->tz64);
     free_tz(P->tz32);
@@ -248,6 +253,7 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     P.rcond_min = o->rcond_min > 0.0 ? o->rcond_min : 1e-6;
     P.stream = static_cast<cudaStream_t>(o->stream);
     P.h_ioff.assign(ioff, ioff + K + 1);
+    P.h_psd.assign(psd, psd + npsd);
     P.h_ipsd.assign(ipsd, ipsd + K);
     if (P.h_ioff[0] != 0 || P.h_ioff[(size_t)K] != nt) throw Error{MM_ERR_ARG, "interval offsets must span [0, nt)"};
     int64_t minlen = nt, maxlen = 0;
@@ -672,19 +678,98 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
 }
 
 // -------------------------------------------------------------------------- solve
-static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, double* m, mm_stats* st) {
+static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
+    if (!(so.tol >= 0.0) || so.maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
+    if (so.kind != MM_PREC_BD && so.kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
+    if (so.solver != MM_SOLVE_FP64 && so.solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
+    if (so.kind == MM_PREC_TWOLEVEL && P.coarse.k == 0)
+        throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
+}
+
+// Solve A x = b for the b in P.b64 into xout (device); fills the iteration part of stats
+// and returns the status.
+static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm_stats& stats) {
     cudaStream_t s = P.stream;
     const double tol = so.tol;
     const int maxit = so.maxit;
-    const int kind = so.kind;
-    const int solver = so.solver;
+    const bool two = so.kind == MM_PREC_TWOLEVEL;
     const int max_outer = so.max_outer > 0 ? so.max_outer : 20;
     const double inner_min = so.inner_tol_min > 0.0 ? so.inner_tol_min : 3e-7;
-    if (!(tol >= 0.0) || maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
-    if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
-    if (solver != MM_SOLVE_FP64 && solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
-    const bool two = kind == MM_PREC_TWOLEVEL;
-    if (two && P.coarse.k == 0) throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
+    int status = MM_OK;
+    const double bb = dot64(P, P.b64, P.b64);
+    const double bn = std::sqrt(bb);
+    if (so.solver == MM_SOLVE_FP64) {
+        check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+        const PcgOutcome o = run_pcg<double>(P, two, tol, maxit, nullptr, 0);
+        if (o.status != MM_OK) status = o.status;
+        check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
+        stats.iters = o.iters;
+        stats.outer = 1;
+        stats.rel_resid_rec = bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
+        // true residual of the returned map
+        apply_A<double>(P, xout, P.ax64, nullptr);
+        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+        const double rr = dot64(P, P.r64, P.r64);
+        stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        stats.fp64_products = 1;
+        stats.converged = status == MM_OK;
+        return status;
+    }
+    // iterative refinement: FP64 residual, FP32 inner PCG on the scaled residual
+    check_cuda(cudaMemsetAsync(xout, 0, (size_t)P.n * 8, s), "memset x");
+    check_cuda(cudaMemcpyAsync(P.r64, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+    double rr = bb;
+    int total = 0;
+    int outer = 0;
+    int fp64 = 0;
+    double last_rec = 1.0;
+    status = MM_ERR_NOT_CONVERGED;
+    while (true) {
+        if (std::sqrt(rr) <= tol * bn || bb == 0.0) {
+            status = MM_OK;
+            break;
+        }
+        if (total >= maxit || outer >= max_outer) break;
+        // r32 = r / ||r||  (the norm^2 stays in device memory for the update)
+        launch_dot64(P.r64, P.r64, P.n, P.d_dot, P.d_dot + DOT_BLOCKS, s);
+        launch_scale_to_f32(P.r64, P.d_dot + DOT_BLOCKS, static_cast<float*>(P.pcg.r), P.n, s);
+        double tol_in = 0.5 * tol * bn / std::sqrt(rr);
+        tol_in = std::min(0.5, std::max(tol_in, inner_min));
+        if (outer == 0 && so.first_inner_tol > 0.0) tol_in = so.first_inner_tol;
+        const PcgOutcome o = run_pcg<float>(P, two, tol_in, maxit - total, nullptr, 0);
+        if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
+            status = o.status;
+            break;
+        }
+        total += o.iters;
+        last_rec = o.bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
+        launch_axpy_f32(xout, static_cast<const float*>(P.pcg.x), P.d_dot + DOT_BLOCKS, P.n, s);
+        apply_A<double>(P, xout, P.ax64, nullptr);
+        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+        ++fp64;
+        rr = dot64(P, P.r64, P.r64);
+        ++outer;
+        if (!std::isfinite(rr)) {
+            status = MM_ERR_NUMERIC;
+            break;
+        }
+    }
+    stats.iters = total;
+    stats.outer = outer;
+    stats.fp64_products = fp64;
+    stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+    stats.rel_resid_rec = last_rec;
+    stats.converged = status == MM_OK;
+    return status;
+}
+
+static const char* status_text(int status) {
+    return status == MM_ERR_NOT_CONVERGED ? "maxit reached before tol" : "solve failed";
+}
+
+static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, double* m, mm_stats* st) {
+    cudaStream_t s = P.stream;
+    check_solve_opts(P, so);
     mm_stats stats{};
     check_cuda(cudaEventRecord(P.ev0, s), "event");
     const double* dd = d;
@@ -703,71 +788,7 @@ static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, doubl
     check_cuda(cudaEventRecord(P.ev1, s), "event");
     const bool m_dev = is_device_ptr(m);
     double* xout = m_dev ? m : P.x64;
-    int status = MM_OK;
-    const double bb = dot64(P, P.b64, P.b64);
-    const double bn = std::sqrt(bb);
-    if (solver == MM_SOLVE_FP64) {
-        check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
-        const PcgOutcome o = run_pcg<double>(P, two, tol, maxit, nullptr, 0);
-        if (o.status != MM_OK) status = o.status;
-        check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
-        stats.iters = o.iters;
-        stats.outer = 1;
-        stats.rel_resid_rec = bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
-        // true residual of the returned map
-        apply_A<double>(P, xout, P.ax64, nullptr);
-        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
-        const double rr = dot64(P, P.r64, P.r64);
-        stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
-        stats.fp64_products = 1;
-        stats.converged = status == MM_OK;
-    } else {
-        // iterative refinement: FP64 residual, FP32 inner PCG on the scaled residual
-        check_cuda(cudaMemsetAsync(xout, 0, (size_t)P.n * 8, s), "memset x");
-        check_cuda(cudaMemcpyAsync(P.r64, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
-        double rr = bb;
-        int total = 0;
-        int outer = 0;
-        int fp64 = 0;
-        double last_rec = 1.0;
-        status = MM_ERR_NOT_CONVERGED;
-        while (true) {
-            if (std::sqrt(rr) <= tol * bn || bb == 0.0) {
-                status = MM_OK;
-                break;
-            }
-            if (total >= maxit || outer >= max_outer) break;
-            // r32 = r / ||r||  (the norm^2 stays in device memory for the update)
-            launch_dot64(P.r64, P.r64, P.n, P.d_dot, P.d_dot + DOT_BLOCKS, s);
-            launch_scale_to_f32(P.r64, P.d_dot + DOT_BLOCKS, static_cast<float*>(P.pcg.r), P.n, s);
-            double tol_in = 0.5 * tol * bn / std::sqrt(rr);
-            tol_in = std::min(0.5, std::max(tol_in, inner_min));
-            if (outer == 0 && so.first_inner_tol > 0.0) tol_in = so.first_inner_tol;
-            const PcgOutcome o = run_pcg<float>(P, two, tol_in, maxit - total, nullptr, 0);
-            if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
-                status = o.status;
-                break;
-            }
-            total += o.iters;
-            last_rec = o.bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
-            launch_axpy_f32(xout, static_cast<const float*>(P.pcg.x), P.d_dot + DOT_BLOCKS, P.n, s);
-            apply_A<double>(P, xout, P.ax64, nullptr);
-            launch_sub(P.b64, P.ax64, P.r64, P.n, s);
-            ++fp64;
-            rr = dot64(P, P.r64, P.r64);
-            ++outer;
-            if (!std::isfinite(rr)) {
-                status = MM_ERR_NUMERIC;
-                break;
-            }
-        }
-        stats.iters = total;
-        stats.outer = outer;
-        stats.fp64_products = fp64;
-        stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
-        stats.rel_resid_rec = last_rec;
-        stats.converged = status == MM_OK;
-    }
+    const int status = solve_from_b(P, so, xout, stats);
     if (!m_dev) d2h(m, xout, (size_t)P.n * 8, s);
     check_cuda(cudaEventRecord(P.ev2, s), "event");
     sync(P);
@@ -777,7 +798,93 @@ static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, doubl
     stats.ms_total = ms;
     stats.ms_rhs = ms_rhs;
     if (st != nullptr) *st = stats;
-    if (status != MM_OK) throw Error{(mm_status)status, status == MM_ERR_NOT_CONVERGED ? "maxit reached before tol" : "solve failed"};
+    if (status != MM_OK) throw Error{(mm_status)status, status_text(status)};
+}
+
+// ----------------------------------------------------------------------- gradient
+// Derivative spectra of the Toeplitz rows, built on the first gradient call.
+static void ensure_grad(PlanHolder& P) {
+    if (P.grad_H != nullptr) return;
+    const int64_t N = int64_t(1) << P.tz64.logn;
+    std::vector<double> H((size_t)3 * P.npsd * (N + 1));
+    for (int p = 0; p < P.npsd; ++p) {
+        if (!(P.h_psd[(size_t)p].fknee > 0.0)) throw Error{MM_ERR_ARG, "the PSD gradient needs fknee > 0"};
+        const auto D = toeplitz_row_derivatives(P.h_psd[(size_t)p].sigma, P.h_psd[(size_t)p].fknee,
+                                                P.h_psd[(size_t)p].alpha, P.L_grid, P.fsamp, P.lambda, P.window);
+        for (int c = 0; c < 3; ++c) {
+            const std::vector<double> h = overlap_save_spectrum(D[(size_t)c], N);
+            std::copy(h.begin(), h.end(), H.begin() + ((size_t)c * P.npsd + p) * (N + 1));
+        }
+    }
+    P.grad_H = dalloc<double>(H.size());
+    h2d(P.grad_H, H.data(), H.size() * 8, P.stream);
+    P.grad_u = dalloc<double>((size_t)P.nt);
+    P.grad_part = dalloc<double>((size_t)P.K);
+    sync(P.stream);
+}
+
+// dL/dd = N^-1 P mu and dL/dtheta[p][c] = u^T (dN^-1/dtheta_pc) (d - P m), mu = A^-1 g.
+static void grad(PlanHolder& P, const double* d, const double* m, const double* g, double* dLdd, double* dLdpsd,
+                 const mm_solve_opts& so, mm_stats* st) {
+    cudaStream_t s = P.stream;
+    check_solve_opts(P, so);
+    if (dLdpsd != nullptr) ensure_grad(P);
+    else if (P.grad_u == nullptr) P.grad_u = dalloc<double>((size_t)P.nt);
+    mm_stats stats{};
+    check_cuda(cudaEventRecord(P.ev0, s), "event");
+    // adjoint solve A mu = g (A is symmetric)
+    if (is_device_ptr(g))
+        check_cuda(cudaMemcpyAsync(P.b64, g, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy g");
+    else
+        h2d(P.b64, g, (size_t)P.n * 8, s);
+    P.have_b = false;
+    double* mu = P.x64;
+    const int status = solve_from_b(P, so, mu, stats);
+    if (status != MM_OK) {
+        if (st) *st = stats;
+        throw Error{(mm_status)status, std::string("adjoint solve: ") + status_text(status)};
+    }
+    // u = P mu
+    launch_gather<double>(P, mu, P.grad_u, s);
+    if (dLdd != nullptr) {
+        const bool dev = is_device_ptr(dLdd);
+        double* out = dev ? dLdd : P.tod64;
+        launch_toeplitz<double>(P, P.tz64, P.grad_u, nullptr, out, nullptr, s);
+        if (!dev) d2h(dLdd, out, (size_t)P.nt * 8, s);
+    }
+    if (dLdpsd != nullptr) {
+        // v = d - P m in dbuf (staging the inputs when they are host memory)
+        const double* mm_ = m;
+        if (!is_device_ptr(m)) {
+            h2d(P.r64, m, (size_t)P.n * 8, s);
+            mm_ = P.r64;
+        }
+        launch_gather<double>(P, mm_, P.tod64, s);
+        const double* dd = d;
+        if (!is_device_ptr(d)) {
+            h2d(P.dbuf, d, (size_t)P.nt * 8, s);
+            dd = P.dbuf;
+        }
+        launch_sub_time(dd, P.tod64, P.dbuf, P.nt, s);
+        const int64_t N = int64_t(1) << P.tz64.logn;
+        std::vector<double> part((size_t)P.K);
+        for (int c = 0; c < 3; ++c) {
+            ToeplitzDev tzc = P.tz64;
+            tzc.H = P.grad_H + (size_t)c * P.npsd * (N + 1);
+            launch_toeplitz<double>(P, tzc, P.dbuf, nullptr, P.tod64, nullptr, s);
+            launch_interval_dot(P.grad_u, P.tod64, P.ioff, P.K, P.grad_part, s);
+            d2h(part.data(), P.grad_part, (size_t)P.K * 8, s);
+            sync(P.stream);
+            for (int p = 0; p < P.npsd; ++p) dLdpsd[(size_t)p * 3 + c] = 0.0;
+            for (int i = 0; i < P.K; ++i) dLdpsd[(size_t)P.h_ipsd[(size_t)i] * 3 + c] += part[(size_t)i];
+        }
+    }
+    check_cuda(cudaEventRecord(P.ev2, s), "event");
+    sync(P);
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, P.ev0, P.ev2), "event time");
+    stats.ms_total = ms;
+    if (st != nullptr) *st = stats;
 }
 
 }  // namespace mm
@@ -1027,6 +1134,15 @@ mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts
         PlanHolder* P = get(plan);
         if (!d || !m || !opts) throw Error{MM_ERR_ARG, "null argument"};
         solve(*P, d, *opts, m, st);
+    });
+}
+
+mm_status mm_grad(mm_plan_t plan, const double* d, const double* m, const double* g, double* dL_dd,
+                  double* dL_dpsd, const mm_solve_opts* opts, mm_stats* st) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!d || !m || !g || !opts) throw Error{MM_ERR_ARG, "null argument"};
+        grad(*P, d, m, g, dL_dd, dL_dpsd, *opts, st);
     });
 }
 

@@ -153,6 +153,8 @@ void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);
 std::vector<double> toeplitz_row(double sigma, double fknee, double alpha, int64_t L,
                                  double fsamp, int lam, int window);
 bool symbol_positive(const std::vector<double>& t);
+std::vector<std::vector<double>> toeplitz_row_derivatives(double sigma, double fknee, double alpha, int64_t L,
+                                                          double fsamp, int lam, int window);
 std::vector<double> overlap_save_spectrum(const std::vector<double>& t, int64_t N);
 double rcond_sym3(const double B[6]);
 
@@ -175,5 +177,9 @@ void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
 template <typename T>
 void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+// gradient helpers (grad.cu)
+void launch_sub_time(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
+void launch_interval_dot(const double* u, const double* w, const int64_t* ioff, int K, double* part,
+                         cudaStream_t s);
 
 }  // namespace mm

@@ -84,6 +84,41 @@ std::vector<double> toeplitz_row(double sigma, double fknee, double alpha, int64
     return t;
 }
 
+// dt_k / d(sigma, fknee, alpha), k = 0..lam: the row transform above applied to the
+// analytic derivatives of 1/S_j (zero at j = 0; needs fknee > 0):
+//   d(1/S)/dsigma = -(2/sigma)/S,  d(1/S)/dfknee = -(1/S) alpha x / (fknee (1+x)),
+//   d(1/S)/dalpha = -(1/S) x ln(fknee/f) / (1+x),  x = (fknee/f)^alpha.
+std::vector<std::vector<double>> toeplitz_row_derivatives(double sigma, double fknee, double alpha, int64_t L,
+                                                          double fsamp, int lam, int window) {
+    std::vector<std::vector<double>> out(3, std::vector<double>((size_t)lam + 1));
+    for (int c = 0; c < 3; ++c) {
+        std::vector<double> re((size_t)L), im((size_t)L, 0.0);
+        for (int64_t j = 0; j < L; ++j) {
+            const int64_t jj = j <= L - j ? j : L - j;
+            double v = 0.0;
+            if (jj > 0) {
+                const double f = (double)jj * fsamp / (double)L;
+                const double x = std::pow(fknee / f, alpha);
+                const double invS = 1.0 / (sigma * sigma * (1.0 + x));
+                if (c == 0) v = -2.0 / sigma * invS;
+                else if (c == 1) v = -invS * alpha * x / (fknee * (1.0 + x));
+                else v = -invS * x * std::log(fknee / f) / (1.0 + x);
+            }
+            re[(size_t)j] = v;
+        }
+        host_fft(re, im, true);
+        for (int k = 0; k <= lam; ++k) {
+            double w = 1.0;
+            if (window == MM_WINDOW_GAUSS && lam > 0) {
+                const double u = (double)k / (double)lam;
+                w = std::exp(-2.0 * u * u);
+            }
+            out[(size_t)c][(size_t)k] = w * re[(size_t)k] / (double)L;
+        }
+    }
+    return out;
+}
+
 // Spectrum of the even kernel (t_|k| for |k| <= lam, 0 beyond) laid out circularly over
 // M points: sigma(2 pi m / M) = t_0 + 2 sum_k t_k cos(2 pi m k / M), m = 0..M-1.
 static std::vector<double> kernel_spectrum(const std::vector<double>& t, int64_t M) {

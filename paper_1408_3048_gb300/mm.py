@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
-           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex"]
+           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad"]
 
 
 class mm_psd(ctypes.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "mm_coarse_vectors": (I32, [P, P]),
     "mm_solve": (I32, [P, P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(mm_stats)]),
     "mm_solve_ex": (I32, [P, P, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
+    "mm_grad": (I32, [P, P, P, P, P, P, ctypes.POINTER(mm_solve_opts), ctypes.POINTER(mm_stats)]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
@@ -244,6 +245,13 @@ def mm_solve_ex(plan, d, opts, m, raise_on_error=True):
     return status, st
 
 
+def mm_grad(plan, d, m, g, dL_dd, dL_dpsd, opts):
+    st = mm_stats()
+    _check(lib().mm_grad(plan, _ptr(d), _ptr(m), _ptr(g), _ptr(dL_dd), _ptr(dL_dpsd), ctypes.byref(opts),
+                         ctypes.byref(st)), plan)
+    return st
+
+
 def mm_destroy(plan):
     lib().mm_destroy(plan)
 
@@ -359,6 +367,15 @@ class Plan:
             status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
         return m, st.as_dict(), status
 
+    def grad(self, d, m, g, tol=1e-10, maxit=10000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, want_d=True,
+             want_psd=True):
+        """(dL/dd [nt] tensor or None, dL/dtheta [npsd, 3] numpy or None, stats) for g = dL/dm."""
+        o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver)
+        dd = self._new(self.nt, MM_FP64) if want_d else None
+        dp = np.zeros((self.npsd, 3), dtype=np.float64) if want_psd else None
+        st = mm_grad(self.handle, d, m, g, dd, dp, o)
+        return dd, dp, st.as_dict()
+
     def profile(self, enable=True):
         mm_profile(self.handle, enable)
 
@@ -378,3 +395,36 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ autograd wrapper
+def map_solve(plan, d, theta, tol=1e-10, maxit=10000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64,
+              adjoint_tol=None):
+    """m = (P^T N^-1 P)^-1 P^T N^-1 d as a differentiable torch op.
+
+    d      cuda float64 tensor [nt] (time-ordered data)
+    theta  float64 tensor [npsd, 3] = (sigma, fknee, alpha) per PSD id; it must equal the
+           plan's PSDs (the plan was built from them) and only carries their gradient.
+    The backward pass runs one adjoint PCG solve (A is symmetric) and the PSD gradient
+    products of mm_grad; no Krylov vectors are kept from the forward solve.
+    """
+    import torch
+
+    class _MapSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, d_, theta_):
+            m, st, _ = plan.solve(d_.contiguous(), tol=tol, maxit=maxit, kind=kind, solver=solver)
+            ctx.save_for_backward(d_, m)
+            return m
+
+        @staticmethod
+        def backward(ctx, g):
+            d_, m = ctx.saved_tensors
+            need_d, need_th = ctx.needs_input_grad
+            dd, dp, _ = plan.grad(d_, m, g.contiguous().to(torch.float64),
+                                  tol=adjoint_tol if adjoint_tol is not None else tol, maxit=maxit,
+                                  kind=kind, solver=solver, want_d=need_d, want_psd=need_th)
+            gth = torch.from_numpy(dp).to(theta.device) if need_th else None
+            return dd, gth
+
+    return _MapSolve.apply(d, theta)
