@@ -252,6 +252,28 @@ typedef struct {
 mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts, double* m, mm_stats* st);
 
 /*
+ * Many right-hand sides through one plan: R maps or data sets that share P, N^-1 and
+ * M_BD (e.g. Monte-Carlo noise realisations).  The paper's setting for re-using a
+ * precomputed preconditioner over many solves (Sec. 3.3.2); batching itself is not in it.
+ *
+ * mm_apply_A_batch: Y_r = A X_r (Eq. 8) in FP32 for r < R, 1 <= R <= 64; X, Y device
+ * float[R][n].  Two right-hand sides share one complex FFT per overlap-save tile (the
+ * Toeplitz spectrum is real), and each tile's pointing is read once for all of them.
+ *
+ * mm_solve_batch: solves A m_r = P^T N^-1 d_r for r < R (any R >= 1, processed 64 at a
+ * time) with per-right-hand-side PCG scalars and stopping (Sec. 3.1 per column), block-
+ * Jacobi preconditioner, MM_SOLVE_MIXED only: FP64 right-hand sides and refinement
+ * residuals per column, batched FP32 inner PCG replayed from a captured CUDA graph when
+ * the plan's stream is not the legacy default stream.  D host or device double[R][nt],
+ * M host or device double[R][n], st host mm_stats[R] or NULL (ms_total is the batch time
+ * divided by the columns of its group of 64).  MM_ERR_NOT_CONVERGED if any column missed
+ * tol (all maps are still written).
+ */
+mm_status mm_apply_A_batch(mm_plan_t plan, int R, const float* X, float* Y);
+mm_status mm_solve_batch(mm_plan_t plan, const double* D, int R, const mm_solve_opts* opts, double* M,
+                         mm_stats* st);
+
+/*
  * Gradients of a loss L(m) of the GLS map m = A^-1 P^T N^-1 d (Eq. 3, 5, 7), given
  * g = dL/dm at the solution m of the data d.  The paper does not differentiate Eq. 3;
  * with A symmetric one more PCG solve gives them:

@@ -14,6 +14,7 @@
 #include "coarse_host.h"
 #include "mm_internal.h"
 #include "pcg.cuh"
+#include "batch.cuh"
 
 namespace mm {
 
@@ -104,7 +105,29 @@ void prof_flush(Plan& P) {
 }
 
 // ----------------------------------------------------------------------------- plan
+// Buffers of the batched (many right-hand sides) solver, allocated on first use.
+struct BatchState {
+    int logb = 0;                 // complex FFT length of the batched Toeplitz kernel
+    int ntiles = 0;
+    Tile* tiles = nullptr;
+    float* H = nullptr;           // [npsd][B/2 + 1] / B
+    int cap = 0;                  // right-hand sides the vectors below hold
+    float *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *tod = nullptr;
+    double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+    double *partial = nullptr, *rho = nullptr, *bb = nullptr, *rr = nullptr, *tol2 = nullptr;
+    int* iters = nullptr;
+    unsigned char* state = nullptr;
+    int* flags = nullptr;
+    unsigned* bar = nullptr;
+    int nblocks = 0;
+    cudaGraphExec_t graph = nullptr;   // `graph_iters` batched iterations, or null
+    int graph_R = -1;             // R and maxit the graph was captured with
+    int graph_maxit = -1;
+    bool graph_failed = false;
+};
+
 struct PlanHolder : Plan {
+    BatchState batch;
     std::vector<mm_psd> h_psd;
     double* grad_H = nullptr;   // [3][npsd][N+1] derivative spectra (FP64 block)
     double* grad_u = nullptr;   // [nt] P mu
@@ -160,6 +183,13 @@ static void destroy_plan(PlanHolder* P) {
         (void)cudaEventDestroy(e.b);
     }
     for (auto e : P->prof.pool) (void)cudaEventDestroy(e);
+    BatchState& bt = P->batch;
+    if (bt.graph) (void)cudaGraphExecDestroy(bt.graph);
+    for (void* p : {(void*)bt.tiles, (void*)bt.H, (void*)bt.x, (void*)bt.r, (void*)bt.p, (void*)bt.q, (void*)bt.z,
+                    (void*)bt.tod, (void*)bt.x64, (void*)bt.b64, (void*)bt.r64, (void*)bt.partial, (void*)bt.rho,
+                    (void*)bt.bb, (void*)bt.rr, (void*)bt.tol2, (void*)bt.iters, (void*)bt.state, (void*)bt.flags,
+                    (void*)bt.bar})
+        dfree(p);
     delete P;
 }
 
@@ -887,6 +917,295 @@ static void grad(PlanHolder& P, const double* d, const double* m, const double* 
     if (st != nullptr) *st = stats;
 }
 
+
+// ------------------------------------------------------------------ batched solver
+static void ensure_batch_tables(PlanHolder& P) {
+    BatchState& bt = P.batch;
+    if (bt.tiles != nullptr) return;
+    int best = -1;
+    double best_cost = 0.0;
+    for (int logb = 9; logb <= 14; ++logb) {
+        const int64_t B = int64_t(1) << logb;
+        const int64_t Lv = B - 2 * (int64_t)P.lambda;
+        if (Lv < 1) continue;
+        int64_t tiles = 0;
+        for (int i = 0; i < P.K; ++i) tiles += (P.h_ioff[i + 1] - P.h_ioff[i] + Lv - 1) / Lv;
+        const double cost = (double)tiles * ((double)B * logb + 4096.0);
+        if (best < 0 || cost < best_cost) {
+            best = logb;
+            best_cost = cost;
+        }
+    }
+    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the batched shared-memory FFT block"};
+    bt.logb = best;
+    const int64_t B = int64_t(1) << best;
+    const int64_t Lv = B - 2 * (int64_t)P.lambda;
+    std::vector<Tile> tiles;
+    for (int i = 0; i < P.K; ++i) {
+        const int64_t a = P.h_ioff[i], b = P.h_ioff[i + 1];
+        for (int64_t s0 = a; s0 < b; s0 += Lv) {
+            Tile t;
+            t.out0 = s0;
+            t.ibeg = a;
+            t.iend = b;
+            t.nout = (int32_t)std::min<int64_t>(Lv, b - s0);
+            t.psd = P.h_ipsd[i];
+            tiles.push_back(t);
+        }
+    }
+    bt.ntiles = (int)tiles.size();
+    bt.tiles = dalloc<Tile>(tiles.size());
+    h2d(bt.tiles, tiles.data(), tiles.size() * sizeof(Tile), P.stream);
+    std::vector<float> H((size_t)P.npsd * (B / 2 + 1));
+    for (int p = 0; p < P.npsd; ++p) {
+        // overlap_save_spectrum(t, N) returns sigma_k / N for k <= N on a 2N grid
+        const std::vector<double> h = overlap_save_spectrum(P.rows[(size_t)p], B / 2);
+        for (int64_t k = 0; k <= B / 2; ++k) H[(size_t)p * (B / 2 + 1) + k] = (float)(h[(size_t)k] * 0.5);
+    }
+    bt.H = dalloc<float>(H.size());
+    h2d(bt.H, H.data(), H.size() * 4, P.stream);
+    sync(P.stream);
+}
+
+static void ensure_batch_buffers(PlanHolder& P, int R) {
+    BatchState& bt = P.batch;
+    if (bt.cap >= R) return;
+    for (void* p : {(void*)bt.x, (void*)bt.r, (void*)bt.p, (void*)bt.q, (void*)bt.z, (void*)bt.tod, (void*)bt.x64,
+                    (void*)bt.b64, (void*)bt.r64})
+        dfree(p);
+    bt.x = bt.r = bt.p = bt.q = bt.z = bt.tod = nullptr;
+    bt.x64 = bt.b64 = bt.r64 = nullptr;
+    bt.cap = 0;
+    if (bt.graph) {
+        (void)cudaGraphExecDestroy(bt.graph);
+        bt.graph = nullptr;
+    }
+    const size_t n = (size_t)P.n, nt = (size_t)P.nt;
+    for (float** v : {&bt.x, &bt.r, &bt.p, &bt.q, &bt.z}) *v = dalloc<float>(n * R);
+    bt.tod = dalloc<float>(nt * R);
+    for (double** v : {&bt.x64, &bt.b64, &bt.r64}) *v = dalloc<double>(n * R);
+    if (bt.partial == nullptr) {
+        bt.nblocks = std::max(1, std::min(batch_pcg_max_blocks(P.num_sms), (P.npix_obs + 31) / 32));
+        bt.partial = dalloc<double>((size_t)bt.nblocks * BATCH_PSTRIDE);
+        for (double** v : {&bt.rho, &bt.bb, &bt.rr, &bt.tol2}) *v = dalloc<double>(BATCH_RMAX);
+        bt.iters = dalloc<int>(BATCH_RMAX);
+        bt.state = dalloc<unsigned char>(BATCH_RMAX);
+        bt.flags = dalloc<int>(8);
+        bt.bar = dalloc<unsigned>(4);
+        check_cuda(cudaMemsetAsync(bt.bar, 0, 16, P.stream), "memset");
+    }
+    bt.cap = R;
+}
+
+static BatchTzArgs batch_tz_args(PlanHolder& P, int R, const float* X, float* Z, const int* done) {
+    BatchTzArgs A{};
+    A.tiles = P.batch.tiles;
+    A.H = P.batch.H;
+    A.X = X;
+    A.pixc = P.pixc;
+    A.w = P.w32;
+    A.Z = Z;
+    A.done = done;
+    A.n = P.n;
+    A.nt = P.nt;
+    A.R = R;
+    A.lambda = P.lambda;
+    return A;
+}
+
+// Y_r = A X_r (FP32), r < R <= BATCH_RMAX
+static void apply_A_batch(PlanHolder& P, int R, const float* X, float* Y, const int* done) {
+    launch_batch_toeplitz(batch_tz_args(P, R, X, P.batch.tod, done), P.batch.logb, P.batch.ntiles, P.ncomp, P.stream);
+    launch_batch_scatter(P, P.batch.tod, Y, R, done, P.stream);
+}
+
+static BatchPcgArgs batch_pcg_args(PlanHolder& P, int R, int maxit) {
+    BatchState& bt = P.batch;
+    BatchPcgArgs a{};
+    a.n = P.n;
+    a.npix = P.npix_obs;
+    a.R = R;
+    a.maxit = maxit;
+    a.x = bt.x;
+    a.r = bt.r;
+    a.p = bt.p;
+    a.q = bt.q;
+    a.z = bt.z;
+    a.bd = P.bd32;
+    a.partial = bt.partial;
+    a.rho = bt.rho;
+    a.bb = bt.bb;
+    a.rr = bt.rr;
+    a.tol2 = bt.tol2;
+    a.iters = bt.iters;
+    a.state = bt.state;
+    a.flags = bt.flags;
+    a.bar = bt.bar;
+    return a;
+}
+
+// One batched PCG run on the right-hand sides in batch.r (FP32); iterations are replayed
+// from a captured CUDA graph of `chunk` iterations when capture works on this stream.
+static void run_batch_pcg(PlanHolder& P, int R, int maxit) {
+    BatchState& bt = P.batch;
+    cudaStream_t s = P.stream;
+    const BatchPcgArgs a = batch_pcg_args(P, R, maxit);
+    check_cuda(cudaMemsetAsync(bt.flags, 0, 32, s), "memset flags");
+    check_cuda(cudaMemsetAsync(bt.state, 0, BATCH_RMAX, s), "memset state");
+    launch_batch_pcg(0, P.ncomp, a, bt.nblocks, s);
+    constexpr int kChunk = 4;
+    auto body = [&]() {
+        for (int i = 0; i < kChunk; ++i) {
+            apply_A_batch(P, R, bt.p, bt.q, bt.flags + F_DONE);
+            launch_batch_pcg(1, P.ncomp, a, bt.nblocks, s);
+        }
+    };
+    // the graph is keyed on R and maxit (kernel arguments are captured by value)
+    if (bt.graph != nullptr && (bt.graph_R != R || bt.graph_maxit != maxit)) {
+        (void)cudaGraphExecDestroy(bt.graph);
+        bt.graph = nullptr;
+    }
+    if (bt.graph == nullptr && !bt.graph_failed && s != nullptr) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            bool ok = true;
+            try {
+                body();
+            } catch (const Error&) {
+                ok = false;
+            }
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            ok = ok && e == cudaSuccess && g != nullptr;
+            if (ok && cudaGraphInstantiate(&bt.graph, g, 0) != cudaSuccess) {
+                bt.graph = nullptr;
+                ok = false;
+            }
+            if (g) (void)cudaGraphDestroy(g);
+            if (!ok) bt.graph_failed = true;
+        } else {
+            bt.graph_failed = true;
+        }
+        (void)cudaGetLastError();
+        bt.graph_R = R;
+        bt.graph_maxit = maxit;
+    }
+    int launched = 0;
+    int h_flags[4];
+    while (true) {
+        d2h(h_flags, bt.flags, 16, s);
+        sync(s);
+        if (h_flags[F_DONE] || launched > maxit) break;
+        if (bt.graph != nullptr) {
+            check_cuda(cudaGraphLaunch(bt.graph, s), "graph launch");
+            note_launch(3 * kChunk);
+        } else {
+            body();
+        }
+        launched += kChunk;
+    }
+}
+
+static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_opts& so, double* M, mm_stats* st) {
+    cudaStream_t s = P.stream;
+    if (R < 1) throw Error{MM_ERR_ARG, "R must be >= 1"};
+    check_solve_opts(P, so);
+    if (so.solver != MM_SOLVE_MIXED || so.kind != MM_PREC_BD)
+        throw Error{MM_ERR_ARG, "the batched solver runs MM_SOLVE_MIXED with MM_PREC_BD"};
+    ensure_batch_tables(P);
+    const int RB = std::min(R, BATCH_RMAX);
+    ensure_batch_buffers(P, RB);
+    BatchState& bt = P.batch;
+    const bool d_dev = is_device_ptr(D), m_dev = is_device_ptr(M);
+    const size_t n = (size_t)P.n, nt = (size_t)P.nt;
+    const int max_outer = so.max_outer > 0 ? so.max_outer : 20;
+    const double inner_min = so.inner_tol_min > 0.0 ? so.inner_tol_min : 3e-7;
+    int overall = MM_OK;
+    for (int c0 = 0; c0 < R; c0 += RB) {
+        const int Rc = std::min(RB, R - c0);
+        check_cuda(cudaEventRecord(P.ev0, s), "event");
+        std::vector<double> bb(Rc), rr(Rc);
+        std::vector<int> iters(Rc, 0), outer(Rc, 0), fp64(Rc, 0);
+        // b_r = P^T N^-1 d_r (FP64)
+        for (int r = 0; r < Rc; ++r) {
+            const double* dr = D + (size_t)(c0 + r) * nt;
+            if (!d_dev) {
+                h2d(P.dbuf, dr, nt * 8, s);
+                dr = P.dbuf;
+            }
+            launch_toeplitz<double>(P, P.tz64, dr, nullptr, P.tod64, nullptr, s);
+            launch_scatter<double>(P, P.tod64, bt.b64 + (size_t)r * n, nullptr, s);
+            bb[(size_t)r] = dot64(P, bt.b64 + (size_t)r * n, bt.b64 + (size_t)r * n);
+            rr[(size_t)r] = bb[(size_t)r];
+        }
+        check_cuda(cudaMemsetAsync(bt.x64, 0, n * Rc * 8, s), "memset x");
+        check_cuda(cudaMemcpyAsync(bt.r64, bt.b64, n * Rc * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+        int total = 0;
+        for (int o = 0; o < max_outer; ++o) {
+            std::vector<double> tol2(BATCH_RMAX, 0.0), nrm(Rc, 0.0);
+            bool any = false;
+            for (int r = 0; r < Rc; ++r) {
+                const bool act = bb[(size_t)r] > 0.0 && std::sqrt(rr[(size_t)r]) > so.tol * std::sqrt(bb[(size_t)r]);
+                float* r32 = bt.r + (size_t)r * n;
+                if (act) {
+                    any = true;
+                    nrm[(size_t)r] = std::sqrt(rr[(size_t)r]);
+                    launch_scale_f32(bt.r64 + (size_t)r * n, 1.0 / nrm[(size_t)r], r32, (int64_t)n, s);
+                    double ti = 0.5 * so.tol * std::sqrt(bb[(size_t)r]) / nrm[(size_t)r];
+                    ti = std::min(0.5, std::max(ti, inner_min));
+                    if (o == 0 && so.first_inner_tol > 0.0) ti = so.first_inner_tol;
+                    tol2[(size_t)r] = ti * ti;
+                } else {
+                    check_cuda(cudaMemsetAsync(r32, 0, n * 4, s), "memset r");
+                }
+            }
+            if (!any || total >= so.maxit) break;
+            h2d(bt.tol2, tol2.data(), BATCH_RMAX * 8, s);
+            run_batch_pcg(P, Rc, so.maxit - total);
+            std::vector<int> it(BATCH_RMAX);
+            std::vector<unsigned char> stt(BATCH_RMAX);
+            d2h(it.data(), bt.iters, BATCH_RMAX * 4, s);
+            d2h(stt.data(), bt.state, BATCH_RMAX, s);
+            sync(s);
+            int mx = 0;
+            for (int r = 0; r < Rc; ++r) {
+                if (nrm[(size_t)r] == 0.0) continue;
+                if (stt[(size_t)r] == 3) throw Error{MM_ERR_NOT_SPD, "batched PCG breakdown"};
+                iters[(size_t)r] += it[(size_t)r];
+                mx = std::max(mx, it[(size_t)r]);
+                outer[(size_t)r] += 1;
+                fp64[(size_t)r] += 1;
+                double* x64 = bt.x64 + (size_t)r * n;
+                launch_axpy_host(x64, bt.x + (size_t)r * n, nrm[(size_t)r], (int64_t)n, s);
+                apply_A<double>(P, x64, P.ax64, nullptr);
+                launch_sub(bt.b64 + (size_t)r * n, P.ax64, bt.r64 + (size_t)r * n, P.n, s);
+                rr[(size_t)r] = dot64(P, bt.r64 + (size_t)r * n, bt.r64 + (size_t)r * n);
+            }
+            total += mx;
+        }
+        for (int r = 0; r < Rc; ++r) {
+            double* mr = M + (size_t)(c0 + r) * n;
+            if (m_dev) check_cuda(cudaMemcpyAsync(mr, bt.x64 + (size_t)r * n, n * 8, cudaMemcpyDeviceToDevice, s), "copy m");
+            else d2h(mr, bt.x64 + (size_t)r * n, n * 8, s);
+        }
+        check_cuda(cudaEventRecord(P.ev2, s), "event");
+        sync(P);
+        float ms = 0.f;
+        check_cuda(cudaEventElapsedTime(&ms, P.ev0, P.ev2), "event time");
+        for (int r = 0; r < Rc; ++r) {
+            mm_stats x{};
+            x.iters = iters[(size_t)r];
+            x.outer = outer[(size_t)r];
+            x.fp64_products = fp64[(size_t)r];
+            x.rel_resid = bb[(size_t)r] > 0 ? std::sqrt(rr[(size_t)r] / bb[(size_t)r]) : 0.0;
+            x.converged = x.rel_resid <= so.tol;
+            x.ms_total = ms / Rc;
+            if (!x.converged) overall = MM_ERR_NOT_CONVERGED;
+            if (st) st[c0 + r] = x;
+        }
+    }
+    if (overall != MM_OK) throw Error{(mm_status)overall, "some right-hand sides did not reach tol"};
+}
+
 }  // namespace mm
 
 // ================================================================== C entry points
@@ -1143,6 +1462,26 @@ mm_status mm_grad(mm_plan_t plan, const double* d, const double* m, const double
         PlanHolder* P = get(plan);
         if (!d || !m || !g || !opts) throw Error{MM_ERR_ARG, "null argument"};
         grad(*P, d, m, g, dL_dd, dL_dpsd, *opts, st);
+    });
+}
+
+mm_status mm_apply_A_batch(mm_plan_t plan, int R, const float* X, float* Y) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!X || !Y || R < 1 || R > BATCH_RMAX) throw Error{MM_ERR_ARG, "need 1 <= R <= 64 and non-null X, Y"};
+        ensure_batch_tables(*P);
+        ensure_batch_buffers(*P, R);
+        apply_A_batch(*P, R, X, Y, nullptr);
+        sync(*P);
+    });
+}
+
+mm_status mm_solve_batch(mm_plan_t plan, const double* D, int R, const mm_solve_opts* opts, double* M,
+                         mm_stats* st) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!D || !M || !opts) throw Error{MM_ERR_ARG, "null argument"};
+        solve_batch(*P, D, R, *opts, M, st);
     });
 }
 

@@ -1,0 +1,59 @@
+// Batched (many right-hand sides) kernels and their arguments (see batch.cu).
+#pragma once
+
+#include "mm_internal.h"
+
+namespace mm {
+
+constexpr int BATCH_RMAX = 64;                 // right-hand sides per batched launch
+constexpr int BATCH_THREADS = 512;
+constexpr int BATCH_PSTRIDE = 3 * BATCH_RMAX;  // per-block partial slots
+
+struct BatchTzArgs {
+    const Tile* tiles;
+    const float* H;            // [npsd][B/2 + 1], divided by B
+    const float* X;            // [R][n]
+    const int32_t* pixc;
+    const float2* w;
+    float* Z;                  // [R][nt]
+    const int* done;
+    int64_t n;
+    int64_t nt;
+    int R;
+    int lambda;
+};
+
+struct BatchPcgArgs {
+    int64_t n;
+    int npix;
+    int R;
+    int maxit;
+    float* x;
+    float* r;
+    float* p;
+    const float* q;
+    float* z;
+    const float* bd;
+    double* partial;           // [grid][BATCH_PSTRIDE]
+    double* rho;               // [R]
+    double* bb;
+    double* rr;
+    const double* tol2;        // [R] squared relative tolerance
+    int* iters;                // [R]
+    unsigned char* state;      // [R] 0 running, 1 converged, 2 maxit, 3 breakdown
+    int* flags;
+    unsigned* bar;
+};
+
+size_t batch_toeplitz_smem(int logb);
+void launch_batch_toeplitz(const BatchTzArgs& A, int logb, int ntiles, int ncomp, cudaStream_t s);
+void launch_batch_scatter(const Plan& P, const float* Z, float* W, int R, const int* done, cudaStream_t s);
+void launch_batch_pcg(int which, int ncomp, const BatchPcgArgs& a, int nblocks, cudaStream_t s);
+int batch_pcg_max_blocks(int num_sms);
+
+}  // namespace mm
+
+namespace mm {
+void launch_scale_f32(const double* a, double s, float* out, int64_t n, cudaStream_t st);
+void launch_axpy_host(double* x, const float* d, double s, int64_t n, cudaStream_t st);
+}  // namespace mm

@@ -17,44 +17,6 @@
 
 namespace mm {
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Returns false when this block gave up waiting (timeout recorded in flags).
-__device__ bool grid_sync(unsigned* bar, int* flags) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned nb = gridDim.x;
-        const unsigned inc = blockIdx.x == 0 ? (0x80000000u - (nb - 1u)) : 1u;
-        __threadfence();
-        const unsigned old = atomicAdd(bar, inc);
-        const unsigned long long t0 = global_ns();
-        while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0u) {
-            if (global_ns() - t0 > 2000000000ull) {
-                atomicExch(&flags[F_STATUS], (int)MM_ERR_TIMEOUT);
-                atomicExch(&flags[F_DONE], 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // Block-wide FP64 sum (fixed order); result valid in every thread.
 __device__ double block_sum(double v, double* sh) {
 #pragma unroll

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
-           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad"]
+           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch", "mm_solve_batch"]
 
 
 class mm_psd(ctypes.Structure):
@@ -89,6 +89,8 @@ _SIGS = {
     "mm_solve": (I32, [P, P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(mm_stats)]),
     "mm_solve_ex": (I32, [P, P, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
     "mm_grad": (I32, [P, P, P, P, P, P, ctypes.POINTER(mm_solve_opts), ctypes.POINTER(mm_stats)]),
+    "mm_apply_A_batch": (I32, [P, ctypes.c_int, P, P]),
+    "mm_solve_batch": (I32, [P, P, ctypes.c_int, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
@@ -252,6 +254,18 @@ def mm_grad(plan, d, m, g, dL_dd, dL_dpsd, opts):
     return st
 
 
+def mm_apply_A_batch(plan, R, X, Y):
+    _check(lib().mm_apply_A_batch(plan, int(R), _ptr(X), _ptr(Y)), plan)
+
+
+def mm_solve_batch(plan, D, R, opts, M, raise_on_error=True):
+    st = (mm_stats * int(R))()
+    status = lib().mm_solve_batch(plan, _ptr(D), int(R), ctypes.byref(opts), _ptr(M), st)
+    if raise_on_error:
+        _check(status, plan)
+    return status, [x.as_dict() for x in st]
+
+
 def mm_destroy(plan):
     lib().mm_destroy(plan)
 
@@ -315,35 +329,42 @@ class Plan:
 
     def gather(self, x, precision=MM_FP64):
         y = self._new(self.nt, precision)
+        self._sync_in()
         mm_gather(self.handle, precision, x, y)
         return y
 
     def apply_ninv(self, y, precision=MM_FP64):
         z = self._new(self.nt, precision)
+        self._sync_in()
         mm_apply_ninv(self.handle, precision, y, z)
         return z
 
     def scatter(self, z, precision=MM_FP64):
         w = self._new(self.n, precision)
+        self._sync_in()
         mm_scatter(self.handle, precision, z, w)
         return w
 
     def apply_A(self, x, precision=MM_FP64, out=None):
         y = self._new(self.n, precision) if out is None else out
+        self._sync_in()
         mm_apply_A(self.handle, precision, x, y)
         return y
 
     def rhs(self, d):
         b = self._new(self.n, MM_FP64)
+        self._sync_in()
         mm_rhs(self.handle, d, b)
         return b
 
     def precond(self, r, kind=MM_PREC_BD, precision=MM_FP64):
         z = self._new(self.n, precision)
+        self._sync_in()
         mm_precond(self.handle, kind, precision, r, z)
         return z
 
     def build_coarse(self, k, precision=MM_FP64, bprime=None, tol=1e-6, maxit=1000):
+        self._sync_in()
         mm_build_coarse(self.handle, k, precision, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
 
@@ -362,8 +383,10 @@ class Plan:
                               max_outer=int(extra.get("max_outer", 0)),
                               inner_tol_min=float(extra.get("inner_tol_min", 0.0)),
                               first_inner_tol=float(extra.get("first_inner_tol", 0.0)))
+            self._sync_in()
             status, st = mm_solve_ex(self.handle, d, o, m, raise_on_error)
         else:
+            self._sync_in()
             status, st = mm_solve(self.handle, d, tol, maxit, kind, solver, m, raise_on_error)
         return m, st.as_dict(), status
 
@@ -373,8 +396,35 @@ class Plan:
         o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver)
         dd = self._new(self.nt, MM_FP64) if want_d else None
         dp = np.zeros((self.npsd, 3), dtype=np.float64) if want_psd else None
+        self._sync_in()
         st = mm_grad(self.handle, d, m, g, dd, dp, o)
         return dd, dp, st.as_dict()
+
+    def apply_A_batch(self, X, out=None):
+        """Y[r] = A X[r] in FP32 for a float32 cuda tensor X [R, n] (R <= 64)."""
+        R = X.shape[0]
+        Y = self._torch.empty((R, self.n), dtype=self._torch.float32, device="cuda") if out is None else out
+        self._sync_in()
+        mm_apply_A_batch(self.handle, R, X, Y)
+        return Y
+
+    def solve_batch(self, D, tol=1e-6, maxit=5000, out=None, raise_on_error=True, **extra):
+        """Maps for D [R, nt] float64 (mixed precision, block-Jacobi); returns (M, stats, status)."""
+        R = D.shape[0]
+        M = self._torch.empty((R, self.n), dtype=self._torch.float64, device="cuda") if out is None else out
+        o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=MM_PREC_BD, solver=MM_SOLVE_MIXED,
+                          max_outer=int(extra.get("max_outer", 0)),
+                          inner_tol_min=float(extra.get("inner_tol_min", 0.0)),
+                          first_inner_tol=float(extra.get("first_inner_tol", 0.0)))
+        self._sync_in()
+        status, st = mm_solve_batch(self.handle, D, R, o, M, raise_on_error)
+        return M, st, status
+
+    def _sync_in(self):
+        """Make work queued on the caller's current stream visible to the plan's stream."""
+        cur = self._torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.synchronize()
 
     def profile(self, enable=True):
         mm_profile(self.handle, enable)
