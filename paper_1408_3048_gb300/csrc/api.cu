@@ -111,6 +111,7 @@ struct BatchState {
     int ntiles = 0;
     Tile* tiles = nullptr;
     float* H = nullptr;           // [npsd][B/2 + 1] / B
+    float* ptw = nullptr;         // per-pass FFT twiddles of the B-point transform
     int cap = 0;                  // right-hand sides the vectors below hold
     float *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *tod = nullptr;
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
@@ -144,6 +145,7 @@ struct PlanHolder : Plan {
 static void free_tz(ToeplitzDev& t) {
     dfree(t.tiles);
     dfree(t.twiddle);
+    dfree(t.ptw);
     dfree(t.H);
     t = ToeplitzDev{};
 }
@@ -185,7 +187,7 @@ static void destroy_plan(PlanHolder* P) {
     for (auto e : P->prof.pool) (void)cudaEventDestroy(e);
     BatchState& bt = P->batch;
     if (bt.graph) (void)cudaGraphExecDestroy(bt.graph);
-    for (void* p : {(void*)bt.tiles, (void*)bt.H, (void*)bt.x, (void*)bt.r, (void*)bt.p, (void*)bt.q, (void*)bt.z,
+    for (void* p : {(void*)bt.tiles, (void*)bt.H, (void*)bt.ptw, (void*)bt.x, (void*)bt.r, (void*)bt.p, (void*)bt.q, (void*)bt.z,
                     (void*)bt.tod, (void*)bt.x64, (void*)bt.b64, (void*)bt.r64, (void*)bt.partial, (void*)bt.rho,
                     (void*)bt.bb, (void*)bt.rr, (void*)bt.tol2, (void*)bt.iters, (void*)bt.state, (void*)bt.flags,
                     (void*)bt.bar})
@@ -250,6 +252,13 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     for (int64_t k = 0; k <= B / 4; ++k) tw[(size_t)k] = (T)std::cos(2.0 * 3.14159265358979323846 * (double)k / (double)B);
     tz.twiddle = dalloc<T>(tw.size());
     h2d(tz.twiddle, tw.data(), tw.size() * sizeof(T), P.stream);
+    {
+        const std::vector<double> pt = pass_twiddle_table(tz.logn);
+        std::vector<T> ptT(pt.begin(), pt.end());
+        tz.ptw = dalloc<T>(ptT.size());
+        h2d(tz.ptw, ptT.data(), ptT.size() * sizeof(T), P.stream);
+        sync(P.stream);
+    }
     std::vector<T> H((size_t)P.npsd * (N + 1));
     for (int p = 0; p < P.npsd; ++p) {
         const std::vector<double> h = overlap_save_spectrum(P.rows[(size_t)p], N);
@@ -964,6 +973,10 @@ static void ensure_batch_tables(PlanHolder& P) {
     }
     bt.H = dalloc<float>(H.size());
     h2d(bt.H, H.data(), H.size() * 4, P.stream);
+    const std::vector<double> pt = pass_twiddle_table(best);
+    std::vector<float> ptf(pt.begin(), pt.end());
+    bt.ptw = dalloc<float>(ptf.size());
+    h2d(bt.ptw, ptf.data(), ptf.size() * 4, P.stream);
     sync(P.stream);
 }
 
@@ -1001,6 +1014,7 @@ static BatchTzArgs batch_tz_args(PlanHolder& P, int R, const float* X, float* Z,
     BatchTzArgs A{};
     A.tiles = P.batch.tiles;
     A.H = P.batch.H;
+    A.ptw = reinterpret_cast<const float2*>(P.batch.ptw);
     A.X = X;
     A.pixc = P.pixc;
     A.w = P.w32;

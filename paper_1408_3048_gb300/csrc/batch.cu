@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
         }
     }
     __syncthreads();
-    fft_all<float, LOGB, NT, 0>(a, nullptr);
+    fft_all<float, LOGB, NT, 0>(a, A.ptw);
     // spectrum product (real, even kernel; H holds k = 0..Bn/2, already divided by Bn),
     // conjugated for the inverse by the forward transform
     const float* H = A.H + (int64_t)tile.psd * (Bn / 2 + 1);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
         a[pad<float>(k)] = v;
     }
     __syncthreads();
-    fft_all<float, LOGB, NT, 0>(a, nullptr);
+    fft_all<float, LOGB, NT, 0>(a, A.ptw);
     float* z0 = A.Z + (size_t)r0 * A.nt + tile.out0;
     float* z1 = A.Z + (size_t)(r0 + 1) * A.nt + tile.out0;
     for (int n = tid; n < tile.nout; n += NT) {
@@ -190,34 +190,56 @@ void launch_batch_scatter(const Plan& P, const float* Z, float* W, int R, const 
 
 // --------------------------------------------------------------------- batched PCG
 
-// Totals over blocks of slot j for j < count, one warp per slot, lanes over blocks in a
-// fixed order; result in sh[j].
+// FP32-pair helpers (exact two-sum; see pcg.cu for why the wide reductions avoid FP64).
+__device__ __forceinline__ void bpair_add(float& hi, float& lo, float h2, float l2) {
+    const float s = hi + h2;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (h2 - bv);
+    hi = s;
+    lo = lo + l2 + e;
+}
+
+// Totals over blocks of slot j for j < count (slots hold FP32 pairs), one warp per slot,
+// lanes over blocks in a fixed order; result (FP64) in sh[j].
 __device__ void batch_totals(const double* part, int stride, int slot0, int count, double* sh) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < count; j += nw) {
-        double s = 0.0;
-        for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * stride + slot0 + j);
+        float hi = 0.f, lo = 0.f;
+        for (unsigned b = l; b < gridDim.x; b += 32) {
+            const float2 p = __ldcg(reinterpret_cast<const float2*>(part + (size_t)b * stride + slot0 + j));
+            bpair_add(hi, lo, p.x, p.y);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (l == 0) sh[j] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            bpair_add(hi, lo, h2, l2);
+        }
+        if (l == 0) sh[j] = (double)hi + (double)lo;
     }
     __syncthreads();
 }
 
-// Block partial of sum_i a_r[i] b_r[i] for every RHS r, i over this block's elements.
+// Block partial of sum_i a_r[i] b_r[i] for every RHS r, i over this block's elements:
+// exact products accumulated as FP32 pairs, stored as a pair in the slot.
 __device__ void batch_dots(const float* A_, const float* B_, int64_t n, int64_t e0, int64_t e1, int R,
                            double* part_row, const unsigned char* active) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int r = w; r < R; r += nw) {
-        double s = 0.0;
+        DotAcc<float> acc;
         if (active[r]) {
             const float* a = A_ + (size_t)r * n;
             const float* b = B_ + (size_t)r * n;
-            for (int64_t i = e0 + l; i < e1; i += 32) s += (double)a[i] * (double)b[i];
+            for (int64_t i = e0 + l; i < e1; i += 32) acc.add(a[i], b[i]);
         }
+        float hi = acc.hi, lo = acc.lo;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (l == 0) part_row[r] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            bpair_add(hi, lo, h2, l2);
+        }
+        if (l == 0) *reinterpret_cast<float2*>(part_row + r) = make_float2(hi, lo);
     }
 }
 

@@ -12,6 +12,7 @@ constexpr int BATCH_PSTRIDE = 3 * BATCH_RMAX;  // per-block partial slots
 struct BatchTzArgs {
     const Tile* tiles;
     const float* H;            // [npsd][B/2 + 1], divided by B
+    const float2* ptw;         // per-pass FFT twiddles of the B-point transform
     const float* X;            // [R][n]
     const int32_t* pixc;
     const float2* w;

@@ -28,6 +28,7 @@ struct ToeplitzDev {
     int ntiles = 0;
     Tile* tiles = nullptr;   // [ntiles]
     void* twiddle = nullptr; // T[B/4 + 1]: cos(2 pi k / B)
+    void* ptw = nullptr;     // T2[...]: per-pass twiddles of the N-point FFT
     void* H = nullptr;       // T[npsd][N + 1]: kernel spectrum / N (real, even kernel)
 };
 
@@ -156,6 +157,8 @@ bool symbol_positive(const std::vector<double>& t);
 std::vector<std::vector<double>> toeplitz_row_derivatives(double sigma, double fknee, double alpha, int64_t L,
                                                           double fsamp, int lam, int window);
 std::vector<double> overlap_save_spectrum(const std::vector<double>& t, int64_t N);
+// per-pass Stockham twiddles of an N = 2^logn point FFT as interleaved (cos, sin)
+std::vector<double> pass_twiddle_table(int logn);
 double rcond_sym3(const double B[6]);
 
 // kernels (launchers) --------------------------------------------------------------------

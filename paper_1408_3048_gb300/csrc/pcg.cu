@@ -17,26 +17,78 @@
 
 namespace mm {
 
-// Block-wide FP64 sum (fixed order); result valid in every thread.
-__device__ double block_sum(double v, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < nw; ++i) s += sh[i];
-    return s;
+// Reductions.  GB300 runs FP64 at 1/64 of the FP32 rate, so the wide part of every
+// reduction (within warps) works on exact FP32 pairs and only warp 0 does a few FP64
+// additions.  All trees are fixed (xor shuffles, lanes over blocks in order), so every
+// block obtains bit-identical scalars.
+
+// (hi, lo) += (h2, l2) with a two-sum of the high parts; symmetric in its operands.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
+    const float s = hi + h2;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (h2 - bv);
+    hi = s;
+    lo = lo + l2 + e;
 }
 
-// Sum of slot `slot` over all block partials: every thread reads at most a few partials
-// (L2 loads, bypassing L1) and the block reduces them in a fixed order, so every block
-// obtains the same value.  Must be called by all threads of the block.
+__device__ __forceinline__ void warp_pair_reduce(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        pair_add(hi, lo, h2, l2);
+    }
+}
+
+__device__ __forceinline__ double warp_sum64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block total of per-thread accumulators; valid in every thread.  Call with all threads.
+__device__ double block_total(DotAcc<float> acc, double* sh) {
+    __shared__ float2 wp[32];
+    float hi = acc.hi, lo = acc.lo;
+    warp_pair_reduce(hi, lo);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) wp[w] = make_float2(hi, lo);
+    __syncthreads();
+    if (w == 0) {
+        const double v = warp_sum64(l < nw ? (double)wp[l].x + (double)wp[l].y : 0.0);
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+__device__ double block_total(DotAcc<double> acc, double* sh) {
+    const double v = warp_sum64(acc.s);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[1 + w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const double t = warp_sum64(l < nw ? sh[1 + l] : 0.0);
+        if (l == 0) sh[0] = t;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// Sum of slot `slot` over all block partials (warp 0: lanes over blocks in order, then a
+// shuffle tree), valid in every thread.  Call with all threads.
 __device__ double grid_total(const double* part, int slot, double* sh) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(part + (size_t)b * PSTRIDE + slot);
-    return block_sum(s, sh);
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * PSTRIDE + slot);
+        s = warp_sum64(s);
+        if (threadIdx.x == 0) sh[0] = s;
+    }
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
 }
 
 // Pixel range of this block.
@@ -59,10 +111,15 @@ __device__ void coarse_partials(const PcgArgs<T>& a, const T* r, int64_t e0, int
         T sl = (T)0;
 #pragma unroll 8
         for (int64_t i = e0 + l; i < e1; i += 32) sl += __ldg(zj + i) * r[i];
-        double s = (double)sl;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (l == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_COARSE + j] = s;
+        double* slot = a.partial + (size_t)blockIdx.x * PSTRIDE + S_COARSE + j;
+        if constexpr (sizeof(T) == 4) {
+            float hi = sl, lo = 0.f;
+            warp_pair_reduce(hi, lo);
+            if (l == 0) *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+        } else {
+            const double s = warp_sum64(sl);
+            if (l == 0) *slot = s;
+        }
     }
 }
 
@@ -73,11 +130,21 @@ template <typename T>
 __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < a.k; j += nw) {
-        double s = 0.0;
-        for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(a.partial + (size_t)b * PSTRIDE + S_COARSE + j);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (l == 0) v_sh[j] = s;
+        const double* col = a.partial + S_COARSE + j;
+        if constexpr (sizeof(T) == 4) {
+            float hi = 0.f, lo = 0.f;
+            for (unsigned b = l; b < gridDim.x; b += 32) {
+                const float2 p = __ldcg(reinterpret_cast<const float2*>(col + (size_t)b * PSTRIDE));
+                pair_add(hi, lo, p.x, p.y);
+            }
+            warp_pair_reduce(hi, lo);
+            if (l == 0) v_sh[j] = (double)hi + (double)lo;
+        } else {
+            double s = 0.0;
+            for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(col + (size_t)b * PSTRIDE);
+            s = warp_sum64(s);
+            if (l == 0) v_sh[j] = s;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -112,20 +179,26 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
 
 // z = M_BD (r - AZ v) + Z v (or M_BD r) on this block's pixels; returns partial r^T z.
 template <typename T, int NC, bool TWO>
-__device__ double apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0, int p1) {
-    double rz = 0.0;
+__device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0, int p1) {
+    __shared__ T vt[KMAX];
+    if constexpr (TWO) {
+        if (threadIdx.x < a.k) vt[threadIdx.x] = (T)v_sh[threadIdx.x];
+        __syncthreads();
+    }
+    DotAcc<T> rz;
     for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
         const int64_t e = (int64_t)q * NC;
-        T t[NC], zc[NC];
+        T t[NC], zc[NC], t0[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             t[c] = a.r[e + c];
+            t0[c] = t[c];
             zc[c] = (T)0;
         }
         if constexpr (TWO) {
 #pragma unroll 8
             for (int j = 0; j < a.k; ++j) {
-                const T vj = (T)v_sh[j];
+                const T vj = vt[j];
                 const T* az = a.AZ + (size_t)j * a.n + e;
                 const T* zz = a.Z + (size_t)j * a.n + e;
 #pragma unroll
@@ -147,7 +220,7 @@ __device__ double apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0,
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             a.z[e + c] = out[c];
-            rz += (double)a.r[e + c] * (double)out[c];
+            rz.add(t0[c], out[c]);
         }
     }
     return rz;
@@ -162,24 +235,24 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     int p0, p1;
     block_pixels(a.npix, p0, p1);
     const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
-    double bb = 0.0;
+    DotAcc<T> bacc;
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
         a.x[i] = (T)0;
-        bb += (double)a.r[i] * (double)a.r[i];
+        bacc.add(a.r[i], a.r[i]);
     }
-    bb = block_sum(bb, sh);
+    const double bb = block_total(bacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = bb;
     if constexpr (TWO) coarse_partials(a, a.r, e0, e1);
     if (!grid_sync(a.bar, a.flags)) return;
     const double bbt = grid_total(a.partial, S_RR, sh);
     if constexpr (TWO) coarse_solve(a, v_sh);
-    double rz = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    const DotAcc<T> rzacc = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
     __syncthreads();
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
         a.p[i] = a.z[i];
         if (a.zstore != nullptr) a.zstore[i] = a.z[i];
     }
-    rz = block_sum(rz, sh);
+    const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags)) return;
     const double rho = grid_total(a.partial, S_RZ, sh);
@@ -213,9 +286,9 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     block_pixels(a.npix, p0, p1);
     const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
     // phase A: p^T q
-    double pq = 0.0;
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) pq += (double)a.p[i] * (double)a.q[i];
-    pq = block_sum(pq, sh);
+    DotAcc<T> pacc;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) pacc.add(a.p[i], a.q[i]);
+    const double pq = block_total(pacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_PQ] = pq;
     if (!grid_sync(a.bar, a.flags)) return;
     const double pqt = grid_total(a.partial, S_PQ, sh);
@@ -230,14 +303,14 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     const double alpha = rho / pqt;
     // phase B: x += alpha p, r -= alpha q, r^T r, Z^T r
     const T al = (T)alpha;
-    double rr = 0.0;
+    DotAcc<T> racc;
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
         a.x[i] += al * a.p[i];
         const T ri = a.r[i] - al * a.q[i];
         a.r[i] = ri;
-        rr += (double)ri * (double)ri;
+        racc.add(ri, ri);
     }
-    rr = block_sum(rr, sh);
+    const double rr = block_total(racc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = rr;
     if constexpr (TWO) {
         __syncthreads();
@@ -272,8 +345,8 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     }
     // phase C: z = M r, r^T z
     if constexpr (TWO) coarse_solve(a, v_sh);
-    double rz = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
-    rz = block_sum(rz, sh);
+    const DotAcc<T> rzacc = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags)) return;
     const double rzt = grid_total(a.partial, S_RZ, sh);
@@ -364,7 +437,7 @@ __global__ void dot_partial_kernel(const TA* a, const TB* b, int64_t n, double* 
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s += (double)a[i] * (double)b[i];
-    s = block_sum(s, sh);
+    s = block_total(DotAcc<double>{s}, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 

@@ -89,6 +89,31 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* flags) {
     return ok != 0;
 }
 
+// Dot-product accumulator of one thread.  FP64 vectors: plain FP64 FMAs.  FP32 vectors:
+// each product a b is formed exactly as p + e (p = fl(a b), e = fma(a, b, -p)) and
+// accumulated as an unevaluated FP32 pair (hi, lo) with a two-sum, so the per-thread
+// partial carries ~48 bits; it is converted to FP64 once for the block and grid sums.
+// (Per-element FP32 -> FP64 conversions would run on the FP64 pipe, 1/64 of FP32 rate.)
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double total() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);
+        const float s = hi + p;
+        const float bv = s - hi;
+        const float err = (hi - (s - bv)) + (p - bv);
+        hi = s;
+        lo += err + e;
+    }
+    __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
+};
+
 template <typename T>
 void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks, cudaStream_t s);
 int pcg_max_blocks(int num_sms);

@@ -152,6 +152,31 @@ std::vector<double> overlap_save_spectrum(const std::vector<double>& t, int64_t 
     return h;
 }
 
+// Twiddles of the in-shared-memory Stockham FFT (toeplitz.cuh): for every pass after the
+// first, radix R = 16 (8 for N < 512) or the remainder, Ns = product of the earlier
+// radices, entry [(r - 1) Ns + k] = (cos, sin) of 2 pi r k / (Ns R).  Same pass schedule
+// as fft_all on the device.
+std::vector<double> pass_twiddle_table(int logn) {
+    const int maxr = ((1 << logn) / 16 >= 32) ? 4 : 3;
+    std::vector<double> out;
+    int l = 0;
+    while (l < logn) {
+        const int rem = logn - l;
+        const int lr = rem >= maxr ? maxr : rem;
+        const int64_t Ns = int64_t(1) << l, R = int64_t(1) << lr;
+        // (the first pass, Ns = 1, reads no twiddles but keeps its R - 1 slots so the
+        // offsets match ptw_offset on the device)
+        for (int64_t r = 1; r < R; ++r)
+            for (int64_t k = 0; k < Ns; ++k) {
+                const double ang = 2.0 * kPi * (double)((r * k) % (Ns * R)) / (double)(Ns * R);
+                out.push_back(std::cos(ang));
+                out.push_back(std::sin(ang));
+            }
+        l += lr;
+    }
+    return out;
+}
+
 // lambda_min / lambda_max of a symmetric 3x3 block given packed (a00 a01 a02 a11 a12 a22),
 // by cyclic Jacobi rotations (converges to working precision in a few sweeps).
 double rcond_sym3(const double Bp[6]) {

@@ -31,7 +31,8 @@ template <> struct Cx<float> { using type = float2; };
 template <typename T>
 struct TzArgs {
     const Tile* tiles;
-    const T* twiddle;      // [N/2 + 1]
+    const T* twiddle;      // [N/2 + 1]: cos(2 pi k / B), real-FFT split
+    const typename Cx<T>::type* ptw;  // per-pass FFT twiddles (ptw_offset)
     const T* H;            // [npsd][N + 1]
     const T* y;            // time-domain input (mode 0)
     const T* x;            // map (gather modes)
@@ -131,57 +132,85 @@ __device__ __forceinline__ void dft<double, 8>(double2* v) { dft8<double>(v); }
 template <>
 __device__ __forceinline__ void dft<float, 8>(float2* v) { dft8<float>(v); }
 
-// padding: one slot every 128 bytes
+// 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle W16^(n2 k1), DFT4 over
+// n2; outputs in natural order.  (c, s) below are cos and sin of 2 pi m / 16.
+template <typename T>
+__device__ __forceinline__ void dft16(typename Cx<T>::type* v) {
+    using C2 = typename Cx<T>::type;
+    const T C1 = (T)0.92387953251128675613, S1 = (T)0.38268343236508977173, H = (T)0.70710678118654752440;
+    C2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C2 a0 = v[n2], a1 = v[4 + n2], a2 = v[8 + n2], a3 = v[12 + n2];
+        dft4<T>(a0, a1, a2, a3);
+        y[n2][0] = a0;
+        y[n2][1] = a1;
+        y[n2][2] = a2;
+        y[n2][3] = a3;
+    }
+    // W16^(n2 k1): (1,1):m1 (1,2):m2 (1,3):m3 (2,1):m2 (2,2):m4 (2,3):m6 (3,1):m3 (3,2):m6 (3,3):m9
+    y[1][1] = cmul<T>(y[1][1], C1, S1);
+    y[1][2] = cmul<T>(y[1][2], H, H);
+    y[1][3] = cmul<T>(y[1][3], S1, C1);
+    y[2][1] = cmul<T>(y[2][1], H, H);
+    {
+        const C2 t = y[2][2];   // * (-i)
+        y[2][2].x = t.y;
+        y[2][2].y = -t.x;
+    }
+    y[2][3] = cmul<T>(y[2][3], -H, H);
+    y[3][1] = cmul<T>(y[3][1], S1, C1);
+    y[3][2] = cmul<T>(y[3][2], -H, H);
+    y[3][3] = cmul<T>(y[3][3], -C1, -S1);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C2 b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
+        dft4<T>(b0, b1, b2, b3);
+        v[k1] = b0;
+        v[k1 + 4] = b1;
+        v[k1 + 8] = b2;
+        v[k1 + 12] = b3;
+    }
+}
+
+template <>
+__device__ __forceinline__ void dft<double, 16>(double2* v) { dft16<double>(v); }
+template <>
+__device__ __forceinline__ void dft<float, 16>(float2* v) { dft16<float>(v); }
+
+// Padding: one slot after every 16 elements, so the stride-16 stores of a first radix-16
+// pass (thread j writes 16 j + r) hit distinct banks within every 128-byte wavefront for
+// both 8-byte (float2) and 16-byte (double2) elements; the other passes are contiguous.
 template <typename T> struct PadLog;
-template <> struct PadLog<double> { static constexpr int v = 3; };   // 8 x 16 B
-template <> struct PadLog<float> { static constexpr int v = 4; };    // 16 x 8 B
+template <> struct PadLog<double> { static constexpr int v = 4; };
+template <> struct PadLog<float> { static constexpr int v = 4; };
 
 template <typename T>
 __device__ __forceinline__ int pad(int i) { return i + (i >> PadLog<T>::v); }
 
-// v[r] *= W_{Ns R}^{r k}, r = 1..R-1 (W_M = exp(-2 pi i / M)).
-// FP64: every power read from the quarter-wave table (the FP64 pipe is the bottleneck of
-// the FP64 kernel, table reads go to the otherwise idle load/store unit).
-// FP32: one sincospif per butterfly and the powers by a multiplication tree of depth <= 3
-// (the FP32 kernel is shared-memory bound, and power-of-two strided table reads conflict).
-template <typename T, int LOGN, int LOGR, int LOGNS>
-__device__ __forceinline__ void pass_twiddles(typename Cx<T>::type* v, int k, const T* tab) {
-    constexpr int R = 1 << LOGR;
-    if constexpr (sizeof(T) == 8) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            const int m = (r * k) << (LOGN + 1 - LOGNS - LOGR);
-            T c, s;
-            twiddle<T, LOGN - 1>(tab, m, c, s);
-            v[r] = cmul<T>(v[r], c, s);
-        }
-    } else {
-        float sn, cs;
-        // angle 2 pi k / (Ns R) = pi * x, x = 2k / 2^(LOGNS + LOGR) exactly representable
-        sincospif((float)(2 * k) * (1.0f / (float)(1 << (LOGNS + LOGR))), &sn, &cs);
-        float2 w[8];
-        w[1] = make_float2(cs, sn);   // (cos, sin) of theta; multiply uses c - i s
-        auto mulw = [](float2 a, float2 b) {   // (cos, sin) of the sum of the two angles
-            return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-        };
-        if constexpr (R >= 4) {
-            w[2] = mulw(w[1], w[1]);
-            w[3] = mulw(w[1], w[2]);
-        }
-        if constexpr (R >= 8) {
-            w[4] = mulw(w[2], w[2]);
-            w[5] = mulw(w[2], w[3]);
-            w[6] = mulw(w[3], w[3]);
-            w[7] = mulw(w[3], w[4]);
-        }
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul<T>(v[r], w[r].x, w[r].y);
+// Largest radix of the passes: 16 when N/16 >= 32 threads can hold one butterfly each.
+template <int LOGN>
+__host__ __device__ constexpr int fft_max_logr() { return (1 << LOGN) / 16 >= 32 ? 4 : 3; }
+
+// Per-pass twiddle table: pass p (Ns_p = 2^LOGNS, radix R_p) stores W_{Ns R}^{r k} as
+// (cos, sin) of 2 pi r k / (Ns R) at [(r - 1) Ns + k], r = 1..R-1, k < Ns (consecutive
+// threads read consecutive entries); the passes follow each other.  Offset of the pass
+// that starts at LOGNS:
+template <int LOGN>
+__host__ __device__ constexpr int ptw_offset(int logns) {
+    int off = 0, l = 0;
+    while (l < logns) {
+        const int rem = LOGN - l;
+        const int lr = rem >= fft_max_logr<LOGN>() ? fft_max_logr<LOGN>() : rem;
+        off += (1 << l) * ((1 << lr) - 1);
+        l += lr;
     }
+    return off;
 }
 
 // One in-place Stockham pass of radix R on N = 2^LOGN points (Ns = 2^LOGNS).
 template <typename T, int LOGN, int NT, int LOGR, int LOGNS>
-__device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) {
+__device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename Cx<T>::type* ptw) {
     using C2 = typename Cx<T>::type;
     constexpr int N = 1 << LOGN;
     constexpr int R = 1 << LOGR;
@@ -202,7 +231,14 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) 
     for (int b = 0; b < BPT; ++b) {
         const int j = tid + b * NT;
         const int k = j & (Ns - 1);
-        if (LOGNS > 0) pass_twiddles<T, LOGN, LOGR, LOGNS>(v[b], k, tab);
+        if constexpr (LOGNS > 0) {
+            const C2* tw = ptw + ptw_offset<LOGN>(LOGNS) + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C2 w = __ldg(tw + (r - 1) * Ns);
+                v[b][r] = cmul<T>(v[b][r], w.x, w.y);
+            }
+        }
         dft<T, R>(v[b]);
         const int idx = ((j - k) << LOGR) + k;
 #pragma unroll
@@ -212,12 +248,13 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const T* tab) 
 }
 
 template <typename T, int LOGN, int NT, int LOGNS>
-__device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const T* tab) {
+__device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const typename Cx<T>::type* ptw) {
     if constexpr (LOGNS < LOGN) {
         constexpr int REM = LOGN - LOGNS;
-        constexpr int LOGR = REM >= 3 ? 3 : REM;
-        fft_pass<T, LOGN, NT, LOGR, LOGNS>(a, tab);
-        fft_all<T, LOGN, NT, LOGNS + LOGR>(a, tab);
+        constexpr int MAXR = fft_max_logr<LOGN>();
+        constexpr int LOGR = REM >= MAXR ? MAXR : REM;
+        fft_pass<T, LOGN, NT, LOGR, LOGNS>(a, ptw);
+        fft_all<T, LOGN, NT, LOGNS + LOGR>(a, ptw);
     }
 }
 
@@ -235,66 +272,57 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const int tid = threadIdx.x;
     for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     const int64_t ws = tile.out0 - A.lambda;
-    // Load the block in batches: all pointing / weight loads of a batch are issued before
-    // the dependent map gathers, so each thread keeps UNR pairs of samples in flight.
-    constexpr int PER = N / NT;                 // complex points per thread
+    // Load the B = 2N real samples, one per lane (fully coalesced pointing / weight loads),
+    // into the packed complex array viewed as reals: sample s -> component s & 1 of u_(s/2).
+    // Batches keep UNR independent pointing loads in flight before the map gathers.
+    T* ar = reinterpret_cast<T*>(a);
+    constexpr int PER = 2 * N / NT;             // real samples per thread
     constexpr int UMAX = MODE == 3 ? 4 : 8;
     constexpr int UNR = PER < UMAX ? PER : UMAX;
+    const bool interior = ws >= tile.ibeg && ws + 2 * (int64_t)N <= tile.iend;
 #pragma unroll 1
     for (int base = 0; base < PER; base += UNR) {
-        T v0[UNR], v1[UNR];
+        T v[UNR];
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const int64_t t0 = ws + 2 * (int64_t)((base + u) * NT + tid);
-                v0[u] = (t0 >= tile.ibeg && t0 < tile.iend) ? A.y[t0] : (T)0;
-                v1[u] = (t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend) ? A.y[t0 + 1] : (T)0;
+                const int64_t t = ws + (int64_t)((base + u) * NT + tid);
+                v[u] = (interior || (t >= tile.ibeg && t < tile.iend)) ? A.y[t] : (T)0;
             }
         } else {
-            int q0[UNR], q1[UNR];
-            typename Cx<T>::type w0[UNR], w1[UNR];
+            int q[UNR];
+            typename Cx<T>::type w[UNR];
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const int64_t t0 = ws + 2 * (int64_t)((base + u) * NT + tid);
-                const bool ok0 = t0 >= tile.ibeg && t0 < tile.iend;
-                const bool ok1 = t0 + 1 >= tile.ibeg && t0 + 1 < tile.iend;
-                q0[u] = ok0 ? __ldg(A.pixc + t0) : -1;
-                q1[u] = ok1 ? __ldg(A.pixc + t0 + 1) : -1;
+                const int64_t t = ws + (int64_t)((base + u) * NT + tid);
+                const bool ok = interior || (t >= tile.ibeg && t < tile.iend);
+                q[u] = ok ? __ldg(A.pixc + t) : -1;
                 if constexpr (MODE == 3) {
-                    if (ok0) w0[u] = A.w[t0];
-                    if (ok1) w1[u] = A.w[t0 + 1];
+                    if (ok) w[u] = A.w[t];
                 }
             }
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                if constexpr (MODE == 1) {
-                    v0[u] = q0[u] >= 0 ? __ldg(A.x + q0[u]) : (T)0;
-                    v1[u] = q1[u] >= 0 ? __ldg(A.x + q1[u]) : (T)0;
-                } else {
-                    T r0 = (T)0, r1 = (T)0;
-                    if (q0[u] >= 0) {
-                        const T* xq = A.x + 3 * (int64_t)q0[u];
-                        r0 = __ldg(xq) + w0[u].x * __ldg(xq + 1) + w0[u].y * __ldg(xq + 2);
+                T r = (T)0;
+                if (q[u] >= 0) {
+                    if constexpr (MODE == 1) {
+                        r = __ldg(A.x + q[u]);
+                    } else {
+                        const T* xq = A.x + 3 * (int64_t)q[u];
+                        r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
                     }
-                    if (q1[u] >= 0) {
-                        const T* xq = A.x + 3 * (int64_t)q1[u];
-                        r1 = __ldg(xq) + w1[u].x * __ldg(xq + 1) + w1[u].y * __ldg(xq + 2);
-                    }
-                    v0[u] = r0;
-                    v1[u] = r1;
                 }
+                v[u] = r;
             }
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            C2 c;
-            c.x = v0[u];
-            c.y = v1[u];
-            a[pad<T>((base + u) * NT + tid)] = c;
+            const int sidx = (base + u) * NT + tid;
+            ar[2 * pad<T>(sidx >> 1) + (sidx & 1)] = v[u];
         }
     }
     __syncthreads();
-    fft_all<T, LOGN, NT, 0>(a, tab);
+    fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // real-FFT post-processing, spectrum product, pre-processing for the inverse.
     const T* H = A.H + (int64_t)tile.psd * (N + 1);
     for (int k = tid; k <= N / 2; k += NT) {
@@ -342,7 +370,7 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
         if (k2 != k) a[pad<T>(k2)] = V2;
     }
     __syncthreads();
-    fft_all<T, LOGN, NT, 0>(a, tab);
+    fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // outputs: real samples lambda .. lambda + nout - 1 of the block
     T* zo = A.z + tile.out0;
     for (int n = tid; n < tile.nout; n += NT) {
@@ -352,12 +380,14 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     }
 }
 
-// Threads per CTA: N/8 (one radix-8 butterfly per thread and pass), capped at
-// 512 (at 1024 threads the 64-register limit spills the butterflies), at least 32.
+// Threads per CTA: one largest-radix butterfly per thread and pass (N/16, or N/8 for
+// small N), capped at 1024 for FP32 (16 complex values per thread fit the 64-register
+// budget of a 1024-thread CTA) and 512 for FP64, at least 32.
 template <typename T, int LOGN>
-constexpr int tz_threads() {
-    constexpr int cap = 512;
-    return (1 << LOGN) / 8 >= cap ? cap : ((1 << LOGN) / 8 < 32 ? 32 : (1 << LOGN) / 8);
+__host__ __device__ constexpr int tz_threads() {
+    constexpr int cap = sizeof(T) == 4 ? 1024 : 512;
+    constexpr int want = (1 << LOGN) >> fft_max_logr<LOGN>();
+    return want >= cap ? cap : (want < 32 ? 32 : want);
 }
 
 template <typename T>

@@ -16,6 +16,7 @@ void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y
     TzArgs<float> A;
     A.tiles = tz.tiles;
     A.twiddle = static_cast<const float*>(tz.twiddle);
+    A.ptw = static_cast<const typename Cx<float>::type*>(tz.ptw);
     A.H = static_cast<const float*>(tz.H);
     A.y = y;
     A.x = x;

@@ -16,6 +16,7 @@ void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double*
     TzArgs<double> A;
     A.tiles = tz.tiles;
     A.twiddle = static_cast<const double*>(tz.twiddle);
+    A.ptw = static_cast<const typename Cx<double>::type*>(tz.ptw);
     A.H = static_cast<const double*>(tz.H);
     A.y = y;
     A.x = x;
