@@ -195,19 +195,22 @@ static void destroy_plan(PlanHolder* P) {
     delete P;
 }
 
-// Overlap-save block choice: minimise (tiles x B log2 B) over admissible blocks.
+// Overlap-save block choice: minimise tiles x (B log2 B + 4096) over admissible blocks,
+// the largest one on a two-CTA cluster (weighted 1.1 for its cross-CTA steps).
+// Returns logn; sets *cluster to 1 or 2.
 template <typename T>
-static int choose_logn(const Plan& P, int forced_log2B) {
+static int choose_logn(const Plan& P, int forced_log2B, int* cluster) {
     const int maxl = toeplitz_max_logn<T>();
     if (forced_log2B > 0) {
         const int logn = forced_log2B - 1;
-        if (logn < 8 || logn > maxl) throw Error{MM_ERR_ARG, "fft block size out of range"};
+        if (logn < 8 || logn > maxl + 1) throw Error{MM_ERR_ARG, "fft block size out of range"};
         if ((int64_t(2) << logn) - 2 * (int64_t)P.lambda < 1) throw Error{MM_ERR_ARG, "fft block too short for lambda"};
+        *cluster = logn > maxl ? 2 : 1;
         return logn;
     }
     int best = -1;
     double best_cost = 0.0;
-    for (int logn = 8; logn <= maxl; ++logn) {
+    for (int logn = 8; logn <= maxl + 1; ++logn) {
         const int64_t B = int64_t(2) << logn;
         const int64_t Lv = B - 2 * (int64_t)P.lambda;
         if (Lv < 1) continue;
@@ -216,19 +219,20 @@ static int choose_logn(const Plan& P, int forced_log2B) {
             const int64_t len = P.h_ioff[i + 1] - P.h_ioff[i];
             tiles += (len + Lv - 1) / Lv;
         }
-        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0);
+        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0) * (logn > maxl ? 1.1 : 1.0);
         if (best < 0 || cost < best_cost) {
             best = logn;
             best_cost = cost;
         }
     }
-    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the shared-memory FFT block"};
+    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the largest FFT block"};
+    *cluster = best > maxl ? 2 : 1;
     return best;
 }
 
 template <typename T>
 static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
-    tz.logn = choose_logn<T>(P, forced_log2B);
+    tz.logn = choose_logn<T>(P, forced_log2B, &tz.cluster);
     const int64_t N = int64_t(1) << tz.logn;
     const int64_t B = 2 * N;
     const int64_t Lv = B - 2 * (int64_t)P.lambda;
@@ -253,7 +257,8 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     tz.twiddle = dalloc<T>(tw.size());
     h2d(tz.twiddle, tw.data(), tw.size() * sizeof(T), P.stream);
     {
-        const std::vector<double> pt = pass_twiddle_table(tz.logn);
+        // the cluster kernel runs local FFTs of half the length
+        const std::vector<double> pt = pass_twiddle_table(tz.cluster == 2 ? tz.logn - 1 : tz.logn);
         std::vector<T> ptT(pt.begin(), pt.end());
         tz.ptw = dalloc<T>(ptT.size());
         h2d(tz.ptw, ptT.data(), ptT.size() * sizeof(T), P.stream);
@@ -421,8 +426,19 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     h2d(P.ipsd, P.h_ipsd.data(), (size_t)K * 4, s);
     P.t0 = dalloc<double>((size_t)npsd);
     h2d(P.t0, t0.data(), (size_t)npsd * 8, s);
-    build_toeplitz<double>(P, P.tz64, o->fft_log2_f64);
-    build_toeplitz<float>(P, P.tz32, o->fft_log2_f32);
+    // A precision whose largest block cannot hold the band is left unbuilt (logn = 0):
+    // its operators then fail with MM_ERR_ARG; at least one precision must exist.
+    for (int prec = 0; prec < 2; ++prec) {
+        try {
+            if (prec == 0) build_toeplitz<double>(P, P.tz64, o->fft_log2_f64);
+            else build_toeplitz<float>(P, P.tz32, o->fft_log2_f32);
+        } catch (const Error& e) {
+            const bool forced = prec == 0 ? o->fft_log2_f64 > 0 : o->fft_log2_f32 > 0;
+            if (e.st != MM_ERR_ARG || forced) throw;
+            (prec == 0 ? P.tz64 : P.tz32) = ToeplitzDev{};
+        }
+    }
+    if (P.tz64.logn == 0 && P.tz32.logn == 0) throw Error{MM_ERR_ARG, "lambda too large for every FFT block"};
     // M_BD (Eq. 10)
     const size_t bdn = (size_t)P.npix_obs * (P.ncomp == 3 ? 6 : 1);
     P.bd64 = dalloc<double>(bdn);
@@ -844,6 +860,7 @@ static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, doubl
 // Derivative spectra of the Toeplitz rows, built on the first gradient call.
 static void ensure_grad(PlanHolder& P) {
     if (P.grad_H != nullptr) return;
+    if (P.tz64.logn == 0) throw Error{MM_ERR_ARG, "the PSD gradient needs an FP64 Toeplitz block for this lambda"};
     const int64_t N = int64_t(1) << P.tz64.logn;
     std::vector<double> H((size_t)3 * P.npsd * (N + 1));
     for (int p = 0; p < P.npsd; ++p) {
@@ -1289,8 +1306,8 @@ mm_status mm_plan_info(mm_plan_t plan, int32_t* npix_obs, int64_t* n, int64_t* n
         if (npix_obs) *npix_obs = P->npix_obs;
         if (n) *n = P->n;
         if (nkept) *nkept = P->nkept;
-        if (fft_block_f64) *fft_block_f64 = 2 << P->tz64.logn;
-        if (fft_block_f32) *fft_block_f32 = 2 << P->tz32.logn;
+        if (fft_block_f64) *fft_block_f64 = P->tz64.logn ? 2 << P->tz64.logn : 0;
+        if (fft_block_f32) *fft_block_f32 = P->tz32.logn ? 2 << P->tz32.logn : 0;
     });
 }
 

@@ -20,6 +20,8 @@
 // The tile load can evaluate y = P x on the fly from the map (fused de-pointing).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "mm_internal.h"
 
 namespace mm {
@@ -259,50 +261,40 @@ __device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const typename 
 }
 
 // MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map.
-template <typename T, int LOGN, int NT, int MODE>
-__global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
-    using C2 = typename Cx<T>::type;
-    constexpr int N = 1 << LOGN;
-    constexpr int Q = N / 2;             // B/4
-    if (A.done != nullptr && *(volatile const int*)A.done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C2* a = reinterpret_cast<C2*>(smem_raw);
-    T* tab = reinterpret_cast<T*>(smem_raw + sizeof(C2) * (N + (N >> PadLog<T>::v)));
-    const Tile tile = A.tiles[blockIdx.x];
+// Load real samples [s0, s0 + count) of the block that starts at time ws into ar[0..count)
+// (one sample per lane, coalesced; ar is the packed complex array viewed as reals, so local
+// sample s lands in component s & 1 of complex slot s / 2).  Samples outside the tile's
+// interval read as 0.  MODE 0: from A.y; 1: T gather; 3: I/Q/U gather.
+template <typename T, int NT, int MODE>
+__device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile, int64_t ws, T* ar, int s0,
+                                           int count) {
     const int tid = threadIdx.x;
-    for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
-    const int64_t ws = tile.out0 - A.lambda;
-    // Load the B = 2N real samples, one per lane (fully coalesced pointing / weight loads),
-    // into the packed complex array viewed as reals: sample s -> component s & 1 of u_(s/2).
-    // Batches keep UNR independent pointing loads in flight before the map gathers.
-    T* ar = reinterpret_cast<T*>(a);
-    constexpr int PER = 2 * N / NT;             // real samples per thread
+    const int PER = count / NT;
     constexpr int UMAX = MODE == 3 ? 4 : 8;
-    constexpr int UNR = PER < UMAX ? PER : UMAX;
-    const bool interior = ws >= tile.ibeg && ws + 2 * (int64_t)N <= tile.iend;
+    const bool interior = ws + s0 >= tile.ibeg && ws + s0 + count <= tile.iend;
 #pragma unroll 1
-    for (int base = 0; base < PER; base += UNR) {
-        T v[UNR];
+    for (int base = 0; base < PER; base += UMAX) {
+        T v[UMAX];
         if constexpr (MODE == 0) {
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int64_t t = ws + (int64_t)((base + u) * NT + tid);
-                v[u] = (interior || (t >= tile.ibeg && t < tile.iend)) ? A.y[t] : (T)0;
+            for (int u = 0; u < UMAX; ++u) {
+                const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
+                v[u] = (base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend))) ? A.y[t] : (T)0;
             }
         } else {
-            int q[UNR];
-            typename Cx<T>::type w[UNR];
+            int q[UMAX];
+            typename Cx<T>::type w[UMAX];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int64_t t = ws + (int64_t)((base + u) * NT + tid);
-                const bool ok = interior || (t >= tile.ibeg && t < tile.iend);
+            for (int u = 0; u < UMAX; ++u) {
+                const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
+                const bool ok = base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend));
                 q[u] = ok ? __ldg(A.pixc + t) : -1;
                 if constexpr (MODE == 3) {
                     if (ok) w[u] = A.w[t];
                 }
             }
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
+            for (int u = 0; u < UMAX; ++u) {
                 T r = (T)0;
                 if (q[u] >= 0) {
                     if constexpr (MODE == 1) {
@@ -316,56 +308,79 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
             }
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            const int sidx = (base + u) * NT + tid;
-            ar[2 * pad<T>(sidx >> 1) + (sidx & 1)] = v[u];
+        for (int u = 0; u < UMAX; ++u) {
+            if (base + u < PER) {
+                const int sidx = (base + u) * NT + tid;
+                ar[2 * pad<T>(sidx >> 1) + (sidx & 1)] = v[u];
+            }
         }
     }
+}
+
+// Real-FFT split of the packed spectrum at the bin pair (k, N - k), product with the real
+// kernel spectrum (h1 = H[k], h2 = H[N - k]) and the merge back to packed form, returned
+// conjugated for the inverse-by-forward transform.  (cw, sw) = (cos, sin) of 2 pi k / B.
+template <typename T>
+__device__ __forceinline__ void split_product(typename Cx<T>::type u1, typename Cx<T>::type u2, T cw, T sw, T h1,
+                                              T h2, typename Cx<T>::type& V1, typename Cx<T>::type& V2) {
+    using C2 = typename Cx<T>::type;
+    // E = (u1 + conj u2)/2, O = -i (u1 - conj u2)/2
+    C2 E, O;
+    E.x = (T)0.5 * (u1.x + u2.x); E.y = (T)0.5 * (u1.y - u2.y);
+    O.x = (T)0.5 * (u1.y + u2.y); O.y = (T)-0.5 * (u1.x - u2.x);
+    const C2 WO = cmul<T>(O, cw, sw);
+    C2 X1, X2;                         // X_k = E + W O, X_{N-k} = conj(E - W O)
+    X1.x = E.x + WO.x; X1.y = E.y + WO.y;
+    X2.x = E.x - WO.x; X2.y = -(E.y - WO.y);
+    C2 Z1, Z2;
+    Z1.x = h1 * X1.x; Z1.y = h1 * X1.y;
+    Z2.x = h2 * X2.x; Z2.y = h2 * X2.y;
+    // V1 = (Z1 + conj Z2)/2 + i conj(W) (Z1 - conj Z2)/2
+    // V2 = (Z2 + conj Z1)/2 - i W (Z2 - conj Z1)/2
+    C2 S1, D1, S2, D2;
+    S1.x = (T)0.5 * (Z1.x + Z2.x); S1.y = (T)0.5 * (Z1.y - Z2.y);
+    D1.x = (T)0.5 * (Z1.x - Z2.x); D1.y = (T)0.5 * (Z1.y + Z2.y);
+    S2.x = S1.x; S2.y = -S1.y;
+    D2.x = -D1.x; D2.y = D1.y;
+    {
+        const T px = cw * D1.x - sw * D1.y;   // conj(W) * D1
+        const T py = cw * D1.y + sw * D1.x;
+        V1.x = S1.x - py; V1.y = S1.y + px;   // + i (px + i py)
+    }
+    {
+        const T px = cw * D2.x + sw * D2.y;   // W * D2
+        const T py = cw * D2.y - sw * D2.x;
+        V2.x = S2.x + py; V2.y = S2.y - px;   // - i (px + i py)
+    }
+    // conjugates: the forward FFT of conj(V) is conj of N * IFFT(V)
+    V1.y = -V1.y;
+    V2.y = -V2.y;
+}
+
+template <typename T, int LOGN, int NT, int MODE>
+__global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
+    using C2 = typename Cx<T>::type;
+    constexpr int N = 1 << LOGN;
+    constexpr int Q = N / 2;             // B/4
+    if (A.done != nullptr && *(volatile const int*)A.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* a = reinterpret_cast<C2*>(smem_raw);
+    T* tab = reinterpret_cast<T*>(smem_raw + sizeof(C2) * (N + (N >> PadLog<T>::v)));
+    const Tile tile = A.tiles[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
+    const int64_t ws = tile.out0 - A.lambda;
+    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), 0, 2 * N);
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // real-FFT post-processing, spectrum product, pre-processing for the inverse.
     const T* H = A.H + (int64_t)tile.psd * (N + 1);
     for (int k = tid; k <= N / 2; k += NT) {
         const int k2 = (N - k) & (N - 1);
-        const C2 u1 = a[pad<T>(k)];
-        const C2 u2 = a[pad<T>(k2)];
         T cw, sw;                         // W = cw - i sw = exp(-2 pi i k / B)
         twiddle<T, LOGN - 1>(tab, k, cw, sw);
-        // E = (u1 + conj u2)/2, O = -i (u1 - conj u2)/2
-        C2 E, O;
-        E.x = (T)0.5 * (u1.x + u2.x); E.y = (T)0.5 * (u1.y - u2.y);
-        O.x = (T)0.5 * (u1.y + u2.y); O.y = (T)-0.5 * (u1.x - u2.x);
-        const C2 WO = cmul<T>(O, cw, sw);
-        C2 X1, X2;                         // X_k = E + W O, X_{N-k} = conj(E - W O)
-        X1.x = E.x + WO.x; X1.y = E.y + WO.y;
-        X2.x = E.x - WO.x; X2.y = -(E.y - WO.y);
-        const T h1 = H[k];
-        const T h2 = H[N - k];
-        C2 Z1, Z2;
-        Z1.x = h1 * X1.x; Z1.y = h1 * X1.y;
-        Z2.x = h2 * X2.x; Z2.y = h2 * X2.y;
-        // V1 = (Z1 + conj Z2)/2 + i conj(W) (Z1 - conj Z2)/2
-        // V2 = (Z2 + conj Z1)/2 - i W (Z2 - conj Z1)/2
-        C2 S1, D1, S2, D2;
-        S1.x = (T)0.5 * (Z1.x + Z2.x); S1.y = (T)0.5 * (Z1.y - Z2.y);
-        D1.x = (T)0.5 * (Z1.x - Z2.x); D1.y = (T)0.5 * (Z1.y + Z2.y);
-        S2.x = S1.x; S2.y = -S1.y;
-        D2.x = -D1.x; D2.y = D1.y;
-        // conj(W) = cw + i sw ; i conj(W) D1
         C2 V1, V2;
-        {
-            const T px = cw * D1.x - sw * D1.y;   // conj(W) * D1
-            const T py = cw * D1.y + sw * D1.x;
-            V1.x = S1.x - py; V1.y = S1.y + px;   // + i (px + i py)
-        }
-        {
-            const T px = cw * D2.x + sw * D2.y;   // W * D2
-            const T py = cw * D2.y - sw * D2.x;
-            V2.x = S2.x + py; V2.y = S2.y - px;   // - i (px + i py)
-        }
-        // store conjugates: the forward FFT of conj(V) is conj of N * IFFT(V)
-        V1.y = -V1.y;
-        V2.y = -V2.y;
+        split_product<T>(a[pad<T>(k)], a[pad<T>(k2)], cw, sw, H[k], H[N - k], V1, V2);
         a[pad<T>(k)] = V1;
         if (k2 != k) a[pad<T>(k2)] = V2;
     }
@@ -380,6 +395,91 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     }
 }
 
+// Two-CTA cluster variant: the packed block of N = 2M complex points (B = 4M reals) is
+// split in halves, CTA c holding u[c M + n1].  Forward transform (decimation in
+// frequency): y_0 = u_0 + u_1, y_1 = (u_0 - u_1) W_N^n1 across the pair (distributed
+// shared memory, same local index), then a local M-point FFT leaves X[2 k1 + c] in CTA c.
+// The real-FFT partner N - k of every bin k has the same parity, so the split / product
+// / merge stays inside each CTA.  Inverse (decimation in time): local M-point FFT, then
+// out_c = Z_0 + (-1)^c W_N^n1 Z_1 across the pair, written straight to global memory.
+template <typename T, int LOGM, int NT, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) toeplitz_os2_kernel(TzArgs<T> A) {
+    using C2 = typename Cx<T>::type;
+    constexpr int M = 1 << LOGM;
+    constexpr int N = 2 * M;
+    constexpr int PER = M / NT;
+    static_assert(PER >= 1 && M % NT == 0, "points per thread");
+    if (A.done != nullptr && *(volatile const int*)A.done) return;   // uniform over the pair
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* a = reinterpret_cast<C2*>(smem_raw);
+    C2* rem = cl.map_shared_rank(a, rank ^ 1);
+    const Tile tile = A.tiles[blockIdx.x >> 1];
+    const int tid = threadIdx.x;
+    const int64_t ws = tile.out0 - A.lambda;
+    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M);
+    cl.sync();
+    C2 y[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int n1 = u * NT + tid;
+        const C2 own = a[pad<T>(n1)];
+        const C2 oth = rem[pad<T>(n1)];
+        if (rank == 0) {
+            y[u].x = own.x + oth.x;
+            y[u].y = own.y + oth.y;
+        } else {
+            C2 d;
+            d.x = oth.x - own.x;
+            d.y = oth.y - own.y;
+            T c, s;
+            twiddle<T, LOGM>(A.twiddle, 2 * n1, c, s);   // W_N^n1 = W_B^(2 n1)
+            y[u] = cmul<T>(d, c, s);
+        }
+    }
+    cl.sync();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) a[pad<T>(u * NT + tid)] = y[u];
+    __syncthreads();
+    fft_all<T, LOGM, NT, 0>(a, A.ptw);
+    const T* H = A.H + (int64_t)tile.psd * (N + 1);
+    const int npairs = rank == 0 ? M / 2 + 1 : M / 2;
+    for (int k1 = tid; k1 < npairs; k1 += NT) {
+        const int k = 2 * k1 + rank;
+        const int p = rank == 0 ? ((M - k1) & (M - 1)) : (M - 1 - k1);
+        T cw, sw;
+        twiddle<T, LOGM>(A.twiddle, k, cw, sw);
+        C2 V1, V2;
+        split_product<T>(a[pad<T>(k1)], a[pad<T>(p)], cw, sw, H[k], H[N - k], V1, V2);
+        a[pad<T>(k1)] = V1;
+        if (p != k1) a[pad<T>(p)] = V2;
+    }
+    __syncthreads();
+    fft_all<T, LOGM, NT, 0>(a, A.ptw);
+    cl.sync();
+    T* zo = A.z + tile.out0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int n1 = u * NT + tid;
+        const C2 own = a[pad<T>(n1)];
+        const C2 oth = rem[pad<T>(n1)];
+        const C2 z0 = rank == 0 ? own : oth;
+        T c, s;
+        twiddle<T, LOGM>(A.twiddle, 2 * n1, c, s);
+        const C2 z1 = cmul<T>(rank == 0 ? oth : own, c, s);
+        C2 f;
+        f.x = rank == 0 ? z0.x + z1.x : z0.x - z1.x;
+        f.y = rank == 0 ? z0.y + z1.y : z0.y - z1.y;
+        // packed index m = rank M + n1 -> real samples 2m (f.x) and 2m + 1 (-f.y)
+        const int i0 = 2 * (rank * M + n1) - A.lambda;
+        if (i0 >= 0 && i0 < tile.nout) zo[i0] = f.x;
+        if (i0 + 1 >= 0 && i0 + 1 < tile.nout) zo[i0 + 1] = -f.y;
+    }
+    cl.sync();   // the partner may still read this CTA's shared memory
+}
+
 // Threads per CTA: one largest-radix butterfly per thread and pass (N/16, or N/8 for
 // small N), capped at 1024 for FP32 (16 complex values per thread fit the 64-register
 // budget of a 1024-thread CTA) and 512 for FP64, at least 32.
@@ -388,6 +488,37 @@ __host__ __device__ constexpr int tz_threads() {
     constexpr int cap = sizeof(T) == 4 ? 1024 : 512;
     constexpr int want = (1 << LOGN) >> fft_max_logr<LOGN>();
     return want >= cap ? cap : (want < 32 ? 32 : want);
+}
+
+template <typename T>
+size_t toeplitz2_smem_bytes_impl(int logm) {
+    const size_t M = size_t(1) << logm;
+    return sizeof(typename Cx<T>::type) * (M + (M >> PadLog<T>::v));
+}
+
+template <typename T, int LOGM, int MODE>
+void launch_two(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
+    constexpr int NT = tz_threads<T, LOGM>();
+    const size_t smem = toeplitz2_smem_bytes_impl<T>(LOGM);
+    auto kern = toeplitz_os2_kernel<T, LOGM, NT, MODE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(toeplitz cluster)");
+        attr_set = true;
+    }
+    kern<<<2 * ntiles, NT, smem, s>>>(A);
+    check_cuda(cudaGetLastError(), "toeplitz cluster kernel launch");
+    note_launch();
+}
+
+template <typename T, int LOGM>
+void launch_mode_two(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
+    switch (mode) {
+        case 0: launch_two<T, LOGM, 0>(A, ntiles, s); break;
+        case 1: launch_two<T, LOGM, 1>(A, ntiles, s); break;
+        default: launch_two<T, LOGM, 3>(A, ntiles, s); break;
+    }
 }
 
 template <typename T>

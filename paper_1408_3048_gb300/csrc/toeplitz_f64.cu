@@ -12,6 +12,7 @@ int toeplitz_max_logn<double>() { return 13; }
 template <>
 void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x,
                           double* z, const int* done, cudaStream_t s) {
+    if (tz.logn == 0) throw Error{MM_ERR_ARG, "no FP64 Toeplitz block fits this lambda"};
     if (tz.ntiles == 0) return;
     TzArgs<double> A;
     A.tiles = tz.tiles;
@@ -26,6 +27,12 @@ void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double*
     A.done = done;
     A.lambda = P.lambda;
     const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
+    if (tz.cluster == 2) {
+        switch (tz.logn) {
+            case 14: launch_mode_two<double, 13>(A, tz.ntiles, mode, s); return;
+            default: throw Error{MM_ERR_ARG, "unsupported cluster FFT length"};
+        }
+    }
     switch (tz.logn) {
         case 8: launch_mode<double, 8>(A, tz.ntiles, mode, s); break;
         case 9: launch_mode<double, 9>(A, tz.ntiles, mode, s); break;

@@ -234,3 +234,50 @@ def test_host_buffers_e2e():
     ref = pcg(pr.A, oprec.BlockJacobi(pr).apply, pr.rhs(d), 1e-8, 1000)
     assert _rel(out, ref.x) <= 1e-6 and st.converged == 1
     plan.close()
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_cluster_fft_blocks_forced(ncomp):
+    # blocks one size above the single-CTA maximum run on a two-CTA cluster
+    scan = SCANS["T_ragged" if ncomp == 1 else "P_ragged"]()
+    pr = oracle_problem(scan)
+    plan = _plan(scan, fft_log2=(15, 16))
+    assert plan.fft_block_f64 == 2 ** 15 and plan.fft_block_f32 == 2 ** 16
+    rng = np.random.default_rng(8)
+    t = rng.standard_normal(pr.nt)
+    x = rng.standard_normal(pr.n)
+    for prec, dt, tol in ((mm.MM_FP64, torch.float64, 1e-12), (mm.MM_FP32, torch.float32, 2e-5)):
+        tc = _cuda(t, dt)
+        z = plan.apply_ninv(tc, prec).cpu().numpy()
+        assert _rel(z, pr.Ninv(tc.double().cpu().numpy())) <= tol
+        xc = _cuda(x, dt)
+        y = plan.apply_A(xc, prec).cpu().numpy()
+        assert _rel(y, pr.A(xc.double().cpu().numpy())) <= (tol if prec == mm.MM_FP64 else 3e-5)
+    plan.close()
+
+
+@pytest.mark.parametrize("lam", [8192, 16384])
+def test_long_band_uses_cluster_blocks(lam):
+    # lambda = 8192 (the large polarised workload's band) needs the FP64 cluster block,
+    # lambda = 16384 (the longest batched band) the FP32 one
+    scan = synth.raster_scan(64, 64, 1, 4 * 2 ** 17, 1, 4, lam, [(1.0, 1.0, 1.0)], seed=9)
+    pr = oracle_problem(scan)
+    plan = _plan(scan)
+    if lam == 8192:
+        assert plan.fft_block_f64 == 2 ** 15
+    else:
+        assert plan.fft_block_f32 == 2 ** 16
+        assert plan.fft_block_f64 == 0          # no FP64 block holds this band
+        with pytest.raises(mm.MMError) as e:
+            plan.apply_ninv(_cuda(np.ones(pr.nt)), mm.MM_FP64)
+        assert e.value.status == mm.MM_ERR_ARG
+    rng = np.random.default_rng(lam)
+    t = rng.standard_normal(pr.nt)
+    ref = pr.Ninv(t, route="fft")
+    if lam == 8192:
+        z = plan.apply_ninv(_cuda(t), mm.MM_FP64).cpu().numpy()
+        assert _rel(z, ref) <= 1e-12
+    tc = _cuda(t, torch.float32)
+    z32 = plan.apply_ninv(tc, mm.MM_FP32).cpu().numpy()
+    assert _rel(z32, pr.Ninv(tc.double().cpu().numpy(), route="fft")) <= 2e-5
+    plan.close()
