@@ -1,0 +1,84 @@
+"""Full-size workloads on the GPU against oracle results stored by the golden scripts
+(tests/golden/make_c2_oracle.py, make_c3_oracle.py -- oracle only) and against
+properties that hold at any size.  Needs a GPU; each test takes seconds to a minute.
+
+Tolerances: iteration counts at tolerance within 2 of the oracle's (same algorithm,
+FP64); maps at 1e-6 relative residual within 1e-6 (relative to ||m||) of the oracle's
+sampled values when both run the same FP64 algorithm to the same tolerance.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1408_3048_gb300 import mm, synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _load(name):
+    p = os.path.join(GOLDEN, name)
+    if not os.path.exists(p):
+        pytest.skip(f"{name} not generated")
+    with open(p) as f:
+        return json.load(f)
+
+
+def _plan(scan, **kw):
+    return mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
+                   scan.lam, scan.fsamp, **kw)
+
+
+def _tod(scan, sky_seed, noise_seed):
+    sky = synth.sky_map(scan.npix_sky, scan.ncomp, sky_seed)
+    return synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds, scan.fsamp,
+                                                        noise_seed))
+
+
+def test_polarised_2e24_matches_oracle_iterations_and_map():
+    g = _load("c2_oracle.json")
+    scan = synth.config(2)
+    plan = _plan(scan)
+    assert plan.n == g["n"] and plan.npix_obs == g["npix_obs"]
+    d0 = torch.from_numpy(_tod(scan, 1002, 2200)).cuda()
+    d1 = torch.from_numpy(_tod(scan, 1002, 2201)).cuda()
+    idx = torch.tensor(g["sample_index"], device="cuda")
+    m, st, status = plan.solve(d1, tol=1e-6, maxit=5000, kind=mm.MM_PREC_BD)
+    assert status == mm.MM_OK and abs(st["iters"] - g["iters_bd"]) <= 2
+    err = np.abs(m[idx].cpu().numpy() - np.array(g["m_bd_sample"])).max() / g["m_bd_norm"]
+    assert err <= 1e-6
+    kk, ritz = plan.build_coarse(g["k"], mm.MM_FP64, bprime=plan.rhs(d0), tol=1e-6, maxit=5000)
+    assert kk == g["k_kept"]
+    np.testing.assert_allclose(ritz[:4], g["ritz"][:4], rtol=1e-4)
+    m2, st2, status2 = plan.solve(d1, tol=1e-6, maxit=5000, kind=mm.MM_PREC_TWOLEVEL)
+    assert status2 == mm.MM_OK and abs(st2["iters"] - g["iters_2lvl"]) <= 2
+    err2 = np.abs(m2[idx].cpu().numpy() - np.array(g["m_2lvl_sample"])).max() / g["m_2lvl_norm"]
+    assert err2 <= 1e-6
+    # the mixed-precision two-level solve reaches the same residual target
+    m3, st3, status3 = plan.solve(d1, tol=1e-6, maxit=5000, kind=mm.MM_PREC_TWOLEVEL, solver=mm.MM_SOLVE_MIXED)
+    assert status3 == mm.MM_OK and st3["rel_resid"] <= 1e-6
+    plan.close()
+
+
+def test_temperature_2e27_mixed_precision_error_vs_oracle():
+    g = _load("c3_oracle.json")
+    scan = synth.config(3)
+    plan = _plan(scan)
+    d = torch.from_numpy(_tod(scan, 1003, 2301)).cuda()
+    idx = torch.tensor(g["sample_index"], device="cuda")
+    ref = np.array(g["m_sample"])
+    m64, st64, _ = plan.solve(d, tol=1e-6, maxit=5000)
+    assert abs(st64["iters"] - g["iters_1e-6"]) <= 2
+    errs = {}
+    for tol in (1e-6, 1e-8):
+        m, st, status = plan.solve(d, tol=tol, maxit=5000, solver=mm.MM_SOLVE_MIXED)
+        assert status == mm.MM_OK and st["rel_resid"] <= tol
+        errs[tol] = np.abs(m[idx].cpu().numpy() - ref).max() / np.abs(ref).max()
+    # the error against the oracle's converged map shrinks with the residual target
+    assert errs[1e-8] < errs[1e-6]
+    print(f"\nmixed-precision error vs FP64 oracle map: {errs}")
+    plan.close()
