@@ -82,3 +82,40 @@ def test_temperature_2e27_mixed_precision_error_vs_oracle():
     assert errs[1e-8] < errs[1e-6]
     print(f"\nmixed-precision error vs FP64 oracle map: {errs}")
     plan.close()
+
+
+def test_differentiable_2e29_solve_and_gradient():
+    # 1024 x 768 grid, 64 detectors x 2^23 samples, lambda 8192, two-level k = 64:
+    # properties that hold at any size (the oracle cannot run this size)
+    scan = synth.config(5)
+    assert scan.nt == 2 ** 29
+    plan = _plan(scan, stream=torch.cuda.Stream())
+    frac = plan.npix_obs / scan.npix_sky
+    assert 0.55 <= frac <= 0.65
+    rng = np.random.default_rng(1)
+    x = torch.from_numpy(rng.standard_normal(plan.n)).cuda()
+    y = torch.from_numpy(rng.standard_normal(plan.n)).cuda()
+    Ax, Ay = plan.apply_A(x), plan.apply_A(y)
+    assert abs(float(y @ Ax) - float(x @ Ay)) <= 1e-11 * float(torch.linalg.norm(Ax) * torch.linalg.norm(y))
+    d = torch.from_numpy(_tod(scan, 1005, 2501)).cuda()
+    kk, _ = plan.build_coarse(64, mm.MM_FP32, bprime=plan.rhs(d), tol=1e-6, maxit=5000)
+    assert kk == 64
+    _, st_bd, s1 = plan.solve(d, tol=1e-6, maxit=10000, kind=mm.MM_PREC_BD, solver=mm.MM_SOLVE_MIXED)
+    _, st_2l, s2 = plan.solve(d, tol=1e-6, maxit=10000, kind=mm.MM_PREC_TWOLEVEL, solver=mm.MM_SOLVE_MIXED)
+    assert s1 == s2 == mm.MM_OK and st_2l["iters"] < st_bd["iters"]
+    # adjoint data gradient of L = 1/2 ||m - m_ref||^2 against a central difference
+    mref = torch.from_numpy(rng.standard_normal(plan.n)).cuda()
+    kw = dict(tol=1e-10, maxit=20000, kind=mm.MM_PREC_TWOLEVEL, solver=mm.MM_SOLVE_MIXED)
+    m, _, _ = plan.solve(d, **kw)
+    dd, dp, _ = plan.grad(d, m, m - mref, **kw)
+    assert np.all(np.isfinite(dp))
+    e = torch.from_numpy(rng.standard_normal(plan.nt)).cuda()
+    h = 1e-4 * float(torch.linalg.norm(d)) / float(torch.linalg.norm(e))
+
+    def loss(dv):
+        mm_, _, _ = plan.solve(dv, **kw)
+        return 0.5 * float(torch.sum((mm_ - mref) ** 2))
+
+    fd = (loss(d + h * e) - loss(d - h * e)) / (2 * h)
+    assert fd == pytest.approx(float(dd @ e), rel=1e-3)
+    plan.close()
