@@ -195,22 +195,22 @@ static void destroy_plan(PlanHolder* P) {
     delete P;
 }
 
-// Overlap-save block choice: minimise tiles x (B log2 B + 4096) over admissible blocks,
-// the largest one on a two-CTA cluster (weighted 1.1 for its cross-CTA steps).
-// Returns logn; sets *cluster to 1 or 2.
+// Overlap-save block choice: minimise tiles x (B log2 B + 4096) over admissible blocks;
+// the two blocks above the single-CTA maximum run on 2- and 4-CTA clusters (weighted
+// 1.1 and 1.25 for their cross-CTA steps).  Returns logn; sets *cluster to 1, 2 or 4.
 template <typename T>
 static int choose_logn(const Plan& P, int forced_log2B, int* cluster) {
     const int maxl = toeplitz_max_logn<T>();
     if (forced_log2B > 0) {
         const int logn = forced_log2B - 1;
-        if (logn < 8 || logn > maxl + 1) throw Error{MM_ERR_ARG, "fft block size out of range"};
+        if (logn < 8 || logn > maxl + 2) throw Error{MM_ERR_ARG, "fft block size out of range"};
         if ((int64_t(2) << logn) - 2 * (int64_t)P.lambda < 1) throw Error{MM_ERR_ARG, "fft block too short for lambda"};
-        *cluster = logn > maxl ? 2 : 1;
+        *cluster = logn > maxl ? 1 << (logn - maxl) : 1;
         return logn;
     }
     int best = -1;
     double best_cost = 0.0;
-    for (int logn = 8; logn <= maxl + 1; ++logn) {
+    for (int logn = 8; logn <= maxl + 2; ++logn) {
         const int64_t B = int64_t(2) << logn;
         const int64_t Lv = B - 2 * (int64_t)P.lambda;
         if (Lv < 1) continue;
@@ -219,14 +219,15 @@ static int choose_logn(const Plan& P, int forced_log2B, int* cluster) {
             const int64_t len = P.h_ioff[i + 1] - P.h_ioff[i];
             tiles += (len + Lv - 1) / Lv;
         }
-        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0) * (logn > maxl ? 1.1 : 1.0);
+        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0) *
+                            (logn > maxl + 1 ? 1.25 : (logn > maxl ? 1.1 : 1.0));
         if (best < 0 || cost < best_cost) {
             best = logn;
             best_cost = cost;
         }
     }
     if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the largest FFT block"};
-    *cluster = best > maxl ? 2 : 1;
+    *cluster = best > maxl ? 1 << (best - maxl) : 1;
     return best;
 }
 
@@ -258,7 +259,8 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     h2d(tz.twiddle, tw.data(), tw.size() * sizeof(T), P.stream);
     {
         // the cluster kernel runs local FFTs of half the length
-        const std::vector<double> pt = pass_twiddle_table(tz.cluster == 2 ? tz.logn - 1 : tz.logn);
+        const int lc = tz.cluster == 4 ? 2 : (tz.cluster == 2 ? 1 : 0);
+        const std::vector<double> pt = pass_twiddle_table(tz.logn - lc);
         std::vector<T> ptT(pt.begin(), pt.end());
         tz.ptw = dalloc<T>(ptT.size());
         h2d(tz.ptw, ptT.data(), ptT.size() * sizeof(T), P.stream);

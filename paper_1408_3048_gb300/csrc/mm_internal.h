@@ -25,7 +25,7 @@ struct Tile {
 // Device tables of one arithmetic precision (T = double or float).
 struct ToeplitzDev {
     int logn = 0;            // complex FFT length N = 2^logn, real block B = 2N
-    int cluster = 1;         // CTAs per tile (2: split across a two-CTA cluster)
+    int cluster = 1;         // CTAs per tile (2 or 4: split across a thread-block cluster)
     int ntiles = 0;
     Tile* tiles = nullptr;   // [ntiles]
     void* twiddle = nullptr; // T[B/4 + 1]: cos(2 pi k / B)
@@ -170,7 +170,7 @@ void launch_toeplitz(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const
 template <typename T>
 size_t toeplitz_smem_bytes(int logn);
 template <typename T>
-int toeplitz_max_logn();          // largest single-CTA FFT (the cluster kernel adds one)
+int toeplitz_max_logn();          // largest single-CTA FFT (the cluster kernels add one or two)
 
 // pointing (pointing.cu)
 template <typename T>

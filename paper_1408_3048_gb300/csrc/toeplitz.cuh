@@ -395,28 +395,47 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     }
 }
 
-// Two-CTA cluster variant: the packed block of N = 2M complex points (B = 4M reals) is
-// split in halves, CTA c holding u[c M + n1].  Forward transform (decimation in
-// frequency): y_0 = u_0 + u_1, y_1 = (u_0 - u_1) W_N^n1 across the pair (distributed
-// shared memory, same local index), then a local M-point FFT leaves X[2 k1 + c] in CTA c.
-// The real-FFT partner N - k of every bin k has the same parity, so the split / product
-// / merge stays inside each CTA.  Inverse (decimation in time): local M-point FFT, then
-// out_c = Z_0 + (-1)^c W_N^n1 Z_1 across the pair, written straight to global memory.
-template <typename T, int LOGM, int NT, int MODE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) toeplitz_os2_kernel(TzArgs<T> A) {
+// v * W_C^m for C in {2, 4} (m taken mod C): multiplications by +-1, +-i only.
+template <typename T, int C>
+__device__ __forceinline__ typename Cx<T>::type rot_c(typename Cx<T>::type v, int m) {
+    typename Cx<T>::type r;
+    const int q = (C == 2 ? 2 * m : m) & 3;   // power of W_4 = -i
+    switch (q) {
+        case 0: r = v; break;
+        case 1: r.x = v.y; r.y = -v.x; break;    // * (-i)
+        case 2: r.x = -v.x; r.y = -v.y; break;
+        default: r.x = -v.y; r.y = v.x; break;   // * (+i)
+    }
+    return r;
+}
+
+// Cluster variant (C = 2 or 4 CTAs): the packed block of N = C M complex points (B = 2N
+// reals) is split in C chunks, CTA c holding u[c M + n1].  Forward transform (decimation
+// in frequency): y_c[n1] = W_N^(n1 c) sum_n2 u_n2[n1] W_C^(n2 c) across the cluster
+// (distributed shared memory, same local index in every CTA), then a local M-point FFT
+// leaves X[C k1 + c] in CTA c.  The real-FFT partner N - k of bin k lies in CTA (C - c)
+// mod C: the same CTA for c = 0 (and c = C/2), the opposite one of the pair (1, 3) when
+// C = 4, read there across the cluster.  Inverse (decimation in time): local M-point FFT,
+// then out_c[n1] = sum_m2 W_C^(m2 c) W_N^(m2 n1) Z_m2[n1] across the cluster, written
+// straight to global memory.
+template <typename T, int LOGM, int NT, int MODE, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_kernel(TzArgs<T> A) {
     using C2 = typename Cx<T>::type;
     constexpr int M = 1 << LOGM;
-    constexpr int N = 2 * M;
+    constexpr int N = CL * M;
+    constexpr int LOGQ = LOGM + (CL == 2 ? 0 : 1);   // B/4 = N/2 = 2^LOGQ
     constexpr int PER = M / NT;
     static_assert(PER >= 1 && M % NT == 0, "points per thread");
-    if (A.done != nullptr && *(volatile const int*)A.done) return;   // uniform over the pair
+    if (A.done != nullptr && *(volatile const int*)A.done) return;   // uniform over the cluster
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
-    C2* rem = cl.map_shared_rank(a, rank ^ 1);
-    const Tile tile = A.tiles[blockIdx.x >> 1];
+    C2* part[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) part[c] = cl.map_shared_rank(a, c);
+    const Tile tile = A.tiles[blockIdx.x / CL];
     const int tid = threadIdx.x;
     const int64_t ws = tile.out0 - A.lambda;
     load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M);
@@ -425,19 +444,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) toeplitz_os2_ker
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int n1 = u * NT + tid;
-        const C2 own = a[pad<T>(n1)];
-        const C2 oth = rem[pad<T>(n1)];
-        if (rank == 0) {
-            y[u].x = own.x + oth.x;
-            y[u].y = own.y + oth.y;
-        } else {
-            C2 d;
-            d.x = oth.x - own.x;
-            d.y = oth.y - own.y;
-            T c, s;
-            twiddle<T, LOGM>(A.twiddle, 2 * n1, c, s);   // W_N^n1 = W_B^(2 n1)
-            y[u] = cmul<T>(d, c, s);
+        C2 acc = part[0][pad<T>(n1)];
+#pragma unroll
+        for (int n2 = 1; n2 < CL; ++n2) {
+            const C2 v = rot_c<T, CL>(part[n2][pad<T>(n1)], n2 * rank);
+            acc.x += v.x;
+            acc.y += v.y;
         }
+        if (rank != 0) {
+            T c, s;
+            twiddle<T, LOGQ>(A.twiddle, 2 * n1 * rank, c, s);   // W_N^(n1 rank) = W_B^(2 n1 rank)
+            acc = cmul<T>(acc, c, s);
+        }
+        y[u] = acc;
     }
     cl.sync();
 #pragma unroll
@@ -445,16 +464,38 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) toeplitz_os2_ker
     __syncthreads();
     fft_all<T, LOGM, NT, 0>(a, A.ptw);
     const T* H = A.H + (int64_t)tile.psd * (N + 1);
-    const int npairs = rank == 0 ? M / 2 + 1 : M / 2;
-    for (int k1 = tid; k1 < npairs; k1 += NT) {
-        const int k = 2 * k1 + rank;
-        const int p = rank == 0 ? ((M - k1) & (M - 1)) : (M - 1 - k1);
-        T cw, sw;
-        twiddle<T, LOGM>(A.twiddle, k, cw, sw);
-        C2 V1, V2;
-        split_product<T>(a[pad<T>(k1)], a[pad<T>(p)], cw, sw, H[k], H[N - k], V1, V2);
-        a[pad<T>(k1)] = V1;
-        if (p != k1) a[pad<T>(p)] = V2;
+    const int prank = (CL - rank) % CL;
+    if (prank == rank) {
+        // partner bins inside this CTA: process each pair once
+        const int npairs = rank == 0 ? M / 2 + 1 : M / 2;
+        for (int k1 = tid; k1 < npairs; k1 += NT) {
+            const int k = CL * k1 + rank;
+            const int p = rank == 0 ? ((M - k1) & (M - 1)) : (M - 1 - k1);
+            T cw, sw;
+            twiddle<T, LOGQ>(A.twiddle, k, cw, sw);
+            C2 V1, V2;
+            split_product<T>(a[pad<T>(k1)], a[pad<T>(p)], cw, sw, H[k], H[N - k], V1, V2);
+            a[pad<T>(k1)] = V1;
+            if (p != k1) a[pad<T>(p)] = V2;
+        }
+        cl.sync();
+        cl.sync();
+    } else {
+        // partner bins in CTA prank (C = 4, ranks 1 and 3): compute this CTA's bins only
+        C2 vo[PER];
+        cl.sync();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k1 = u * NT + tid;
+            const int k = CL * k1 + rank;
+            T cw, sw;
+            twiddle<T, LOGQ>(A.twiddle, k, cw, sw);
+            C2 V2;
+            split_product<T>(a[pad<T>(k1)], part[prank][pad<T>(M - 1 - k1)], cw, sw, H[k], H[N - k], vo[u], V2);
+        }
+        cl.sync();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) a[pad<T>(u * NT + tid)] = vo[u];
     }
     __syncthreads();
     fft_all<T, LOGM, NT, 0>(a, A.ptw);
@@ -463,21 +504,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) toeplitz_os2_ker
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int n1 = u * NT + tid;
-        const C2 own = a[pad<T>(n1)];
-        const C2 oth = rem[pad<T>(n1)];
-        const C2 z0 = rank == 0 ? own : oth;
-        T c, s;
-        twiddle<T, LOGM>(A.twiddle, 2 * n1, c, s);
-        const C2 z1 = cmul<T>(rank == 0 ? oth : own, c, s);
-        C2 f;
-        f.x = rank == 0 ? z0.x + z1.x : z0.x - z1.x;
-        f.y = rank == 0 ? z0.y + z1.y : z0.y - z1.y;
+        C2 f = part[0][pad<T>(n1)];
+#pragma unroll
+        for (int m2 = 1; m2 < CL; ++m2) {
+            T c, s;
+            twiddle<T, LOGQ>(A.twiddle, 2 * n1 * m2, c, s);   // W_N^(m2 n1)
+            const C2 v = rot_c<T, CL>(cmul<T>(part[m2][pad<T>(n1)], c, s), m2 * rank);
+            f.x += v.x;
+            f.y += v.y;
+        }
         // packed index m = rank M + n1 -> real samples 2m (f.x) and 2m + 1 (-f.y)
         const int i0 = 2 * (rank * M + n1) - A.lambda;
         if (i0 >= 0 && i0 < tile.nout) zo[i0] = f.x;
         if (i0 + 1 >= 0 && i0 + 1 < tile.nout) zo[i0 + 1] = -f.y;
     }
-    cl.sync();   // the partner may still read this CTA's shared memory
+    cl.sync();   // the other CTAs may still read this CTA's shared memory
 }
 
 // Threads per CTA: one largest-radix butterfly per thread and pass (N/16, or N/8 for
@@ -496,28 +537,28 @@ size_t toeplitz2_smem_bytes_impl(int logm) {
     return sizeof(typename Cx<T>::type) * (M + (M >> PadLog<T>::v));
 }
 
-template <typename T, int LOGM, int MODE>
-void launch_two(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
+template <typename T, int LOGM, int MODE, int CL>
+void launch_cl(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<T, LOGM>();
     const size_t smem = toeplitz2_smem_bytes_impl<T>(LOGM);
-    auto kern = toeplitz_os2_kernel<T, LOGM, NT, MODE>;
+    auto kern = toeplitz_oscl_kernel<T, LOGM, NT, MODE, CL>;
     static bool attr_set = false;
     if (!attr_set) {
         check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                    "cudaFuncSetAttribute(toeplitz cluster)");
         attr_set = true;
     }
-    kern<<<2 * ntiles, NT, smem, s>>>(A);
+    kern<<<CL * ntiles, NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz cluster kernel launch");
     note_launch();
 }
 
-template <typename T, int LOGM>
-void launch_mode_two(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
+template <typename T, int LOGM, int CL>
+void launch_mode_cl(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
     switch (mode) {
-        case 0: launch_two<T, LOGM, 0>(A, ntiles, s); break;
-        case 1: launch_two<T, LOGM, 1>(A, ntiles, s); break;
-        default: launch_two<T, LOGM, 3>(A, ntiles, s); break;
+        case 0: launch_cl<T, LOGM, 0, CL>(A, ntiles, s); break;
+        case 1: launch_cl<T, LOGM, 1, CL>(A, ntiles, s); break;
+        default: launch_cl<T, LOGM, 3, CL>(A, ntiles, s); break;
     }
 }
 

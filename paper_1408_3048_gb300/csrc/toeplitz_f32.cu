@@ -27,12 +27,15 @@ void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y
     A.done = done;
     A.lambda = P.lambda;
     const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
-    if (tz.cluster == 2) {
-        switch (tz.logn) {
-            case 15: launch_mode_two<float, 14>(A, tz.ntiles, mode, s); return;
-            default: throw Error{MM_ERR_ARG, "unsupported cluster FFT length"};
-        }
+    if (tz.cluster == 2 && tz.logn == 15) {
+        launch_mode_cl<float, 14, 2>(A, tz.ntiles, mode, s);
+        return;
     }
+    if (tz.cluster == 4 && tz.logn == 16) {
+        launch_mode_cl<float, 14, 4>(A, tz.ntiles, mode, s);
+        return;
+    }
+    if (tz.cluster != 1) throw Error{MM_ERR_ARG, "unsupported cluster FFT length"};
     switch (tz.logn) {
         case 8: launch_mode<float, 8>(A, tz.ntiles, mode, s); break;
         case 9: launch_mode<float, 9>(A, tz.ntiles, mode, s); break;

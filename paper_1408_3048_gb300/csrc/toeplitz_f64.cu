@@ -27,12 +27,15 @@ void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double*
     A.done = done;
     A.lambda = P.lambda;
     const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
-    if (tz.cluster == 2) {
-        switch (tz.logn) {
-            case 14: launch_mode_two<double, 13>(A, tz.ntiles, mode, s); return;
-            default: throw Error{MM_ERR_ARG, "unsupported cluster FFT length"};
-        }
+    if (tz.cluster == 2 && tz.logn == 14) {
+        launch_mode_cl<double, 13, 2>(A, tz.ntiles, mode, s);
+        return;
     }
+    if (tz.cluster == 4 && tz.logn == 15) {
+        launch_mode_cl<double, 13, 4>(A, tz.ntiles, mode, s);
+        return;
+    }
+    if (tz.cluster != 1) throw Error{MM_ERR_ARG, "unsupported cluster FFT length"};
     switch (tz.logn) {
         case 8: launch_mode<double, 8>(A, tz.ntiles, mode, s); break;
         case 9: launch_mode<double, 9>(A, tz.ntiles, mode, s); break;

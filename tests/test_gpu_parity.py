@@ -237,12 +237,14 @@ def test_host_buffers_e2e():
 
 
 @pytest.mark.parametrize("ncomp", [1, 3])
-def test_cluster_fft_blocks_forced(ncomp):
-    # blocks one size above the single-CTA maximum run on a two-CTA cluster
+@pytest.mark.parametrize("cl", [2, 4])
+def test_cluster_fft_blocks_forced(ncomp, cl):
+    # blocks one and two sizes above the single-CTA maximum run on 2- and 4-CTA clusters
     scan = SCANS["T_ragged" if ncomp == 1 else "P_ragged"]()
     pr = oracle_problem(scan)
-    plan = _plan(scan, fft_log2=(15, 16))
-    assert plan.fft_block_f64 == 2 ** 15 and plan.fft_block_f32 == 2 ** 16
+    lb = 14 + cl // 2
+    plan = _plan(scan, fft_log2=(lb, lb + 1))
+    assert plan.fft_block_f64 == 2 ** lb and plan.fft_block_f32 == 2 ** (lb + 1)
     rng = np.random.default_rng(8)
     t = rng.standard_normal(pr.nt)
     x = rng.standard_normal(pr.n)
@@ -256,25 +258,24 @@ def test_cluster_fft_blocks_forced(ncomp):
     plan.close()
 
 
-@pytest.mark.parametrize("lam", [8192, 16384])
+@pytest.mark.parametrize("lam", [8192, 16384, 40000])
 def test_long_band_uses_cluster_blocks(lam):
-    # lambda = 8192 (the large polarised workload's band) needs the FP64 cluster block,
-    # lambda = 16384 (the longest batched band) the FP32 one
+    # lambda = 8192 (the large polarised workload's band) needs a cluster FP64 block,
+    # lambda = 16384 (the longest batched band) the four-CTA FP64 block, and
+    # lambda = 40000 exceeds every FP64 block (2^16 reals) but fits the four-CTA FP32 one
     scan = synth.raster_scan(64, 64, 1, 4 * 2 ** 17, 1, 4, lam, [(1.0, 1.0, 1.0)], seed=9)
     pr = oracle_problem(scan)
     plan = _plan(scan)
-    if lam == 8192:
-        assert plan.fft_block_f64 == 2 ** 15
-    else:
-        assert plan.fft_block_f32 == 2 ** 16
-        assert plan.fft_block_f64 == 0          # no FP64 block holds this band
+    assert plan.fft_block_f64 in {8192: (2 ** 15, 2 ** 16), 16384: (2 ** 16,), 40000: (0,)}[lam]
+    assert plan.fft_block_f32 in {8192: (2 ** 15, 2 ** 16, 2 ** 17), 16384: (2 ** 16, 2 ** 17), 40000: (2 ** 17,)}[lam]
+    if lam == 40000:
         with pytest.raises(mm.MMError) as e:
             plan.apply_ninv(_cuda(np.ones(pr.nt)), mm.MM_FP64)
         assert e.value.status == mm.MM_ERR_ARG
     rng = np.random.default_rng(lam)
     t = rng.standard_normal(pr.nt)
     ref = pr.Ninv(t, route="fft")
-    if lam == 8192:
+    if lam != 40000:
         z = plan.apply_ninv(_cuda(t), mm.MM_FP64).cpu().numpy()
         assert _rel(z, ref) <= 1e-12
     tc = _cuda(t, torch.float32)
