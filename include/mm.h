@@ -68,9 +68,9 @@ typedef struct {
     int32_t ncomp;          /* 1 (temperature) or 3 (I, Q, U)                             */
     int32_t lambda;         /* Toeplitz half bandwidth: lags |k| <= lambda are kept       */
     int32_t window;         /* MM_WINDOW_GAUSS (default) or MM_WINDOW_RECT                */
-    int32_t fft_log2_f64;   /* 0: automatic; else overlap-save block 2^v for FP64 (9..14) */
-    int32_t fft_log2_f32;   /* 0: automatic; else overlap-save block 2^v for FP32 (9..15) */
-    int32_t reserved;
+    int32_t fft_log2_f64;   /* 0: automatic; else overlap-save block 2^v for FP64 (9..16) */
+    int32_t fft_log2_f32;   /* 0: automatic; else overlap-save block 2^v for FP32 (9..17) */
+    int32_t autotune;       /* 0: blocks by cost model; 1: time candidates, keep fastest  */
     double fsamp;           /* sampling frequency in Hz (> 0)                             */
     double rcond_min;       /* I/Q/U pixel acceptance (<= 0: 1e-6), see mm_plan           */
     void* stream;           /* cudaStream_t; NULL = legacy default stream                 */
@@ -127,6 +127,31 @@ mm_status mm_plan(mm_plan_t* out, const int32_t* pix, int64_t nt, int32_t npix_s
 /* Sizes of a plan.  Any output pointer may be NULL.  n = npix_obs * ncomp. */
 mm_status mm_plan_info(mm_plan_t plan, int32_t* npix_obs, int64_t* n, int64_t* nkept,
                        int32_t* fft_block_f64, int32_t* fft_block_f32);
+
+/*
+ * Autotuning record (plans built with opts.autotune = 1; the paper has no counterpart).
+ * ms_f64[v - 9] / ms_f32[v - 9]: average device milliseconds of one de-pointing Toeplitz
+ * launch with the 2^v-real overlap-save block (v = 9..24), 0 for blocks not timed; at
+ * most the three cheapest blocks of the cost model are timed per precision, the fastest
+ * is kept.  Either pointer (host float[16]) may be NULL.
+ */
+mm_status mm_autotune_read(mm_plan_t plan, float* ms_f64, float* ms_f32);
+
+/*
+ * Form of the batched operator (mm_apply_A_batch, mm_solve_batch), fixed once per plan by
+ * its first batched call or by this call; the paper has no counterpart.
+ *   kind  (host, in/out) in: -1 = choose, 0 or 1 = use that form; out: the form in use.
+ *         0: two right-hand sides per complex FFT of 2^log2_block points (real kernel
+ *         spectrum: real and imaginary parts convolve independently);
+ *         1: one real FFT per right-hand side with the FP32 block of mm_plan_info, the
+ *         right-hand side as the fastest grid index.
+ *         Choosing times both forms at R columns when the plan autotunes, else takes the
+ *         cheaper by the cost model.  Asking for a form other than the fixed one, or one
+ *         that no block supports for this lambda, is MM_ERR_ARG.
+ *   R     1..64, the column count for the timing (and the buffers it allocates).
+ *   log2_block, ms (host float[2]: timed launches of forms 0 and 1, or 0): may be NULL.
+ */
+mm_status mm_batch_config(mm_plan_t plan, int32_t R, int32_t* kind, int32_t* log2_block, float* ms);
 
 /* obs2sky[q] (sky index of observed pixel q) and hits[q] (its sample count), both
  * host or device int32[npix_obs]; either may be NULL.  Bit-exact integer outputs. */

@@ -106,12 +106,17 @@ void prof_flush(Plan& P) {
 
 // ----------------------------------------------------------------------------- plan
 // Buffers of the batched (many right-hand sides) solver, allocated on first use.
+enum { BATCH_PAIR = 0, BATCH_REAL = 1 };
+
 struct BatchState {
-    int logb = 0;                 // complex FFT length of the batched Toeplitz kernel
+    int kind = -1;                // BATCH_PAIR / BATCH_REAL, -1 before the first batched call
+    float tuned_ms[2] = {};       // timed forms (autotuning), 0 when not timed
+    int logb = 0;                 // complex FFT length of the pair kernel
     int ntiles = 0;
     Tile* tiles = nullptr;
     float* H = nullptr;           // [npsd][B/2 + 1] / B
-    float* ptw = nullptr;         // per-pass FFT twiddles of the B-point transform
+    float* ptw = nullptr;         // per-pass FFT twiddles of the per-CTA transform
+    float* twiddle = nullptr;     // cos(2 pi k / B), k = 0..B/4 (cluster blocks)
     int cap = 0;                  // right-hand sides the vectors below hold
     float *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *tod = nullptr;
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
@@ -140,6 +145,9 @@ struct PlanHolder : Plan {
     double* r64 = nullptr;      // [n] refinement residual
     double* ax64 = nullptr;     // [n]
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    bool autotune = false;      // measured block / batched-kernel choice (mm_opts.autotune)
+    float tuned_ms64[16] = {};  // timed candidates by logn - 8 (0: not tried)
+    float tuned_ms32[16] = {};
 };
 
 static void free_tz(ToeplitzDev& t) {
@@ -187,7 +195,8 @@ static void destroy_plan(PlanHolder* P) {
     for (auto e : P->prof.pool) (void)cudaEventDestroy(e);
     BatchState& bt = P->batch;
     if (bt.graph) (void)cudaGraphExecDestroy(bt.graph);
-    for (void* p : {(void*)bt.tiles, (void*)bt.H, (void*)bt.ptw, (void*)bt.x, (void*)bt.r, (void*)bt.p, (void*)bt.q, (void*)bt.z,
+    for (void* p : {(void*)bt.tiles, (void*)bt.H, (void*)bt.ptw, (void*)bt.twiddle, (void*)bt.x, (void*)bt.r,
+                    (void*)bt.p, (void*)bt.q, (void*)bt.z,
                     (void*)bt.tod, (void*)bt.x64, (void*)bt.b64, (void*)bt.r64, (void*)bt.partial, (void*)bt.rho,
                     (void*)bt.bb, (void*)bt.rr, (void*)bt.tol2, (void*)bt.iters, (void*)bt.state, (void*)bt.flags,
                     (void*)bt.bar})
@@ -195,40 +204,61 @@ static void destroy_plan(PlanHolder* P) {
     delete P;
 }
 
-// Overlap-save block choice: minimise tiles x (B log2 B + 4096) over admissible blocks;
-// the two blocks above the single-CTA maximum run on 2- and 4-CTA clusters (weighted
-// 1.1 and 1.25 for their cross-CTA steps).  Returns logn; sets *cluster to 1, 2 or 4.
+// Cost of a block relative to its FFT operation count, from launch timings of every
+// admissible block on polarised scans of 2^24-2^25 samples with lambda = 1024, 4096,
+// 8192 and 16384.  FP64 kernels are bound by the FP64 pipe, so the cross-CTA steps of a
+// 2-CTA cluster cost little; the largest single-CTA FP64 block (2^14 reals) runs one
+// 512-thread CTA per SM.  FP32 kernels are bound by shared-memory and L1 latency, where
+// the cluster steps (distributed shared memory) cost more.  The batched complex-pair
+// blocks are FP32 and take the FP32 weights by cluster size.
+static double fp32_cluster_weight(int cluster) { return cluster == 4 ? 3.3 : (cluster == 2 ? 1.6 : 1.0); }
+template <typename T>
+static double block_weight(int logn);
+template <>
+double block_weight<double>(int logn) { return logn >= 15 ? 2.0 : (logn == 14 ? 1.2 : (logn == 13 ? 1.12 : 1.0)); }
+template <>
+double block_weight<float>(int logn) { return fp32_cluster_weight(logn >= 16 ? 4 : (logn == 15 ? 2 : 1)); }
+
+static int64_t overlap_tiles(const Plan& P, int64_t Lv) {
+    int64_t tiles = 0;
+    for (int i = 0; i < P.K; ++i) tiles += (P.h_ioff[i + 1] - P.h_ioff[i] + Lv - 1) / Lv;
+    return tiles;
+}
+
+// Admissible overlap-save blocks (B = 2^(logn+1) reals > 2 lambda) ordered by the cost
+// model tiles x (N (logn + 1) + 2048) x block weight; the two blocks above the
+// single-CTA maximum run on 2- and 4-CTA clusters.
+template <typename T>
+static std::vector<std::pair<double, int>> block_candidates(const Plan& P) {
+    const int maxl = toeplitz_max_logn<T>();
+    std::vector<std::pair<double, int>> c;
+    for (int logn = 8; logn <= maxl + 2; ++logn) {
+        const int64_t N = int64_t(1) << logn;
+        const int64_t Lv = 2 * N - 2 * (int64_t)P.lambda;
+        if (Lv < 1) continue;
+        c.push_back({(double)overlap_tiles(P, Lv) * ((double)N * (logn + 1) + 2048.0) * block_weight<T>(logn), logn});
+    }
+    std::stable_sort(c.begin(), c.end());
+    return c;
+}
+
+// Block choice: forced (log2 of the real block), else the cheapest candidate.  Returns
+// logn; sets *cluster to 1, 2 or 4.
 template <typename T>
 static int choose_logn(const Plan& P, int forced_log2B, int* cluster) {
     const int maxl = toeplitz_max_logn<T>();
+    int logn;
     if (forced_log2B > 0) {
-        const int logn = forced_log2B - 1;
+        logn = forced_log2B - 1;
         if (logn < 8 || logn > maxl + 2) throw Error{MM_ERR_ARG, "fft block size out of range"};
         if ((int64_t(2) << logn) - 2 * (int64_t)P.lambda < 1) throw Error{MM_ERR_ARG, "fft block too short for lambda"};
-        *cluster = logn > maxl ? 1 << (logn - maxl) : 1;
-        return logn;
+    } else {
+        const auto c = block_candidates<T>(P);
+        if (c.empty()) throw Error{MM_ERR_ARG, "lambda too large for the largest FFT block"};
+        logn = c[0].second;
     }
-    int best = -1;
-    double best_cost = 0.0;
-    for (int logn = 8; logn <= maxl + 2; ++logn) {
-        const int64_t B = int64_t(2) << logn;
-        const int64_t Lv = B - 2 * (int64_t)P.lambda;
-        if (Lv < 1) continue;
-        int64_t tiles = 0;
-        for (int i = 0; i < P.K; ++i) {
-            const int64_t len = P.h_ioff[i + 1] - P.h_ioff[i];
-            tiles += (len + Lv - 1) / Lv;
-        }
-        const double cost = (double)tiles * ((double)B * (logn + 1) + 4096.0) *
-                            (logn > maxl + 1 ? 1.25 : (logn > maxl ? 1.1 : 1.0));
-        if (best < 0 || cost < best_cost) {
-            best = logn;
-            best_cost = cost;
-        }
-    }
-    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the largest FFT block"};
-    *cluster = best > maxl ? 1 << (best - maxl) : 1;
-    return best;
+    *cluster = logn > maxl ? 1 << (logn - maxl) : 1;
+    return logn;
 }
 
 template <typename T>
@@ -274,6 +304,51 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     tz.H = dalloc<T>(H.size());
     h2d(tz.H, H.data(), H.size() * sizeof(T), P.stream);
     sync(P.stream);   // host vectors go out of scope
+}
+
+// Average milliseconds of `reps` launches of f on the plan's stream (one untimed first).
+template <typename F>
+static float time_launches(PlanHolder& P, F&& f, int reps) {
+    f();
+    check_cuda(cudaEventRecord(P.ev0, P.stream), "event");
+    for (int i = 0; i < reps; ++i) f();
+    check_cuda(cudaEventRecord(P.ev1, P.stream), "event");
+    check_cuda(cudaEventSynchronize(P.ev1), "event sync");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, P.ev0, P.ev1), "event time");
+    return ms / (float)reps;
+}
+
+// Measured block choice: the (up to) three cheapest candidates of the cost model are built
+// and their de-pointing launch (the one inside A x) is timed on a zero map; the fastest
+// stays in tz.  Timings go to tuned_ms (0 for candidates not tried).
+template <typename T>
+static void autotune_toeplitz(PlanHolder& P, ToeplitzDev& tz, T* tod, const T* zmap, float* tuned_ms) {
+    const auto c = block_candidates<T>(P);
+    if (c.size() < 2) return;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < c.size() && i < 3; ++i) {
+        ToeplitzDev cand;
+        if (c[i].second == tz.logn) {
+            cand = tz;
+        } else {
+            build_toeplitz<T>(P, cand, c[i].second + 1);
+        }
+        const float ms =
+            time_launches(P, [&] { launch_toeplitz<T>(P, cand, nullptr, zmap, tod, nullptr, P.stream); }, 3);
+        tuned_ms[c[i].second - 8] = ms;
+        if (cand.logn == tz.logn) {
+            if (best_ms == 0.f || ms < best_ms) best_ms = ms;
+            continue;
+        }
+        if (ms < best_ms || best_ms == 0.f) {
+            free_tz(tz);
+            tz = cand;
+            best_ms = ms;
+        } else {
+            free_tz(cand);
+        }
+    }
 }
 
 static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t npix_sky, const double* weights,
@@ -471,6 +546,14 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     check_cuda(cudaEventCreate(&P.ev0), "event");
     check_cuda(cudaEventCreate(&P.ev1), "event");
     check_cuda(cudaEventCreate(&P.ev2), "event");
+    P.autotune = o->autotune != 0;
+    if (P.autotune) {
+        // zero maps for the timed launches (x64 / the first half of r64 as FP32)
+        check_cuda(cudaMemsetAsync(P.x64, 0, (size_t)P.n * 8, s), "memset");
+        if (P.tz64.logn != 0 && o->fft_log2_f64 <= 0) autotune_toeplitz<double>(P, P.tz64, P.tod64, P.x64, P.tuned_ms64);
+        if (P.tz32.logn != 0 && o->fft_log2_f32 <= 0)
+            autotune_toeplitz<float>(P, P.tz32, P.tod32, reinterpret_cast<const float*>(P.x64), P.tuned_ms32);
+    }
     sync(s);
 }
 
@@ -947,26 +1030,11 @@ static void grad(PlanHolder& P, const double* d, const double* m, const double* 
 
 
 // ------------------------------------------------------------------ batched solver
-static void ensure_batch_tables(PlanHolder& P) {
+// Complex-pair kernel tables for a 2^logb-point block.
+static void build_batch_pair(PlanHolder& P, int logb) {
     BatchState& bt = P.batch;
-    if (bt.tiles != nullptr) return;
-    int best = -1;
-    double best_cost = 0.0;
-    for (int logb = 9; logb <= 14; ++logb) {
-        const int64_t B = int64_t(1) << logb;
-        const int64_t Lv = B - 2 * (int64_t)P.lambda;
-        if (Lv < 1) continue;
-        int64_t tiles = 0;
-        for (int i = 0; i < P.K; ++i) tiles += (P.h_ioff[i + 1] - P.h_ioff[i] + Lv - 1) / Lv;
-        const double cost = (double)tiles * ((double)B * logb + 4096.0);
-        if (best < 0 || cost < best_cost) {
-            best = logb;
-            best_cost = cost;
-        }
-    }
-    if (best < 0) throw Error{MM_ERR_ARG, "lambda too large for the batched shared-memory FFT block"};
-    bt.logb = best;
-    const int64_t B = int64_t(1) << best;
+    bt.logb = logb;
+    const int64_t B = int64_t(1) << logb;
     const int64_t Lv = B - 2 * (int64_t)P.lambda;
     std::vector<Tile> tiles;
     for (int i = 0; i < P.K; ++i) {
@@ -992,11 +1060,71 @@ static void ensure_batch_tables(PlanHolder& P) {
     }
     bt.H = dalloc<float>(H.size());
     h2d(bt.H, H.data(), H.size() * 4, P.stream);
-    const std::vector<double> pt = pass_twiddle_table(best);
+    const std::vector<double> pt = pass_twiddle_table(std::min(logb, BATCH_MAX_LOGB_CTA));
     std::vector<float> ptf(pt.begin(), pt.end());
     bt.ptw = dalloc<float>(ptf.size());
     h2d(bt.ptw, ptf.data(), ptf.size() * 4, P.stream);
+    std::vector<float> tw((size_t)(B / 4 + 1));
+    for (int64_t k = 0; k <= B / 4; ++k) tw[(size_t)k] = (float)std::cos(2.0 * 3.14159265358979323846 * (double)k / (double)B);
+    bt.twiddle = dalloc<float>(tw.size());
+    h2d(bt.twiddle, tw.data(), tw.size() * 4, P.stream);
     sync(P.stream);
+}
+
+static void launch_batch_tz(PlanHolder& P, int R, const float* X, float* Z, const int* done);
+
+// Batched Toeplitz form, chosen once per plan (before any graph capture), after the
+// R-column buffers exist:
+//   BATCH_PAIR  two RHS per complex FFT (y_a + i y_b, one complex block of 2^logb points,
+//               block > 2 lambda complex points);
+//   BATCH_REAL  the single-RHS real-FFT kernel with an RHS grid dimension (its FP32
+//               block, B > 2 lambda reals, so half the FFT length of the pair form).
+// Cost model per RHS: tiles x (points x log2 + 2048) x cluster weight, halved for the
+// pair form; ties go to the pair form.  With autotuning both are timed at this R.
+static void ensure_batch_tables(PlanHolder& P, int R, int want = -1) {
+    BatchState& bt = P.batch;
+    if (bt.kind >= 0) {
+        if (want >= 0 && want != bt.kind) throw Error{MM_ERR_ARG, "the batched form is already fixed"};
+        return;
+    }
+    int best = -1;
+    double best_cost = 0.0;
+    for (int logb = 9; logb <= BATCH_MAX_LOGB; ++logb) {
+        const int64_t B = int64_t(1) << logb;
+        const int64_t Lv = B - 2 * (int64_t)P.lambda;
+        if (Lv < 1) continue;
+        const int cl = logb > BATCH_MAX_LOGB_CTA ? 1 << (logb - BATCH_MAX_LOGB_CTA) : 1;
+        const double cost = 0.5 * (double)overlap_tiles(P, Lv) * ((double)B * logb + 2048.0) * fp32_cluster_weight(cl);
+        if (best < 0 || cost < best_cost) {
+            best = logb;
+            best_cost = cost;
+        }
+    }
+    double real_cost = -1.0;
+    if (P.tz32.logn != 0) {
+        const int64_t N = int64_t(1) << P.tz32.logn;
+        real_cost = (double)P.tz32.ntiles * ((double)N * (P.tz32.logn + 1) + 2048.0) * block_weight<float>(P.tz32.logn);
+    }
+    if (best < 0 && real_cost < 0.0) throw Error{MM_ERR_ARG, "lambda too large for the batched FFT blocks"};
+    if ((want == BATCH_PAIR && best < 0) || (want == BATCH_REAL && real_cost < 0.0))
+        throw Error{MM_ERR_ARG, "no FFT block supports this batched form for lambda"};
+    if (best >= 0) build_batch_pair(P, best);
+    if (want >= 0) {
+        bt.kind = want;
+    } else if (best < 0) {
+        bt.kind = BATCH_REAL;
+    } else if (real_cost < 0.0) {
+        bt.kind = BATCH_PAIR;
+    } else if (P.autotune) {
+        check_cuda(cudaMemsetAsync(bt.x, 0, (size_t)R * P.n * 4, P.stream), "memset");
+        bt.kind = BATCH_PAIR;
+        bt.tuned_ms[0] = time_launches(P, [&] { launch_batch_tz(P, R, bt.x, bt.tod, nullptr); }, 3);
+        bt.kind = BATCH_REAL;
+        bt.tuned_ms[1] = time_launches(P, [&] { launch_batch_tz(P, R, bt.x, bt.tod, nullptr); }, 3);
+        bt.kind = bt.tuned_ms[0] <= bt.tuned_ms[1] ? BATCH_PAIR : BATCH_REAL;
+    } else {
+        bt.kind = best_cost <= real_cost ? BATCH_PAIR : BATCH_REAL;
+    }
 }
 
 static void ensure_batch_buffers(PlanHolder& P, int R) {
@@ -1034,6 +1162,7 @@ static BatchTzArgs batch_tz_args(PlanHolder& P, int R, const float* X, float* Z,
     A.tiles = P.batch.tiles;
     A.H = P.batch.H;
     A.ptw = reinterpret_cast<const float2*>(P.batch.ptw);
+    A.twiddle = P.batch.twiddle;
     A.X = X;
     A.pixc = P.pixc;
     A.w = P.w32;
@@ -1046,9 +1175,17 @@ static BatchTzArgs batch_tz_args(PlanHolder& P, int R, const float* X, float* Z,
     return A;
 }
 
+// Z_r = N^-1 P X_r (FP32) in the plan's batched form
+static void launch_batch_tz(PlanHolder& P, int R, const float* X, float* Z, const int* done) {
+    if (P.batch.kind == BATCH_REAL)
+        launch_toeplitz_rhs<float>(P, P.tz32, nullptr, X, R, P.n, Z, P.nt, done, P.stream);
+    else
+        launch_batch_toeplitz(batch_tz_args(P, R, X, Z, done), P.batch.logb, P.batch.ntiles, P.ncomp, P.stream);
+}
+
 // Y_r = A X_r (FP32), r < R <= BATCH_RMAX
 static void apply_A_batch(PlanHolder& P, int R, const float* X, float* Y, const int* done) {
-    launch_batch_toeplitz(batch_tz_args(P, R, X, P.batch.tod, done), P.batch.logb, P.batch.ntiles, P.ncomp, P.stream);
+    launch_batch_tz(P, R, X, P.batch.tod, done);
     launch_batch_scatter(P, P.batch.tod, Y, R, done, P.stream);
 }
 
@@ -1144,9 +1281,9 @@ static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_op
     check_solve_opts(P, so);
     if (so.solver != MM_SOLVE_MIXED || so.kind != MM_PREC_BD)
         throw Error{MM_ERR_ARG, "the batched solver runs MM_SOLVE_MIXED with MM_PREC_BD"};
-    ensure_batch_tables(P);
     const int RB = std::min(R, BATCH_RMAX);
     ensure_batch_buffers(P, RB);
+    ensure_batch_tables(P, RB);
     BatchState& bt = P.batch;
     const bool d_dev = is_device_ptr(D), m_dev = is_device_ptr(M);
     const size_t n = (size_t)P.n, nt = (size_t)P.nt;
@@ -1498,12 +1635,38 @@ mm_status mm_grad(mm_plan_t plan, const double* d, const double* m, const double
     });
 }
 
+mm_status mm_autotune_read(mm_plan_t plan, float* ms_f64, float* ms_f32) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (ms_f64) std::memcpy(ms_f64, P->tuned_ms64, sizeof(P->tuned_ms64));
+        if (ms_f32) std::memcpy(ms_f32, P->tuned_ms32, sizeof(P->tuned_ms32));
+    });
+}
+
+mm_status mm_batch_config(mm_plan_t plan, int32_t R, int32_t* kind, int32_t* log2_block, float* ms) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (R < 1 || R > BATCH_RMAX) throw Error{MM_ERR_ARG, "need 1 <= R <= 64"};
+        if (kind == nullptr || *kind < -1 || *kind > 1) throw Error{MM_ERR_ARG, "kind must point to -1, 0 or 1"};
+        ensure_batch_buffers(*P, R);
+        ensure_batch_tables(*P, R, *kind);
+        sync(*P);
+        const BatchState& bt = P->batch;
+        *kind = bt.kind;
+        if (log2_block) *log2_block = bt.kind == BATCH_REAL ? P->tz32.logn + 1 : bt.logb;
+        if (ms) {
+            ms[0] = bt.tuned_ms[0];
+            ms[1] = bt.tuned_ms[1];
+        }
+    });
+}
+
 mm_status mm_apply_A_batch(mm_plan_t plan, int R, const float* X, float* Y) {
     return guarded(plan, [&] {
         PlanHolder* P = get(plan);
         if (!X || !Y || R < 1 || R > BATCH_RMAX) throw Error{MM_ERR_ARG, "need 1 <= R <= 64 and non-null X, Y"};
-        ensure_batch_tables(*P);
         ensure_batch_buffers(*P, R);
+        ensure_batch_tables(*P, R);
         apply_A_batch(*P, R, X, Y, nullptr);
         sync(*P);
     });

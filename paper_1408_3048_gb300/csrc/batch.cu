@@ -17,34 +17,27 @@
 #include "pcg.cuh"
 #include "toeplitz.cuh"
 
+#include <cooperative_groups.h>
+
 namespace mm {
 
 // ------------------------------------------------------------------ batched Toeplitz
-template <int LOGB, int NT, int NC>
-__global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
-    constexpr int Bn = 1 << LOGB;            // complex points (= real block length)
-    if (A.done != nullptr && *(volatile const int*)A.done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* a = reinterpret_cast<float2*>(smem_raw);
-    const int npairs = (A.R + 1) / 2;
-    const int pair = blockIdx.x % npairs;
-    const Tile tile = A.tiles[blockIdx.x / npairs];
-    const int r0 = 2 * pair;
-    const bool has1 = r0 + 1 < A.R;
-    const float* x0 = A.X + (size_t)r0 * A.n;
-    const float* x1 = A.X + (size_t)(has1 ? r0 + 1 : r0) * A.n;
+// Gathers points [s0, s0 + count) of the packed complex block (column pair x0 + i x1)
+// into a[0 .. count).
+template <int NT, int NC>
+__device__ __forceinline__ void batch_load(const BatchTzArgs& A, const Tile& tile, int64_t ws, const float* x0,
+                                           const float* x1, bool has1, float2* a, int s0, int count) {
     const int tid = threadIdx.x;
-    const int64_t ws = tile.out0 - A.lambda;
-    constexpr int PER = Bn / NT;
-    constexpr int UNR = PER < 4 ? PER : 4;
+    const int PER = count / NT;
+    constexpr int UNR = 4;
 #pragma unroll 1
     for (int base = 0; base < PER; base += UNR) {
         int q[UNR];
         float2 w[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int64_t t = ws + (int64_t)((base + u) * NT + tid);
-            const bool ok = t >= tile.ibeg && t < tile.iend;
+            const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
+            const bool ok = base + u < PER && t >= tile.ibeg && t < tile.iend;
             q[u] = ok ? __ldg(A.pixc + t) : -1;
             if constexpr (NC == 3) {
                 if (ok) w[u] = A.w[t];
@@ -64,9 +57,27 @@ __global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
                 }
                 if (!has1) c.y = 0.f;
             }
-            a[pad<float>((base + u) * NT + tid)] = c;
+            if (base + u < PER) a[pad<float>((base + u) * NT + tid)] = c;
         }
     }
+}
+
+template <int LOGB, int NT, int NC>
+__global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
+    constexpr int Bn = 1 << LOGB;            // complex points (= real block length)
+    if (A.done != nullptr && *(volatile const int*)A.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    const int npairs = (A.R + 1) / 2;
+    const int pair = blockIdx.x % npairs;
+    const Tile tile = A.tiles[blockIdx.x / npairs];
+    const int r0 = 2 * pair;
+    const bool has1 = r0 + 1 < A.R;
+    const float* x0 = A.X + (size_t)r0 * A.n;
+    const float* x1 = A.X + (size_t)(has1 ? r0 + 1 : r0) * A.n;
+    const int tid = threadIdx.x;
+    const int64_t ws = tile.out0 - A.lambda;
+    batch_load<NT, NC>(A, tile, ws, x0, x1, has1, a, 0, Bn);
     __syncthreads();
     fft_all<float, LOGB, NT, 0>(a, A.ptw);
     // spectrum product (real, even kernel; H holds k = 0..Bn/2, already divided by Bn),
@@ -90,8 +101,100 @@ __global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
     }
 }
 
+// Cluster variant (CL = 2 or 4 CTAs) for blocks above the single-CTA maximum: CTA c holds
+// the complex points c M .. c M + M - 1.  Forward: cross-CTA radix-CL step with twiddles
+// W_Bn^(n1 c) (distributed shared memory), local M-point FFT -> bins CL k1 + c; pointwise
+// product; local FFT; cross-CTA radix-CL recombination written straight to global memory
+// (decimation in frequency, then in time, as in the single-RHS cluster kernel).
+template <int LOGM, int NT, int NC, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) batch_toeplitz_cl_kernel(BatchTzArgs A) {
+    constexpr int M = 1 << LOGM;
+    constexpr int Bn = CL * M;
+    constexpr int LOGQ = LOGM + (CL == 2 ? 1 : 2) - 2;   // Bn / 4 = 2^LOGQ
+    constexpr int PER = M / NT;
+    static_assert(PER >= 1 && M % NT == 0, "points per thread");
+    if (A.done != nullptr && *(volatile const int*)A.done) return;   // uniform over the cluster
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* part[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) part[c] = cl.map_shared_rank(a, c);
+    const int npairs = (A.R + 1) / 2;
+    const int cid = blockIdx.x / CL;
+    const int pair = cid % npairs;
+    const Tile tile = A.tiles[cid / npairs];
+    const int r0 = 2 * pair;
+    const bool has1 = r0 + 1 < A.R;
+    const float* x0 = A.X + (size_t)r0 * A.n;
+    const float* x1 = A.X + (size_t)(has1 ? r0 + 1 : r0) * A.n;
+    const int tid = threadIdx.x;
+    const int64_t ws = tile.out0 - A.lambda;
+    batch_load<NT, NC>(A, tile, ws, x0, x1, has1, a, rank * M, M);
+    cl.sync();
+    float2 y[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int n1 = u * NT + tid;
+        float2 acc = part[0][pad<float>(n1)];
+#pragma unroll
+        for (int n2 = 1; n2 < CL; ++n2) {
+            const float2 v = rot_c<float, CL>(part[n2][pad<float>(n1)], n2 * rank);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        if (rank != 0) {
+            float c, s;
+            twiddle<float, LOGQ>(A.twiddle, n1 * rank, c, s);
+            acc = cmul<float>(acc, c, s);
+        }
+        y[u] = acc;
+    }
+    cl.sync();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) a[pad<float>(u * NT + tid)] = y[u];
+    __syncthreads();
+    fft_all<float, LOGM, NT, 0>(a, A.ptw);
+    const float* H = A.H + (int64_t)tile.psd * (Bn / 2 + 1);
+    for (int k1 = tid; k1 < M; k1 += NT) {
+        const int k = CL * k1 + rank;
+        const float h = H[k <= Bn / 2 ? k : Bn - k];
+        float2 v = a[pad<float>(k1)];
+        v.x *= h;
+        v.y *= -h;
+        a[pad<float>(k1)] = v;
+    }
+    __syncthreads();
+    fft_all<float, LOGM, NT, 0>(a, A.ptw);
+    cl.sync();
+    float* z0 = A.Z + (size_t)r0 * A.nt + tile.out0;
+    float* z1 = A.Z + (size_t)(r0 + 1) * A.nt + tile.out0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int n1 = u * NT + tid;
+        float2 f = part[0][pad<float>(n1)];
+#pragma unroll
+        for (int m2 = 1; m2 < CL; ++m2) {
+            float c, s;
+            twiddle<float, LOGQ>(A.twiddle, n1 * m2, c, s);   // W_Bn^(m2 n1)
+            const float2 v = rot_c<float, CL>(cmul<float>(part[m2][pad<float>(n1)], c, s), m2 * rank);
+            f.x += v.x;
+            f.y += v.y;
+        }
+        const int n = rank * M + n1 - A.lambda;
+        if (n >= 0 && n < tile.nout) {
+            z0[n] = f.x;
+            if (has1) z1[n] = -f.y;
+        }
+    }
+    cl.sync();   // the other CTAs may still read this CTA's shared memory
+}
+
 size_t batch_toeplitz_smem(int logb) {
-    const size_t B = size_t(1) << logb;
+    const int lm = logb > BATCH_MAX_LOGB_CTA ? BATCH_MAX_LOGB_CTA : logb;   // per CTA
+    const size_t B = size_t(1) << lm;
     return sizeof(float2) * (B + (B >> PadLog<float>::v));
 }
 
@@ -112,7 +215,35 @@ static void launch_bt(const BatchTzArgs& A, int ntiles, cudaStream_t s) {
     note_launch();
 }
 
+template <int LOGM, int NC, int CL>
+static void launch_bt_cl(const BatchTzArgs& A, int ntiles, cudaStream_t s) {
+    constexpr int NT = tz_threads<float, LOGM>();
+    const size_t smem = batch_toeplitz_smem(LOGM);
+    auto kern = batch_toeplitz_cl_kernel<LOGM, NT, NC, CL>;
+    static bool attr = false;
+    if (!attr) {
+        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(batch toeplitz cluster)");
+        attr = true;
+    }
+    const int64_t grid = (int64_t)CL * ntiles * ((A.R + 1) / 2);
+    kern<<<(unsigned)grid, NT, smem, s>>>(A);
+    check_cuda(cudaGetLastError(), "batch toeplitz cluster launch");
+    note_launch();
+}
+
 void launch_batch_toeplitz(const BatchTzArgs& A, int logb, int ntiles, int ncomp, cudaStream_t s) {
+    static_assert(BATCH_MAX_LOGB_CTA == 14, "cluster instantiations below");
+    if (logb == 15) {
+        if (ncomp == 1) launch_bt_cl<14, 1, 2>(A, ntiles, s);
+        else launch_bt_cl<14, 3, 2>(A, ntiles, s);
+        return;
+    }
+    if (logb == 16) {
+        if (ncomp == 1) launch_bt_cl<14, 1, 4>(A, ntiles, s);
+        else launch_bt_cl<14, 3, 4>(A, ntiles, s);
+        return;
+    }
 #define MM_BT(L)                                                     \
     case L:                                                          \
         if (ncomp == 1) launch_bt<L, 1>(A, ntiles, s);               \

@@ -8,11 +8,14 @@ namespace mm {
 constexpr int BATCH_RMAX = 64;                 // right-hand sides per batched launch
 constexpr int BATCH_THREADS = 512;
 constexpr int BATCH_PSTRIDE = 3 * BATCH_RMAX;  // per-block partial slots
+constexpr int BATCH_MAX_LOGB_CTA = 14;         // largest complex block in one CTA
+constexpr int BATCH_MAX_LOGB = 16;             // 2- and 4-CTA clusters above it
 
 struct BatchTzArgs {
     const Tile* tiles;
     const float* H;            // [npsd][B/2 + 1], divided by B
-    const float2* ptw;         // per-pass FFT twiddles of the B-point transform
+    const float2* ptw;         // per-pass FFT twiddles of the per-CTA transform
+    const float* twiddle;      // cos(2 pi k / B), k = 0..B/4 (cluster variants)
     const float* X;            // [R][n]
     const int32_t* pixc;
     const float2* w;

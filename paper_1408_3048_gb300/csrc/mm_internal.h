@@ -167,6 +167,11 @@ double rcond_sym3(const double B[6]);
 template <typename T>
 void launch_toeplitz(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const T* x_map,
                      T* z, const int* done, cudaStream_t s);
+// R right-hand sides in one launch: RHS r reads y_tod + r in_stride (or x_map + r in_stride)
+// and writes z + r out_stride
+template <typename T>
+void launch_toeplitz_rhs(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const T* x_map, int R,
+                         int64_t in_stride, T* z, int64_t out_stride, const int* done, cudaStream_t s);
 template <typename T>
 size_t toeplitz_smem_bytes(int logn);
 template <typename T>

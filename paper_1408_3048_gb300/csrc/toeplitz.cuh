@@ -43,7 +43,21 @@ struct TzArgs {
     T* z;                  // [nt] output
     const int* done;       // early-exit flag (PCG) or nullptr
     int lambda;
+    int R;                 // right-hand sides (grid: tile-major, RHS fastest)
+    int64_t in_stride;     // elements between RHS in y (mode 0) or x (gather modes)
+    int64_t out_stride;    // elements between RHS in z
 };
+
+// (tile, RHS) of a CTA (or cluster) index: RHS fastest, so the R CTAs of one tile read
+// its pointing from L2 after the first.
+struct TileRhs {
+    int tile;
+    int rhs;
+};
+__device__ __forceinline__ TileRhs tile_rhs(int cid, int R) {
+    if (R == 1) return {cid, 0};
+    return {cid / R, cid % R};
+}
 
 template <typename T>
 __device__ __forceinline__ typename Cx<T>::type cmul(typename Cx<T>::type a, T c, T s) {
@@ -267,7 +281,9 @@ __device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const typename 
 // interval read as 0.  MODE 0: from A.y; 1: T gather; 3: I/Q/U gather.
 template <typename T, int NT, int MODE>
 __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile, int64_t ws, T* ar, int s0,
-                                           int count) {
+                                           int count, int64_t roff) {
+    const T* __restrict__ y = A.y + roff;
+    const T* __restrict__ x = A.x + roff;
     const int tid = threadIdx.x;
     const int PER = count / NT;
     constexpr int UMAX = MODE == 3 ? 4 : 8;
@@ -279,7 +295,7 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
                 const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
-                v[u] = (base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend))) ? A.y[t] : (T)0;
+                v[u] = (base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend))) ? y[t] : (T)0;
             }
         } else {
             int q[UMAX];
@@ -298,9 +314,9 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
                 T r = (T)0;
                 if (q[u] >= 0) {
                     if constexpr (MODE == 1) {
-                        r = __ldg(A.x + q[u]);
+                        r = __ldg(x + q[u]);
                     } else {
-                        const T* xq = A.x + 3 * (int64_t)q[u];
+                        const T* xq = x + 3 * (int64_t)q[u];
                         r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
                     }
                 }
@@ -366,11 +382,12 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
     T* tab = reinterpret_cast<T*>(smem_raw + sizeof(C2) * (N + (N >> PadLog<T>::v)));
-    const Tile tile = A.tiles[blockIdx.x];
+    const TileRhs tr = tile_rhs(blockIdx.x, A.R);
+    const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
     for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     const int64_t ws = tile.out0 - A.lambda;
-    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), 0, 2 * N);
+    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // real-FFT post-processing, spectrum product, pre-processing for the inverse.
@@ -387,7 +404,7 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // outputs: real samples lambda .. lambda + nout - 1 of the block
-    T* zo = A.z + tile.out0;
+    T* zo = A.z + tr.rhs * A.out_stride + tile.out0;
     for (int n = tid; n < tile.nout; n += NT) {
         const int i = n + A.lambda;
         const C2 v = a[pad<T>(i >> 1)];
@@ -435,10 +452,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
     C2* part[CL];
 #pragma unroll
     for (int c = 0; c < CL; ++c) part[c] = cl.map_shared_rank(a, c);
-    const Tile tile = A.tiles[blockIdx.x / CL];
+    const TileRhs tr = tile_rhs(blockIdx.x / CL, A.R);
+    const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
     const int64_t ws = tile.out0 - A.lambda;
-    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M);
+    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M, tr.rhs * A.in_stride);
     cl.sync();
     C2 y[PER];
 #pragma unroll
@@ -500,7 +518,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
     __syncthreads();
     fft_all<T, LOGM, NT, 0>(a, A.ptw);
     cl.sync();
-    T* zo = A.z + tile.out0;
+    T* zo = A.z + tr.rhs * A.out_stride + tile.out0;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int n1 = u * NT + tid;
@@ -548,7 +566,7 @@ void launch_cl(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
                    "cudaFuncSetAttribute(toeplitz cluster)");
         attr_set = true;
     }
-    kern<<<CL * ntiles, NT, smem, s>>>(A);
+    kern<<<(unsigned)((int64_t)CL * ntiles * A.R), NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz cluster kernel launch");
     note_launch();
 }
@@ -579,7 +597,7 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
                    "cudaFuncSetAttribute(toeplitz)");
         attr_set = true;
     }
-    kern<<<ntiles, NT, smem, s>>>(A);
+    kern<<<(unsigned)((int64_t)ntiles * A.R), NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz kernel launch");
     note_launch();
 }

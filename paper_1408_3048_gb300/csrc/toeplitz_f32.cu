@@ -10,8 +10,8 @@ template <>
 int toeplitz_max_logn<float>() { return 14; }
 
 template <>
-void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y, const float* x,
-                          float* z, const int* done, cudaStream_t s) {
+void launch_toeplitz_rhs<float>(const Plan& P, const ToeplitzDev& tz, const float* y, const float* x, int R,
+                             int64_t in_stride, float* z, int64_t out_stride, const int* done, cudaStream_t s) {
     if (tz.logn == 0) throw Error{MM_ERR_ARG, "no FP32 Toeplitz block fits this lambda"};
     if (tz.ntiles == 0) return;
     TzArgs<float> A;
@@ -26,6 +26,9 @@ void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y
     A.z = z;
     A.done = done;
     A.lambda = P.lambda;
+    A.R = R;
+    A.in_stride = in_stride;
+    A.out_stride = out_stride;
     const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
     if (tz.cluster == 2 && tz.logn == 15) {
         launch_mode_cl<float, 14, 2>(A, tz.ntiles, mode, s);
@@ -46,6 +49,12 @@ void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y
         case 14: launch_mode<float, 14>(A, tz.ntiles, mode, s); break;
         default: throw Error{MM_ERR_ARG, "unsupported FFT length"};
     }
+}
+
+template <>
+void launch_toeplitz<float>(const Plan& P, const ToeplitzDev& tz, const float* y, const float* x, float* z,
+                         const int* done, cudaStream_t s) {
+    launch_toeplitz_rhs<float>(P, tz, y, x, 1, 0, z, 0, done, s);
 }
 
 }  // namespace mm

@@ -10,8 +10,8 @@ template <>
 int toeplitz_max_logn<double>() { return 13; }
 
 template <>
-void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x,
-                          double* z, const int* done, cudaStream_t s) {
+void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x, int R,
+                             int64_t in_stride, double* z, int64_t out_stride, const int* done, cudaStream_t s) {
     if (tz.logn == 0) throw Error{MM_ERR_ARG, "no FP64 Toeplitz block fits this lambda"};
     if (tz.ntiles == 0) return;
     TzArgs<double> A;
@@ -26,6 +26,9 @@ void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double*
     A.z = z;
     A.done = done;
     A.lambda = P.lambda;
+    A.R = R;
+    A.in_stride = in_stride;
+    A.out_stride = out_stride;
     const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
     if (tz.cluster == 2 && tz.logn == 14) {
         launch_mode_cl<double, 13, 2>(A, tz.ntiles, mode, s);
@@ -45,6 +48,12 @@ void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double*
         case 13: launch_mode<double, 13>(A, tz.ntiles, mode, s); break;
         default: throw Error{MM_ERR_ARG, "unsupported FFT length"};
     }
+}
+
+template <>
+void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x, double* z,
+                         const int* done, cudaStream_t s) {
+    launch_toeplitz_rhs<double>(P, tz, y, x, 1, 0, z, 0, done, s);
 }
 
 }  // namespace mm

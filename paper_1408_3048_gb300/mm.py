@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 
 EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gather", "mm_apply_ninv",
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
-           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch", "mm_solve_batch"]
+           "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
+           "mm_solve_batch", "mm_autotune_read", "mm_batch_config"]
 
 
 class mm_psd(ctypes.Structure):
@@ -39,7 +40,7 @@ class mm_psd(ctypes.Structure):
 class mm_opts(ctypes.Structure):
     _fields_ = [("ncomp", ctypes.c_int32), ("lambda_", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("fft_log2_f64", ctypes.c_int32), ("fft_log2_f32", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("fsamp", ctypes.c_double), ("rcond_min", ctypes.c_double),
+                ("autotune", ctypes.c_int32), ("fsamp", ctypes.c_double), ("rcond_min", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -91,6 +92,8 @@ _SIGS = {
     "mm_grad": (I32, [P, P, P, P, P, P, ctypes.POINTER(mm_solve_opts), ctypes.POINTER(mm_stats)]),
     "mm_apply_A_batch": (I32, [P, ctypes.c_int, P, P]),
     "mm_solve_batch": (I32, [P, P, ctypes.c_int, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
+    "mm_autotune_read": (I32, [P, P, P]),
+    "mm_batch_config": (I32, [P, ctypes.c_int32, P, P, P]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
@@ -166,6 +169,23 @@ def mm_plan_info(plan):
                               ctypes.byref(b32)), plan)
     return {"npix_obs": npix.value, "n": n.value, "nkept": nk.value, "fft_block_f64": b64.value,
             "fft_block_f32": b32.value}
+
+
+def mm_autotune_read(plan):
+    """(ms_f64, ms_f32): timed candidate blocks, index log2(B) - 9, 0 where not timed."""
+    a = (ctypes.c_float * 16)()
+    b = (ctypes.c_float * 16)()
+    _check(lib().mm_autotune_read(plan, a, b), plan)
+    return list(a), list(b)
+
+
+def mm_batch_config(plan, R, kind=-1):
+    """(kind, log2_block, [ms_pair, ms_real]) of the batched operator for R columns."""
+    kind = ctypes.c_int32(int(kind))
+    lb = ctypes.c_int32()
+    ms = (ctypes.c_float * 2)()
+    _check(lib().mm_batch_config(plan, int(R), ctypes.byref(kind), ctypes.byref(lb), ms), plan)
+    return kind.value, lb.value, list(ms)
 
 
 def mm_plan_pixels(plan, obs2sky, hits):
@@ -280,7 +300,7 @@ class Plan:
     """One map-making problem on the current CUDA device (torch tensors in and out)."""
 
     def __init__(self, pix, npix_sky, weights, offsets, interval_psd, psds, lam, fsamp=100.0, ncomp=None,
-                 window=MM_WINDOW_GAUSS, rcond_min=1e-6, fft_log2=(0, 0), stream=None):
+                 window=MM_WINDOW_GAUSS, rcond_min=1e-6, fft_log2=(0, 0), stream=None, autotune=False):
         torch = _torch()
         self._torch = torch
         pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32))
@@ -295,7 +315,7 @@ class Plan:
             stream = torch.cuda.current_stream()
         self.stream = stream
         o = mm_opts(ncomp=ncomp, lambda_=int(lam), window=window, fft_log2_f64=int(fft_log2[0]),
-                    fft_log2_f32=int(fft_log2[1]), reserved=0, fsamp=float(fsamp), rcond_min=float(rcond_min),
+                    fft_log2_f32=int(fft_log2[1]), autotune=int(bool(autotune)), fsamp=float(fsamp), rcond_min=float(rcond_min),
                     stream=stream.cuda_stream)
         self.handle = mm_plan(pix, pix.size, npix_sky, w, off, off.size - 1, ipsd, arr, len(ps), o)
         info = mm_plan_info(self.handle)
@@ -399,6 +419,16 @@ class Plan:
         self._sync_in()
         st = mm_grad(self.handle, d, m, g, dd, dp, o)
         return dd, dp, st.as_dict()
+
+    def autotune_ms(self):
+        """Timed overlap-save blocks {log2 B: ms} per precision (autotuned plans)."""
+        a, b = mm_autotune_read(self.handle)
+        return ({i + 9: v for i, v in enumerate(a) if v > 0}, {i + 9: v for i, v in enumerate(b) if v > 0})
+
+    def batch_config(self, R, kind=-1):
+        """(kind, log2 block, timings) of the batched operator; fixes it for this plan."""
+        self._sync_in()
+        return mm_batch_config(self.handle, R, kind)
 
     def apply_A_batch(self, X, out=None):
         """Y[r] = A X[r] in FP32 for a float32 cuda tensor X [R, n] (R <= 64)."""

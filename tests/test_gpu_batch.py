@@ -22,17 +22,20 @@ CASES = {
 }
 
 
-def _plan(scan, stream=None):
+def _plan(scan, stream=None, **kw):
     return mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
-                   scan.lam, scan.fsamp, stream=stream)
+                   scan.lam, scan.fsamp, stream=stream, **kw)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("R", [1, 2, 5, 64])
-def test_batched_operator(name, R):
+def test_batched_operator(name, R, kind):
+    # kind 0: two columns per complex FFT; kind 1: one real FFT per column
     scan = CASES[name]()
     pr = oracle_problem(scan)
     plan = _plan(scan)
+    assert plan.batch_config(R, kind)[0] == kind
     X = torch.randn(R, plan.n, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(R))
     Y = plan.apply_A_batch(X).cpu().numpy()
     Xh = X.double().cpu().numpy()
@@ -87,6 +90,19 @@ def test_batched_solve_graph_and_direct_paths_agree_and_groups():
     b.close()
 
 
+def test_batched_form_autotuned_and_fixed():
+    scan = CASES["P"]()
+    plan = _plan(scan, autotune=True)
+    kind, lb, ms = plan.batch_config(8)
+    assert kind in (0, 1) and ms[0] > 0 and ms[1] > 0
+    assert kind == (0 if ms[0] <= ms[1] else 1)
+    with pytest.raises(mm.MMError) as e:          # the form is fixed once chosen
+        plan.batch_config(8, 1 - kind)
+    assert e.value.status == mm.MM_ERR_ARG
+    assert plan.batch_config(8, kind)[0] == kind
+    plan.close()
+
+
 def test_batched_rejects_unsupported_options():
     scan = tiny_scan()
     plan = _plan(scan)
@@ -96,4 +112,34 @@ def test_batched_rejects_unsupported_options():
     with pytest.raises(mm.MMError) as e:
         mm.mm_solve_batch(plan.handle, D, 2, o, M)
     assert e.value.status == mm.MM_ERR_ARG
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("lam", [8192, 16384])
+def test_batched_operator_cluster_blocks(lam, kind):
+    # bands beyond the single-CTA complex block (2^14 points) take the 2-CTA (2^15) and
+    # 4-CTA (2^16) cluster blocks in the pair form, the real form the FP32 cluster blocks;
+    # R = 3 leaves the last column pair half empty
+    scan = synth.raster_scan(64, 48, 2, 3 * 2 ** 16, 3, 2, lam, [(1.0, 1.0, 1.0), (0.8, 1.5, 1.5)],
+                             det_psd=[0, 1], uneven=(2 ** 16 + 5, 2 ** 17 - 7), seed=11)
+    pr = oracle_problem(scan)
+    plan = _plan(scan)
+    R = 3
+    k, lb, _ = plan.batch_config(R, kind)
+    assert k == kind and lb >= (15 if lam == 8192 else 16)
+    X = torch.randn(R, plan.n, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(lam))
+    Y = plan.apply_A_batch(X).cpu().numpy()
+    Xh = X.double().cpu().numpy()
+    for r in range(R):
+        ref = pr.A(Xh[r], route="fft")
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) <= 3e-5, r
+    D = torch.from_numpy(_data(scan, R, 500)).cuda()
+    M, st, status = plan.solve_batch(D, tol=1e-6, maxit=3000)
+    assert status == mm.MM_OK
+    Mh = M.cpu().numpy()
+    for r in range(R):
+        b = pr.rhs(D[r].cpu().numpy(), route="fft")
+        assert st[r]["converged"] == 1
+        assert np.linalg.norm(b - pr.A(Mh[r], route="fft")) / np.linalg.norm(b) <= 1e-6, r
     plan.close()

@@ -258,6 +258,28 @@ def test_cluster_fft_blocks_forced(ncomp, cl):
     plan.close()
 
 
+@pytest.mark.parametrize("case", ["P_ragged", "c2_small"])
+def test_autotuned_blocks(case):
+    # the autotuner times the cheapest admissible blocks and keeps the fastest; the
+    # operator stays within the same tolerances as with cost-model blocks
+    scan = SCANS[case]()
+    pr = oracle_problem(scan)
+    plan = _plan(scan, autotune=True)
+    ms64, ms32 = plan.autotune_ms()
+    for ms, block in ((ms64, plan.fft_block_f64), (ms32, plan.fft_block_f32)):
+        if len(ms) >= 2:
+            assert block == 2 ** min(ms, key=ms.get)
+        assert 1 <= len(ms) <= 3 or len(ms) == 0
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(pr.n)
+    ref = pr.A(x)
+    for prec, dt, tol in ((mm.MM_FP64, torch.float64, 1e-12), (mm.MM_FP32, torch.float32, 3e-5)):
+        xc = _cuda(x, dt)
+        y = plan.apply_A(xc, prec).cpu().numpy()
+        assert _rel(y, pr.A(xc.double().cpu().numpy())) <= tol
+    plan.close()
+
+
 @pytest.mark.parametrize("lam", [8192, 16384, 40000])
 def test_long_band_uses_cluster_blocks(lam):
     # lambda = 8192 (the large polarised workload's band) needs a cluster FP64 block,
