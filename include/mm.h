@@ -240,7 +240,10 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
  *           MM_SOLVE_MIXED: FP32 gather / Toeplitz / scatter and FP32 vectors with FP64
  *           dot products and step scalars inside PCG, FP64 E factor and solve, and an
  *           outer FP64 iterative-refinement loop m += A^-1 (b - A m) that stops on the
- *           true FP64 residual.
+ *           true FP64 residual, computed from the data as P^T N^-1 (d - P m) (one FP64
+ *           Toeplitz pass).  b itself is formed in FP32 (it seeds the first inner solve
+ *           and scales the residual; ||b|| to FP32 accuracy) -- the one FP64 Toeplitz
+ *           pass a converged first step needs is the residual.
  *   m       host or device double[n] output map.
  *   st      host stats (may be NULL).
  * Returns MM_ERR_NOT_CONVERGED (m = last iterate, st filled) when maxit is reached.

@@ -826,9 +826,29 @@ static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
         throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
 }
 
+// FP64 residual r = b - A x: with the data d (device, FP64) as P^T N^-1 (d - P x) -- one
+// Toeplitz pass on the residual data, free of the cancellation between b and A x --
+// else as b - A x from P.b64.
+static void residual64(PlanHolder& P, const double* d, const double* x, double* r) {
+    cudaStream_t s = P.stream;
+    if (d != nullptr) {
+        int sl = prof_begin(P, ST_TZ64);
+        launch_toeplitz_any<double>(P, P.tz64, nullptr, d, x, 1, 0, P.tod64, 0, nullptr, s);
+        prof_end(P, sl);
+        sl = prof_begin(P, ST_SC64);
+        launch_scatter<double>(P, P.tod64, r, nullptr, s);
+        prof_end(P, sl);
+    } else {
+        apply_A<double>(P, x, P.ax64, nullptr);
+        launch_sub(P.b64, P.ax64, r, P.n, s);
+    }
+}
+
 // Solve A x = b for the b in P.b64 into xout (device); fills the iteration part of stats
-// and returns the status.
-static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm_stats& stats) {
+// and returns the status.  d: the data b came from (device, FP64) or null; with it the
+// FP64 residuals take the one-pass form of residual64.
+static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm_stats& stats,
+                        const double* d = nullptr) {
     cudaStream_t s = P.stream;
     const double tol = so.tol;
     const int maxit = so.maxit;
@@ -847,8 +867,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
         stats.outer = 1;
         stats.rel_resid_rec = bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
         // true residual of the returned map
-        apply_A<double>(P, xout, P.ax64, nullptr);
-        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+        residual64(P, d, xout, P.r64);
         const double rr = dot64(P, P.r64, P.r64);
         stats.rel_resid = bn > 0 ? std::sqrt(rr) / bn : 0.0;
         stats.fp64_products = 1;
@@ -884,8 +903,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
         total += o.iters;
         last_rec = o.bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
         launch_axpy_f32(xout, static_cast<const float*>(P.pcg.x), P.d_dot + DOT_BLOCKS, P.n, s);
-        apply_A<double>(P, xout, P.ax64, nullptr);
-        launch_sub(P.b64, P.ax64, P.r64, P.n, s);
+        residual64(P, d, xout, P.r64);
         ++fp64;
         rr = dot64(P, P.r64, P.r64);
         ++outer;
@@ -917,18 +935,31 @@ static void solve(PlanHolder& P, const double* d, const mm_solve_opts& so, doubl
         h2d(P.dbuf, d, (size_t)P.nt * 8, s);
         dd = P.dbuf;
     }
-    // b = P^T N^-1 d (Eq. 7)
-    int sl = prof_begin(P, ST_TZ64);
-    launch_toeplitz<double>(P, P.tz64, dd, nullptr, P.tod64, nullptr, s);
-    prof_end(P, sl);
-    sl = prof_begin(P, ST_SC64);
-    launch_scatter<double>(P, P.tod64, P.b64, nullptr, s);
-    prof_end(P, sl);
+    // b = P^T N^-1 d (Eq. 7): in FP64 for the FP64 solver; in FP32 for the mixed solver,
+    // whose FP64 residuals come from the data (residual64), so b only seeds the first
+    // inner solve and scales the residual norm
+    if (so.solver == MM_SOLVE_MIXED && P.tz32.logn != 0) {
+        int sl = prof_begin(P, ST_TZ32);
+        launch_toeplitz_any<float>(P, P.tz32, nullptr, dd, nullptr, 1, 0, P.tod32, 0, nullptr, s);
+        prof_end(P, sl);
+        sl = prof_begin(P, ST_SC32);
+        float* b32 = static_cast<float*>(P.pcg.z);   // scratch until the first PCG start
+        launch_scatter<float>(P, P.tod32, b32, nullptr, s);
+        prof_end(P, sl);
+        launch_convert_f32_to_f64(b32, P.b64, P.n, s);
+    } else {
+        int sl = prof_begin(P, ST_TZ64);
+        launch_toeplitz<double>(P, P.tz64, dd, nullptr, P.tod64, nullptr, s);
+        prof_end(P, sl);
+        sl = prof_begin(P, ST_SC64);
+        launch_scatter<double>(P, P.tod64, P.b64, nullptr, s);
+        prof_end(P, sl);
+    }
     P.have_b = true;
     check_cuda(cudaEventRecord(P.ev1, s), "event");
     const bool m_dev = is_device_ptr(m);
     double* xout = m_dev ? m : P.x64;
-    const int status = solve_from_b(P, so, xout, stats);
+    const int status = solve_from_b(P, so, xout, stats, P.tz64.logn != 0 ? dd : nullptr);
     if (!m_dev) d2h(m, xout, (size_t)P.n * 8, s);
     check_cuda(cudaEventRecord(P.ev2, s), "event");
     sync(P);

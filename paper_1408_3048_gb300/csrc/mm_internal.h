@@ -172,6 +172,11 @@ void launch_toeplitz(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const
 template <typename T>
 void launch_toeplitz_rhs(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const T* x_map, int R,
                          int64_t in_stride, T* z, int64_t out_stride, const int* done, cudaStream_t s);
+// General form: d_tod (FP64 time domain) alone is rounded to T (FP32 only); with x_map the
+// input is d - P x (FP64 only: the residual data of b - A x).
+template <typename T>
+void launch_toeplitz_any(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const double* d_tod, const T* x_map,
+                         int R, int64_t in_stride, T* z, int64_t out_stride, const int* done, cudaStream_t s);
 template <typename T>
 size_t toeplitz_smem_bytes(int logn);
 template <typename T>
@@ -186,6 +191,7 @@ void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
 template <typename T>
 void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_convert_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
 // gradient helpers (grad.cu)
 void launch_sub_time(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
 void launch_interval_dot(const double* u, const double* w, const int64_t* ioff, int K, double* part,

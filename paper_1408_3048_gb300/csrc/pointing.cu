@@ -266,4 +266,17 @@ void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_
     note_launch();
 }
 
+__global__ void widen_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+void launch_convert_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    widen_kernel<<<grid_for(n, 256, 160), 256, 0, s>>>(a, b, n);
+    check_cuda(cudaGetLastError(), "widen launch");
+    note_launch();
+}
+
 }  // namespace mm

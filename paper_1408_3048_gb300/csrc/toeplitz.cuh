@@ -37,6 +37,7 @@ struct TzArgs {
     const typename Cx<T>::type* ptw;  // per-pass FFT twiddles (ptw_offset)
     const T* H;            // [npsd][N + 1]
     const T* y;            // time-domain input (mode 0)
+    const double* yd;      // FP64 time-domain input (modes 2, 4, 5)
     const T* x;            // map (gather modes)
     const int32_t* pixc;   // [nt]
     const typename Cx<T>::type* w;  // [nt] (cos, sin) for ncomp = 3
@@ -274,7 +275,9 @@ __device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const typename 
     }
 }
 
-// MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map.
+// MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map;
+// 2: y from an FP64 time-domain array (rounded to T); 4 / 5: FP64 data minus the T /
+// I/Q/U gather, d - P x (the residual b - A x = P^T N^-1 (d - P x) of Eq. 5 and 7).
 // Load real samples [s0, s0 + count) of the block that starts at time ws into ar[0..count)
 // (one sample per lane, coalesced; ar is the packed complex array viewed as reals, so local
 // sample s lands in component s & 1 of complex slot s / 2).  Samples outside the tile's
@@ -284,43 +287,50 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
                                            int count, int64_t roff) {
     const T* __restrict__ y = A.y + roff;
     const T* __restrict__ x = A.x + roff;
+    const double* __restrict__ yd = A.yd + roff;
     const int tid = threadIdx.x;
     const int PER = count / NT;
-    constexpr int UMAX = MODE == 3 ? 4 : 8;
+    constexpr bool IQU = MODE == 3 || MODE == 5;
+    constexpr int UMAX = IQU ? 4 : 8;
     const bool interior = ws + s0 >= tile.ibeg && ws + s0 + count <= tile.iend;
 #pragma unroll 1
     for (int base = 0; base < PER; base += UMAX) {
         T v[UMAX];
-        if constexpr (MODE == 0) {
+        if constexpr (MODE == 0 || MODE == 2) {
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
                 const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
-                v[u] = (base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend))) ? y[t] : (T)0;
+                const bool ok = base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend));
+                if constexpr (MODE == 0) v[u] = ok ? y[t] : (T)0;
+                else v[u] = ok ? (T)yd[t] : (T)0;
             }
         } else {
             int q[UMAX];
             typename Cx<T>::type w[UMAX];
+            T dv[UMAX];
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
                 const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
                 const bool ok = base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend));
                 q[u] = ok ? __ldg(A.pixc + t) : -1;
-                if constexpr (MODE == 3) {
+                if constexpr (IQU) {
                     if (ok) w[u] = A.w[t];
                 }
+                if constexpr (MODE >= 4) dv[u] = ok ? (T)yd[t] : (T)0;
             }
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
                 T r = (T)0;
                 if (q[u] >= 0) {
-                    if constexpr (MODE == 1) {
+                    if constexpr (!IQU) {
                         r = __ldg(x + q[u]);
                     } else {
                         const T* xq = x + 3 * (int64_t)q[u];
                         r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
                     }
                 }
-                v[u] = r;
+                if constexpr (MODE >= 4) v[u] = dv[u] - r;
+                else v[u] = r;
             }
         }
 #pragma unroll
@@ -574,10 +584,18 @@ void launch_cl(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
 template <typename T, int LOGM, int CL>
 void launch_mode_cl(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
     switch (mode) {
-        case 0: launch_cl<T, LOGM, 0, CL>(A, ntiles, s); break;
-        case 1: launch_cl<T, LOGM, 1, CL>(A, ntiles, s); break;
-        default: launch_cl<T, LOGM, 3, CL>(A, ntiles, s); break;
+        case 0: launch_cl<T, LOGM, 0, CL>(A, ntiles, s); return;
+        case 1: launch_cl<T, LOGM, 1, CL>(A, ntiles, s); return;
+        case 3: launch_cl<T, LOGM, 3, CL>(A, ntiles, s); return;
+        default: break;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (mode == 2) return launch_cl<T, LOGM, 2, CL>(A, ntiles, s);
+    } else {
+        if (mode == 4) return launch_cl<T, LOGM, 4, CL>(A, ntiles, s);
+        if (mode == 5) return launch_cl<T, LOGM, 5, CL>(A, ntiles, s);
+    }
+    throw Error{MM_ERR_ARG, "unsupported Toeplitz load mode"};
 }
 
 template <typename T>
@@ -602,13 +620,23 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     note_launch();
 }
 
+// Load modes 0, 1, 3 for both precisions; 2 (FP64 data rounded) for FP32 only; 4 and 5
+// (FP64 residual data) for FP64 only.
 template <typename T, int LOGN>
 void launch_mode(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
     switch (mode) {
-        case 0: launch_one<T, LOGN, 0>(A, ntiles, s); break;
-        case 1: launch_one<T, LOGN, 1>(A, ntiles, s); break;
-        default: launch_one<T, LOGN, 3>(A, ntiles, s); break;
+        case 0: launch_one<T, LOGN, 0>(A, ntiles, s); return;
+        case 1: launch_one<T, LOGN, 1>(A, ntiles, s); return;
+        case 3: launch_one<T, LOGN, 3>(A, ntiles, s); return;
+        default: break;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (mode == 2) return launch_one<T, LOGN, 2>(A, ntiles, s);
+    } else {
+        if (mode == 4) return launch_one<T, LOGN, 4>(A, ntiles, s);
+        if (mode == 5) return launch_one<T, LOGN, 5>(A, ntiles, s);
+    }
+    throw Error{MM_ERR_ARG, "unsupported Toeplitz load mode"};
 }
 
 }  // namespace mm

@@ -9,9 +9,11 @@ size_t toeplitz_smem_bytes<double>(int logn) { return toeplitz_smem_bytes_impl<d
 template <>
 int toeplitz_max_logn<double>() { return 13; }
 
+// Load mode from the inputs: y (mode 0), yd without x (2, FP32 only), yd with x (4 / 5,
+// FP64 only), else the gather of x (1 / 3).
 template <>
-void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x, int R,
-                             int64_t in_stride, double* z, int64_t out_stride, const int* done, cudaStream_t s) {
+void launch_toeplitz_any<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* yd, const double* x,
+                             int R, int64_t in_stride, double* z, int64_t out_stride, const int* done, cudaStream_t s) {
     if (tz.logn == 0) throw Error{MM_ERR_ARG, "no FP64 Toeplitz block fits this lambda"};
     if (tz.ntiles == 0) return;
     TzArgs<double> A;
@@ -20,6 +22,7 @@ void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const dou
     A.ptw = static_cast<const typename Cx<double>::type*>(tz.ptw);
     A.H = static_cast<const double*>(tz.H);
     A.y = y;
+    A.yd = yd;
     A.x = x;
     A.pixc = P.pixc;
     A.w = P.w64;
@@ -29,7 +32,7 @@ void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const dou
     A.R = R;
     A.in_stride = in_stride;
     A.out_stride = out_stride;
-    const int mode = y != nullptr ? 0 : (P.ncomp == 1 ? 1 : 3);
+    const int mode = y != nullptr ? 0 : (yd != nullptr ? (x == nullptr ? 2 : (P.ncomp == 1 ? 4 : 5)) : (P.ncomp == 1 ? 1 : 3));
     if (tz.cluster == 2 && tz.logn == 14) {
         launch_mode_cl<double, 13, 2>(A, tz.ntiles, mode, s);
         return;
@@ -53,7 +56,13 @@ void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const dou
 template <>
 void launch_toeplitz<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x, double* z,
                          const int* done, cudaStream_t s) {
-    launch_toeplitz_rhs<double>(P, tz, y, x, 1, 0, z, 0, done, s);
+    launch_toeplitz_any<double>(P, tz, y, nullptr, x, 1, 0, z, 0, done, s);
+}
+
+template <>
+void launch_toeplitz_rhs<double>(const Plan& P, const ToeplitzDev& tz, const double* y, const double* x, int R,
+                             int64_t in_stride, double* z, int64_t out_stride, const int* done, cudaStream_t s) {
+    launch_toeplitz_any<double>(P, tz, y, nullptr, x, R, in_stride, z, out_stride, done, s);
 }
 
 }  // namespace mm
