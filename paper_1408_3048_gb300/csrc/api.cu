@@ -163,8 +163,7 @@ static void free_coarse(CoarseDev& c) {
     dfree(c.AZ64);
     dfree(c.Z32);
     dfree(c.AZ32);
-    dfree(c.L);
-    dfree(c.Ld);
+    dfree(c.Einv);
     c = CoarseDev{};
 }
 
@@ -180,7 +179,8 @@ static void destroy_plan(PlanHolder* P) {
     free_tz(P->tz32);
     free_coarse(P->coarse);
     PcgDev& g = P->pcg;
-    for (void* p : {(void*)g.partial, (void*)g.scal, (void*)g.flags, (void*)g.barrier, g.x, g.r, g.p, g.q, g.z,
+    for (void* p : {(void*)g.partial, (void*)g.sc_part, (void*)g.sc_count, (void*)g.scal, (void*)g.flags,
+                    (void*)g.barrier, g.x, g.r, g.p, g.q, g.z,
                     (void*)g.hist_alpha, (void*)g.hist_beta, (void*)g.hist_rz, (void*)g.hist_rr})
         dfree(p);
     if (P->h_flags) (void)cudaFreeHost(P->h_flags);
@@ -535,6 +535,9 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     g.n = P.n;
     g.nblocks = std::max(1, std::min(pcg_max_blocks(P.num_sms), (P.npix_obs + 31) / 32));
     g.partial = dalloc<double>((size_t)g.nblocks * PSTRIDE);
+    g.sc_part = dalloc<double>((size_t)scatter_blocks(P));
+    g.sc_count = dalloc<unsigned>(1);
+    check_cuda(cudaMemsetAsync(g.sc_count, 0, 4, s), "memset");
     g.scal = dalloc<double>(16);
     g.flags = dalloc<int>(8);
     g.barrier = dalloc<unsigned>(4);
@@ -609,8 +612,7 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
             a.Z = reinterpret_cast<const T*>(P.coarse.Z32);
             a.AZ = reinterpret_cast<const T*>(P.coarse.AZ32);
         }
-        a.L = P.coarse.L;
-        a.Ld = P.coarse.Ld;
+        a.Einv = P.coarse.Einv;
     }
     a.partial = g.partial;
     a.scal = g.scal;
@@ -645,8 +647,16 @@ static PcgOutcome run_pcg(PlanHolder& P, bool two, double tol, int maxit, T* zst
         if (launched >= maxit) break;   // defensive: device counter stops at maxit
         const int c = std::min(chunk, maxit - launched + 1);
         for (int i = 0; i < c; ++i) {
-            apply_A<T>(P, a.p, static_cast<T*>(P.pcg.q), P.pcg.flags + F_DONE);
-            const int sl = prof_begin(P, sizeof(T) == 8 ? ST_PCG64 : ST_PCG32);
+            // q = A p with p^T q fused into the scatter (scal[SC_PQ])
+            const bool f64 = sizeof(T) == 8;
+            int sl = prof_begin(P, f64 ? ST_TZ64 : ST_TZ32);
+            launch_toeplitz<T>(P, tz_of<T>(P), nullptr, a.p, tod_of<T>(P), P.pcg.flags + F_DONE, s);
+            prof_end(P, sl);
+            sl = prof_begin(P, f64 ? ST_SC64 : ST_SC32);
+            launch_scatter_dot<T>(P, tod_of<T>(P), static_cast<T*>(P.pcg.q), a.p, P.pcg.sc_part, P.pcg.sc_count,
+                                  P.pcg.scal + SC_PQ, P.pcg.flags + F_DONE, s);
+            prof_end(P, sl);
+            sl = prof_begin(P, f64 ? ST_PCG64 : ST_PCG32);
             launch_pcg<T>(1, P.ncomp, two, a, nb, s);
             prof_end(P, sl);
         }
@@ -797,12 +807,11 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
             }
         std::vector<double> Lf;
         if (!cholesky_lower(E, kcur, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
-        cd.L = dalloc<double>(Lf.size());
-        h2d(cd.L, Lf.data(), Lf.size() * 8, s);
-        std::vector<double> Ld((size_t)kcur);
-        for (int j = 0; j < kcur; ++j) Ld[(size_t)j] = 1.0 / Lf[(size_t)j * kcur + j];
-        cd.Ld = dalloc<double>(Ld.size());
-        h2d(cd.Ld, Ld.data(), Ld.size() * 8, s);
+        // E^-1 = L^-T L^-1 (FP64): applying it inside PCG is then one k x k matvec spread
+        // over the block instead of two sequential triangular solves in one warp
+        const std::vector<double> Einv = spd_inverse_from_cholesky(Lf, kcur);
+        cd.Einv = dalloc<double>(Einv.size());
+        h2d(cd.Einv, Einv.data(), Einv.size() * 8, s);
         cd.Z32 = dalloc<float>((size_t)kcur * P.n);
         cd.AZ32 = dalloc<float>((size_t)kcur * P.n);
         launch_convert_f64_to_f32(cd.Z64, cd.Z32, (int64_t)kcur * P.n, s);

@@ -284,21 +284,20 @@ __global__ void batch_scatter_kernel(const int32_t* __restrict__ off, const int3
                     a2 += ww.y * v;
                 }
             }
-            double s0 = a0, s1 = a1, s2 = a2;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                if constexpr (NC == 3) {
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                }
+            // exact FP32-pair warp trees (FP64 shuffles per pixel and RHS would make
+            // this kernel FP64-bound on GB300)
+            float h0 = a0, l0 = 0.f, h1 = a1, l1 = 0.f, h2 = a2, l2 = 0.f;
+            warp_pair_reduce(h0, l0);
+            if constexpr (NC == 3) {
+                warp_pair_reduce(h1, l1);
+                warp_pair_reduce(h2, l2);
             }
             if (lane == 0) {
                 float* w = W + (size_t)r * n + (int64_t)q * NC;
-                w[0] = (float)s0;
+                w[0] = h0 + l0;
                 if constexpr (NC == 3) {
-                    w[1] = (float)s1;
-                    w[2] = (float)s2;
+                    w[1] = h1 + l1;
+                    w[2] = h2 + l2;
                 }
             }
         }
@@ -321,15 +320,6 @@ void launch_batch_scatter(const Plan& P, const float* Z, float* W, int R, const 
 
 // --------------------------------------------------------------------- batched PCG
 
-// FP32-pair helpers (exact two-sum; see pcg.cu for why the wide reductions avoid FP64).
-__device__ __forceinline__ void bpair_add(float& hi, float& lo, float h2, float l2) {
-    const float s = hi + h2;
-    const float bv = s - hi;
-    const float e = (hi - (s - bv)) + (h2 - bv);
-    hi = s;
-    lo = lo + l2 + e;
-}
-
 // Totals over blocks of slot j for j < count (slots hold FP32 pairs), one warp per slot,
 // lanes over blocks in a fixed order; result (FP64) in sh[j].
 __device__ void batch_totals(const double* part, int stride, int slot0, int count, double* sh) {
@@ -338,13 +328,13 @@ __device__ void batch_totals(const double* part, int stride, int slot0, int coun
         float hi = 0.f, lo = 0.f;
         for (unsigned b = l; b < gridDim.x; b += 32) {
             const float2 p = __ldcg(reinterpret_cast<const float2*>(part + (size_t)b * stride + slot0 + j));
-            bpair_add(hi, lo, p.x, p.y);
+            pair_add(hi, lo, p.x, p.y);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
             const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            bpair_add(hi, lo, h2, l2);
+            pair_add(hi, lo, h2, l2);
         }
         if (l == 0) sh[j] = (double)hi + (double)lo;
     }
@@ -368,7 +358,7 @@ __device__ void batch_dots(const float* A_, const float* B_, int64_t n, int64_t 
         for (int o = 16; o > 0; o >>= 1) {
             const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
             const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            bpair_add(hi, lo, h2, l2);
+            pair_add(hi, lo, h2, l2);
         }
         if (l == 0) *reinterpret_cast<float2*>(part_row + r) = make_float2(hi, lo);
     }

@@ -187,4 +187,24 @@ bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L)
     return true;
 }
 
+std::vector<double> spd_inverse_from_cholesky(const std::vector<double>& L, int k) {
+    // Y = L^-1 by forward substitution on the identity (lower triangular), E^-1 = Y^T Y
+    std::vector<double> Y((size_t)k * k, 0.0);
+    for (int c = 0; c < k; ++c) {
+        for (int i = c; i < k; ++i) {
+            double v = i == c ? 1.0 : 0.0;
+            for (int j = c; j < i; ++j) v -= L[(size_t)i * k + j] * Y[(size_t)j * k + c];
+            Y[(size_t)i * k + c] = v / L[(size_t)i * k + i];
+        }
+    }
+    std::vector<double> inv((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = 0.0;
+            for (int m = std::max(i, j); m < k; ++m) v += Y[(size_t)m * k + i] * Y[(size_t)m * k + j];
+            inv[(size_t)i * k + j] = inv[(size_t)j * k + i] = v;
+        }
+    return inv;
+}
+
 }  // namespace mm

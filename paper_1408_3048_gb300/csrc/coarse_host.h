@@ -18,5 +18,7 @@ bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::v
 
 // E = L L^T, row-major lower L; false if E is not positive definite.
 bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L);
+// E^-1 (row-major, symmetric) from the lower Cholesky factor L of E: L^-T L^-1.
+std::vector<double> spd_inverse_from_cholesky(const std::vector<double>& L, int k);
 
 }  // namespace mm

@@ -39,8 +39,7 @@ struct CoarseDev {
     double* AZ64 = nullptr;      // [k][n]
     float* Z32 = nullptr;        // [k][n]
     float* AZ32 = nullptr;       // [k][n]
-    double* L = nullptr;         // [k][k] lower Cholesky factor of E (row-major)
-    double* Ld = nullptr;        // [k] reciprocal diagonal of L
+    double* Einv = nullptr;      // [k][k] E^-1 = L^-T L^-1 from the Cholesky factor (row-major)
     std::vector<double> ritz;    // k smallest Ritz values
 };
 
@@ -62,6 +61,8 @@ struct PcgDev {
     double* hist_rz = nullptr;     // [maxhist]
     double* hist_rr = nullptr;     // [maxhist]
     int maxhist = 0;
+    double* sc_part = nullptr;     // [scatter blocks] p^T q partials of the fused scatter
+    unsigned* sc_count = nullptr;  // arrival counter of that scatter's last-block sum
 };
 
 // Per-stage CUDA-event timers (enabled by mm_profile).
@@ -187,6 +188,13 @@ template <typename T>
 void launch_gather(const Plan& P, const T* x, T* y, cudaStream_t s);
 template <typename T>
 void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream_t s);
+// w = P^T z and, fused, *pq = p^T w (FP64, fixed summation order: warp partials over their
+// pixels, block partials in part[], summed in block order by the last block to finish,
+// which also resets *count to 0).  part holds scatter_blocks(P) doubles.
+template <typename T>
+void launch_scatter_dot(const Plan& P, const T* z, T* w, const T* p, double* part, unsigned* count, double* pq,
+                        const int* done, cudaStream_t s);
+int scatter_blocks(const Plan& P);
 void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
 template <typename T>
 void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);

@@ -22,24 +22,6 @@ namespace mm {
 // additions.  All trees are fixed (xor shuffles, lanes over blocks in order), so every
 // block obtains bit-identical scalars.
 
-// (hi, lo) += (h2, l2) with a two-sum of the high parts; symmetric in its operands.
-__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
-    const float s = hi + h2;
-    const float bv = s - hi;
-    const float e = (hi - (s - bv)) + (h2 - bv);
-    hi = s;
-    lo = lo + l2 + e;
-}
-
-__device__ __forceinline__ void warp_pair_reduce(float& hi, float& lo) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        pair_add(hi, lo, h2, l2);
-    }
-}
-
 __device__ __forceinline__ double warp_sum64(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -123,11 +105,12 @@ __device__ void coarse_partials(const PcgArgs<T>& a, const T* r, int64_t e0, int
     }
 }
 
-// v = E^-1 u with E = L L^T (L row-major k x k, reciprocal diagonal in Ld), u = Z^T r
-// from the block partials.  Warps reduce the k coarse slots (lanes over blocks, fixed
-// order), then warp 0 runs the two triangular solves with lanes owning rows l, l + 32.
+// v = E^-1 u, u = Z^T r from the block partials (warps reduce the k coarse slots, lanes
+// over blocks in a fixed order), then the k x k matvec with the stored E^-1: warp w owns
+// rows w, w + nw, ...; lanes split the row, FP64 throughout.
 template <typename T>
 __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
+    __shared__ double u_sh[KMAX];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < a.k; j += nw) {
         const double* col = a.partial + S_COARSE + j;
@@ -138,41 +121,21 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
                 pair_add(hi, lo, p.x, p.y);
             }
             warp_pair_reduce(hi, lo);
-            if (l == 0) v_sh[j] = (double)hi + (double)lo;
+            if (l == 0) u_sh[j] = (double)hi + (double)lo;
         } else {
             double s = 0.0;
             for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(col + (size_t)b * PSTRIDE);
             s = warp_sum64(s);
-            if (l == 0) v_sh[j] = s;
+            if (l == 0) u_sh[j] = s;
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double u0 = l < a.k ? v_sh[l] : 0.0;
-        double u1 = l + 32 < a.k ? v_sh[l + 32] : 0.0;
-        // forward: L y = u
-        for (int j = 0; j < a.k; ++j) {
-            const double uj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
-            const double yj = uj * a.Ld[j];
-            if (l == (j & 31)) {
-                if (j < 32) u0 = yj; else u1 = yj;
-            }
-            if (l > j && l < a.k) u0 -= a.L[(size_t)l * a.k + j] * yj;
-            if (l + 32 > j && l + 32 < a.k) u1 -= a.L[(size_t)(l + 32) * a.k + j] * yj;
-        }
-        // backward: L^T v = y
-        for (int j = a.k - 1; j >= 0; --j) {
-            const double yj = __shfl_sync(0xffffffffu, j < 32 ? u0 : u1, j & 31);
-            const double vj = yj * a.Ld[j];
-            if (l == (j & 31)) {
-                if (j < 32) u0 = vj; else u1 = vj;
-            }
-            if (l < j && l < a.k) u0 -= a.L[(size_t)j * a.k + l] * vj;
-            if (l + 32 < j && l + 32 < a.k) u1 -= a.L[(size_t)j * a.k + l + 32] * vj;
-        }
-        __syncwarp();
-        if (l < a.k) v_sh[l] = u0;
-        if (l + 32 < a.k) v_sh[l + 32] = u1;
+    for (int i = w; i < a.k; i += nw) {
+        const double* row = a.Einv + (size_t)i * a.k;
+        double s = 0.0;
+        for (int j = l; j < a.k; j += 32) s += __ldg(row + j) * u_sh[j];
+        s = warp_sum64(s);
+        if (l == 0) v_sh[i] = s;
     }
     __syncthreads();
 }
@@ -285,13 +248,8 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     int p0, p1;
     block_pixels(a.npix, p0, p1);
     const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
-    // phase A: p^T q
-    DotAcc<T> pacc;
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) pacc.add(a.p[i], a.q[i]);
-    const double pq = block_total(pacc, sh);
-    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_PQ] = pq;
-    if (!grid_sync(a.bar, a.flags)) return;
-    const double pqt = grid_total(a.partial, S_PQ, sh);
+    // p^T q comes from the scatter that formed q = A p (its last block summed it)
+    const double pqt = __ldcg(a.scal + SC_PQ);
     const double rho = a.scal[SC_RHO];
     if (!(pqt > 0.0) || !isfinite(pqt)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {

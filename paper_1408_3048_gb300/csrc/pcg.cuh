@@ -13,8 +13,8 @@ constexpr int DOT_BLOCKS = 304;   // blocks of the stand-alone dot / vector kern
 constexpr int S_PQ = 0, S_RR = 1, S_RZ = 2, S_COARSE = 3;
 constexpr int PSTRIDE = S_COARSE + KMAX;
 
-// device scalars
-constexpr int SC_RHO = 0, SC_BB = 1, SC_RR = 2, SC_TOL2 = 3;
+// device scalars (SC_PQ: p^T q, written by the scatter that forms q = A p)
+constexpr int SC_RHO = 0, SC_BB = 1, SC_RR = 2, SC_TOL2 = 3, SC_PQ = 4;
 // device flags
 constexpr int F_DONE = 0, F_STATUS = 1, F_ITER = 2;
 
@@ -32,8 +32,7 @@ struct PcgArgs {
     int k;               // coarse dimension (TWOLEVEL)
     const T* Z;          // [k][n]
     const T* AZ;         // [k][n]
-    const double* L;     // Cholesky factor of E, row-major [k][k]
-    const double* Ld;    // 1 / L_jj, [k]
+    const double* Einv;  // E^-1 from the Cholesky factor of E, row-major [k][k]
     double* partial;     // [grid][PSTRIDE]
     double* scal;
     int* flags;
@@ -94,6 +93,25 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* flags) {
 // accumulated as an unevaluated FP32 pair (hi, lo) with a two-sum, so the per-thread
 // partial carries ~48 bits; it is converted to FP64 once for the block and grid sums.
 // (Per-element FP32 -> FP64 conversions would run on the FP64 pipe, 1/64 of FP32 rate.)
+// (hi, lo) += (h2, l2) with a two-sum of the high parts; symmetric in its operands.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
+    const float s = hi + h2;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (h2 - bv);
+    hi = s;
+    lo = lo + l2 + e;
+}
+
+// Fixed xor-shuffle tree over the warp on (hi, lo) pairs; every lane gets the total.
+__device__ __forceinline__ void warp_pair_reduce(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        pair_add(hi, lo, h2, l2);
+    }
+}
+
 template <typename T> struct DotAcc;
 template <> struct DotAcc<double> {
     double s = 0.0;

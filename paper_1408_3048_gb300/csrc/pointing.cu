@@ -6,7 +6,10 @@
 //                           the result is bit-reproducible
 //   M_BD     Eq. 10: B_p = sum_{t in p} t^(i(t))_0 w_t w_t^T, stored inverted
 //                           (symmetric, packed a00 a01 a02 a11 a12 a22)
+#include <algorithm>
+
 #include "mm_internal.h"
+#include "pcg.cuh"
 
 namespace mm {
 
@@ -73,66 +76,180 @@ template void launch_gather<float>(const Plan&, const float*, float*, cudaStream
 
 // ---------------------------------------------------------------------------- scatter
 // One warp per observed pixel.  Lanes stride over the pixel's sorted samples and keep
-// per-lane partial sums in T; the warp tree (xor shuffles, fixed order) runs in double.
-template <typename T, int NC>
-__global__ void scatter_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ tsort,
-                               const typename V2<T>::type* __restrict__ ws,
-                               const T* __restrict__ z, T* __restrict__ w, int npix,
-                               const int* done) {
+// per-lane partial sums in T.  The warp tree (xor shuffles, fixed order) runs in double
+// for T = double and on exact FP32 (hi, lo) pairs for T = float -- GB300 issues a warp's
+// FP64 instruction at 1/64 of the FP32 rate, and a double tree per pixel would cost more
+// SM time than the pixel's memory traffic.  The sample loop issues SCATTER_U (index,
+// weight) loads per lane before their dependent TOD loads, so each warp keeps several
+// random TOD reads in flight; every lane still adds its samples j, j + 32, j + 64, ... in
+// ascending order (the result does not depend on the unrolling).
+constexpr int SCATTER_U = 4;
+constexpr int SCATTER_THREADS = 256;
+
+// Optional fused dot product with the output (DOT): *pq = sum_q p_q . w_q.
+struct ScatterDot {
+    const void* p;      // T[n]
+    double* part;       // [gridDim.x]
+    unsigned* count;
+    double* pq;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_total(T v) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    } else {
+        float hi = v, lo = 0.f;
+        warp_pair_reduce(hi, lo);
+        return hi + lo;
+    }
+}
+
+template <typename T, int NC, bool DOT>
+__global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t* __restrict__ off,
+                                                                  const int32_t* __restrict__ tsort,
+                                                                  const typename V2<T>::type* __restrict__ ws,
+                                                                  const T* __restrict__ z, T* __restrict__ w,
+                                                                  int npix, const int* done, ScatterDot sd) {
+    using W2 = typename V2<T>::type;
     if (done != nullptr && *(volatile const int*)done) return;
     const int lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
+    DotAcc<T> dacc;   // DOT: this warp's pixels, ascending (lane 0)
     for (int q = blockIdx.x * warps + (threadIdx.x >> 5); q < npix; q += gridDim.x * warps) {
         const int b = off[q];
         const int e = off[q + 1];
         T a0 = 0, a1 = 0, a2 = 0;
-        for (int j = b + lane; j < e; j += 32) {
-            const T v = z[tsort[j]];
+        int j = b + lane;
+        for (; j + 32 * (SCATTER_U - 1) < e; j += 32 * SCATTER_U) {
+            int t[SCATTER_U];
+            W2 ww[SCATTER_U];
+            T v[SCATTER_U];
+#pragma unroll
+            for (int u = 0; u < SCATTER_U; ++u) t[u] = __ldg(tsort + j + 32 * u);
+            if constexpr (NC == 3) {
+#pragma unroll
+                for (int u = 0; u < SCATTER_U; ++u) ww[u] = __ldg(ws + j + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < SCATTER_U; ++u) v[u] = z[t[u]];
+#pragma unroll
+            for (int u = 0; u < SCATTER_U; ++u) {
+                a0 += v[u];
+                if constexpr (NC == 3) {
+                    a1 += ww[u].x * v[u];
+                    a2 += ww[u].y * v[u];
+                }
+            }
+        }
+        for (; j < e; j += 32) {
+            const T v = z[__ldg(tsort + j)];
             a0 += v;
             if constexpr (NC == 3) {
-                const typename V2<T>::type ww = ws[j];
+                const W2 ww = __ldg(ws + j);
                 a1 += ww.x * v;
                 a2 += ww.y * v;
             }
         }
-        double s0 = a0, s1 = a1, s2 = a2;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            if constexpr (NC == 3) {
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            }
+        const T s0 = warp_total<T>(a0);
+        T s1 = 0, s2 = 0;
+        if constexpr (NC == 3) {
+            s1 = warp_total<T>(a1);
+            s2 = warp_total<T>(a2);
         }
         if (lane == 0) {
             if constexpr (NC == 1) {
-                w[q] = (T)s0;
+                w[q] = s0;
+                if constexpr (DOT) dacc.add(static_cast<const T*>(sd.p)[q], s0);
             } else {
-                w[3 * (int64_t)q] = (T)s0;
-                w[3 * (int64_t)q + 1] = (T)s1;
-                w[3 * (int64_t)q + 2] = (T)s2;
+                w[3 * (int64_t)q] = s0;
+                w[3 * (int64_t)q + 1] = s1;
+                w[3 * (int64_t)q + 2] = s2;
+                if constexpr (DOT) {
+                    const T* pp = static_cast<const T*>(sd.p) + 3 * (int64_t)q;
+                    dacc.add(pp[0], s0);
+                    dacc.add(pp[1], s1);
+                    dacc.add(pp[2], s2);
+                }
+            }
+        }
+    }
+    if constexpr (DOT) {
+        __shared__ DotAcc<T> wacc[SCATTER_THREADS / 32];
+        __shared__ double wsum[SCATTER_THREADS / 32];
+        __shared__ bool last;
+        if (lane == 0) wacc[threadIdx.x >> 5] = dacc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            for (int i = 0; i < warps; ++i) b += wacc[i].total();
+            sd.part[blockIdx.x] = b;
+            __threadfence();
+            last = atomicAdd(sd.count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last) {
+            // fixed partition of the block partials over the warps, then warps in order
+            __threadfence();
+            const int per = (gridDim.x + warps - 1) / warps;
+            const int w0 = (threadIdx.x >> 5) * per;
+            const int w1 = min((int)gridDim.x, w0 + per);
+            double t = 0.0;
+            for (int i = w0 + lane; i < w1; i += 32) t += __ldcg(sd.part + i);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) wsum[threadIdx.x >> 5] = t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int i = 0; i < warps; ++i) tot += wsum[i];
+                *sd.pq = tot;
+                *sd.count = 0;
             }
         }
     }
 }
 
-template <typename T>
-void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream_t s) {
-    if (P.npix_obs == 0) return;
-    const int th = 256;
-    const int64_t warps_needed = P.npix_obs;
-    int g = (int)((warps_needed + (th / 32) - 1) / (th / 32));
-    if (g > P.num_sms * 32) g = P.num_sms * 32;
+// Grid: one warp per pixel up to 8 resident blocks of 256 threads per SM (full
+// occupancy), warps loop over pixels beyond that.
+int scatter_blocks(const Plan& P) {
+    const int wpb = SCATTER_THREADS / 32;
+    int g = (int)(((int64_t)P.npix_obs + wpb - 1) / wpb);
+    return std::max(1, std::min(g, P.num_sms * 8));
+}
+
+template <typename T, bool DOT>
+static void scatter_launch(const Plan& P, const T* z, T* w, const int* done, ScatterDot sd, cudaStream_t s) {
+    const int g = scatter_blocks(P);
     if (P.ncomp == 1)
-        scatter_kernel<T, 1><<<g, th, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs, done);
+        scatter_kernel<T, 1, DOT><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs, done, sd);
     else
-        scatter_kernel<T, 3><<<g, th, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z, w,
-                                               P.npix_obs, done);
+        scatter_kernel<T, 3, DOT><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z, w,
+                                                                P.npix_obs, done, sd);
     check_cuda(cudaGetLastError(), "scatter launch");
     note_launch();
 }
+
+template <typename T>
+void launch_scatter(const Plan& P, const T* z, T* w, const int* done, cudaStream_t s) {
+    if (P.npix_obs == 0) return;
+    scatter_launch<T, false>(P, z, w, done, ScatterDot{nullptr, nullptr, nullptr, nullptr}, s);
+}
 template void launch_scatter<double>(const Plan&, const double*, double*, const int*, cudaStream_t);
 template void launch_scatter<float>(const Plan&, const float*, float*, const int*, cudaStream_t);
+
+template <typename T>
+void launch_scatter_dot(const Plan& P, const T* z, T* w, const T* p, double* part, unsigned* count, double* pq,
+                        const int* done, cudaStream_t s) {
+    if (P.npix_obs == 0) throw Error{MM_ERR_ARG, "no observed pixels"};
+    scatter_launch<T, true>(P, z, w, done, ScatterDot{p, part, count, pq}, s);
+}
+template void launch_scatter_dot<double>(const Plan&, const double*, double*, const double*, double*, unsigned*,
+                                         double*, const int*, cudaStream_t);
+template void launch_scatter_dot<float>(const Plan&, const float*, float*, const float*, double*, unsigned*,
+                                        double*, const int*, cudaStream_t);
 
 // ------------------------------------------------------------------------ M_BD build
 __device__ __forceinline__ int interval_of(const int64_t* ioff, int K, int64_t t) {

@@ -271,8 +271,8 @@ def test_autotuned_blocks(case):
     plan = _plan(scan, autotune=True)
     ms64, ms32 = plan.autotune_ms()
     for ms, block in ((ms64, plan.fft_block_f64), (ms32, plan.fft_block_f32)):
-        if len(ms) >= 2:
-            assert block == 2 ** min(ms, key=ms.get)
+        if len(ms) >= 2:   # the kept block is a fastest one (ties keep the cheaper model cost)
+            assert ms[block.bit_length() - 1] == min(ms.values())
         assert 1 <= len(ms) <= 3 or len(ms) == 0
     rng = np.random.default_rng(21)
     x = rng.standard_normal(pr.n)
