@@ -137,6 +137,42 @@ def fft_tiles(scan, B):
     return int(np.sum((lens + Lv - 1) // Lv))
 
 
+# Sources whose text fixes each profiled kernel: the DRAM traffic recorded from an ncu capture
+# (a "traffic:" line in profiles/*.md) is reported only while their hash is unchanged.
+KERNEL_SOURCES = {
+    "toeplitz_f32": ["toeplitz.cuh", "toeplitz_f32.cu"],
+    "toeplitz_f64": ["toeplitz.cuh", "toeplitz_f64.cu"],
+    "scatter_f32": ["pointing.cu"],
+    "scatter_f64": ["pointing.cu"],
+    "pcg_f32": ["pcg.cu", "pcg.cuh"],
+    "pcg_f64": ["pcg.cu", "pcg.cuh"],
+}
+
+
+def recorded_traffic(kernel):
+    """(bytes per launch, profile file) from profiles/*.md, or (None, why)."""
+    import glob
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None, "no source map"
+    d = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1408_3048_gb300", "csrc", f), "rb") as fh:
+            d.update(fh.read())
+    cur = d.hexdigest()
+    for md in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(md) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == kernel:
+                    kv = dict(x.split("=", 1) for x in parts[2:])
+                    if kv.get("source_sha256") == cur:
+                        return int(kv["dram_bytes_per_launch"]), os.path.relpath(md, ROOT)
+                    return None, f"{os.path.relpath(md, ROOT)} predates the current kernel source"
+    return None, "no ncu capture recorded"
+
+
 def roofline(kernel, ms, plan, scan, hbm, peak_src):
     """Algorithmic bytes and flops of one launch of `kernel` over its measured duration;
     the bound is whichever of HBM or ALU the launch uses the larger fraction of."""
@@ -160,8 +196,9 @@ def roofline(kernel, ms, plan, scan, hbm, peak_src):
         byts = 8 * n * s
     t = ms * 1e-3
     gbs = byts / t / 1e9
+    traffic, tsrc = recorded_traffic(kernel)
     out = {"bound": "hbm", "kernel": kernel, "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-           "frac": round(gbs / hbm, 4), "traffic": None,
+           "frac": round(gbs / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)", "bytes_per_launch": int(byts),
            "ms_per_launch": round(ms, 4)}
     if flops is not None:
@@ -171,7 +208,7 @@ def roofline(kernel, ms, plan, scan, hbm, peak_src):
                       "frac": round(frac_alu, 4), "flops_per_launch": int(flops)}
         if frac_alu > out["frac"]:
             out = {"bound": "alu", "kernel": kernel, "achieved": round(tf, 3), "peak": ALU_PEAK[key] / 1e12,
-                   "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": None,
+                   "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": traffic, "traffic_source": tsrc,
                    "peak_source": ("recipe nominal GB300 FP64 rate" if key == "f64" else
                                    "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
                    "flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
