@@ -119,5 +119,40 @@ def deflation_apriori(prob):
     return Z
 
 
+def deflation_apriori_merged(prob, r):
+    """Z_S with its K interval columns combined into r groups (Sec. 3.3.1: the column
+    count may be reduced by merging stationary periods, keeping every nonzero row's sum
+    at 1).  Groups are runs of consecutive intervals: interval i joins group
+    floor(i r / K); a merged column is the sum of its members' columns."""
+    Z = deflation_apriori(prob)
+    K = Z.shape[1]
+    if not 1 <= r <= K:
+        raise ValueError("need 1 <= r <= K")
+    G = np.zeros((K, r), dtype=np.float64)
+    G[np.arange(K), (np.arange(K) * r) // K] = 1.0
+    return Z @ G
+
+
+def independent_columns(Z, drop_rtol=1e-10):
+    """Columns of Z in order, skipping each column whose component orthogonal to the
+    kept ones has norm < drop_rtol times the largest such norm kept so far (or is 0):
+    Z_S has dependent columns whenever intervals see the same hit fractions, and E =
+    Z^T A Z must be invertible (Eq. 12).  Gram-Schmidt, projected twice."""
+    Z = np.asarray(Z, dtype=np.float64)
+    Q = np.zeros((Z.shape[0], 0))
+    kept, maxpiv = [], 0.0
+    for j in range(Z.shape[1]):
+        v = Z[:, j].copy()
+        for _ in range(2):
+            v -= Q @ (Q.T @ v)
+        piv = np.linalg.norm(v)
+        if piv == 0.0 or piv < drop_rtol * maxpiv:
+            continue
+        kept.append(j)
+        Q = np.column_stack([Q, v / piv])
+        maxpiv = max(maxpiv, piv)
+    return Z[:, kept], kept
+
+
 __all__ = ["BlockJacobi", "TwoLevel", "lanczos_tridiagonal", "ritz_coarse_space",
-           "deflation_apriori"]
+           "deflation_apriori", "deflation_apriori_merged", "independent_columns"]

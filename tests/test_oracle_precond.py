@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import precond
+from paper_1408_3048_gb300 import synth
 from oracle.pcg import pcg
 from problems import oracle_problem, tiny_scan
 
@@ -111,6 +112,58 @@ def test_apriori_rows_sum_to_one(prob):
     np.testing.assert_allclose(Z[0::nc].sum(axis=1), 1.0, rtol=0, atol=1e-15)
     if nc == 3:
         assert np.all(Z[1::3] == 0) and np.all(Z[2::3] == 0)
+
+
+def test_apriori_merged_brute_force(prob):
+    # merged Z_S against a direct count over samples: column g = the fraction of each
+    # observed pixel's kept samples that fall in group g's intervals (Sec. 3.3.1)
+    K = prob.offsets.size - 1
+    nc = prob.ncomp
+    for r in sorted({1, 2, max(1, K // 2), K}):
+        Z = precond.deflation_apriori_merged(prob, r)
+        assert Z.shape == (prob.n, r)
+        cnt = np.zeros((prob.npix_obs, r))
+        for i in range(K):
+            g = i * r // K
+            for t in range(int(prob.offsets[i]), int(prob.offsets[i + 1])):
+                q = prob.pix_c[t]
+                if q >= 0:
+                    cnt[q, g] += 1.0
+        np.testing.assert_array_equal(Z[0::nc], cnt / cnt.sum(axis=1, keepdims=True))
+        if nc == 3:
+            assert np.all(Z[1::3] == 0) and np.all(Z[2::3] == 0)
+        np.testing.assert_allclose(Z[0::nc].sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    # r = K is the unmerged Z_S; r = 1 is the temperature vector of ones (Eq. 15)
+    np.testing.assert_array_equal(precond.deflation_apriori_merged(prob, K), precond.deflation_apriori(prob))
+    ones = np.zeros(prob.n)
+    ones[0::nc] = 1.0
+    np.testing.assert_allclose(precond.deflation_apriori_merged(prob, 1)[:, 0], ones, rtol=0, atol=1e-15)
+
+
+def test_apriori_dependent_columns_dropped(prob):
+    # every interval of the tiny raster sees each pixel equally often: all columns of Z_S
+    # are equal, so one column survives and it spans the temperature ones vector
+    Z = precond.deflation_apriori(prob)
+    Zk, kept = precond.independent_columns(Z)
+    assert kept == [0]
+    Z2 = np.column_stack([Z[:, 0], 2.0 * Z[:, 0] + 1e-3 * np.arange(prob.n), Z[:, 0] + Z[:, 0]])
+    assert precond.independent_columns(Z2)[1] == [0, 1]
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_apriori_two_level_invariants(ncomp):
+    # uneven intervals cut the sweeps mid-way, so the columns of Z_S differ; M_2lvl A Z = Z
+    # holds for the a priori space (the coarse correction is exact on range Z)
+    scan = synth.raster_scan(16, 16, 2, 6000, ncomp, 3, 60, [(1.0, 1.0, 1.0), (0.8, 1.5, 1.5)],
+                             det_psd=[0, 1], uneven=(1000, 3000), seed=7)
+    prob = oracle_problem(scan)
+    K = prob.offsets.size - 1
+    Z, kept = precond.independent_columns(precond.deflation_apriori_merged(prob, min(K, 4)))
+    assert len(kept) >= 2
+    bd = precond.BlockJacobi(prob)
+    tl = precond.TwoLevel(prob, bd, Z)
+    for j in range(Z.shape[1]):
+        np.testing.assert_allclose(tl.apply(prob.A(Z[:, j])), Z[:, j], rtol=0, atol=1e-9 * np.abs(Z[:, j]).max())
 
 
 def test_ones_near_nullspace_with_one_over_f():
