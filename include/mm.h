@@ -215,7 +215,9 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
  * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), its k
  * smallest Ritz pairs, Ritz vectors Z = sum_j (-1)^j z_j / sqrt(r_j^T z_j) s_j,
  * Euclidean orthonormalisation (columns with R_jj < 1e-10 max R_jj dropped), then
- * AZ = A Z (FP64) and E = Z^T A Z, Cholesky-factored in FP64 (App. C, "Constructing").
+ * AZ = A Z (FP64) and E = Z^T A Z, Cholesky-factored in FP64 (App. C, "Constructing"),
+ * kept as E^-1 = L^-T L^-1 for the PCG kernels.  A failed build leaves the previous
+ * coarse space (or none) in place.
  *   k       requested coarse dimension, 1 <= k <= 64.
  *   bprime  device double[n] right-hand side of the first solve, or NULL for b' = the
  *           b of the last mm_solve (MM_ERR_STATE if there was none).
@@ -224,11 +226,28 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
 mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bprime,
                           double tol, int maxit);
 
-/* Kept coarse dimension and the k smallest Ritz values (host double[k], may be NULL). */
+/*
+ * Build the a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) instead: column j of the
+ * unmerged Z_S holds, for each observed pixel, the fraction of its samples inside
+ * stationary interval j (temperature rows; Q/U rows 0), so each temperature row sums to
+ * 1.  Its K columns are merged into r groups of consecutive intervals (interval i joins
+ * group floor(i r / K); merged column = sum of its members, rows still sum to 1), as the
+ * paper allows to reduce the coarse dimension.  Columns dependent on earlier ones
+ * (Cholesky pivot of Z^T Z below 1e-10 times the largest kept pivot; intervals that see
+ * the same hit fractions give equal columns) are dropped; the kept columns are used as
+ * they are.  Then AZ, E and E^-1 as for mm_build_coarse.  No solve is needed.
+ *   r       1 <= r <= min(64, K).
+ * Errors: MM_ERR_ARG for r out of range, MM_ERR_NOT_SPD when E is not positive definite.
+ */
+mm_status mm_build_coarse_apriori(mm_plan_t plan, int r);
+
+/* Kept coarse dimension and, for the a posteriori space, the k smallest Ritz values
+ * (host double[k], may be NULL; nothing is written for the a priori space). */
 mm_status mm_coarse_info(mm_plan_t plan, int32_t* k_kept, double* ritz_values);
 
-/* The orthonormal coarse basis Z (FP64), column j at Z[j*n .. j*n + n), host or device
- * double[k_kept * n].  MM_ERR_STATE before mm_build_coarse. */
+/* The coarse basis Z (FP64), column j at Z[j*n .. j*n + n), host or device
+ * double[k_kept * n]: orthonormal for the a posteriori space, the merged hit fractions
+ * for the a priori one.  MM_ERR_STATE before a coarse space was built. */
 mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
 
 /*

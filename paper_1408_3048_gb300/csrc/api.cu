@@ -715,6 +715,88 @@ static std::vector<double> gram_host(PlanHolder& P, const double* A, int ka, con
     }
 }
 
+// Takes Z (FP64 [k][n], device, ownership passes here), forms AZ = A Z (FP64),
+// E = Z^T A Z (symmetrised), its Cholesky factor and E^-1 = L^-T L^-1 (FP64: inside PCG
+// the coarse solve is then one k x k matvec spread over the block instead of two
+// sequential triangular solves in one warp), and the FP32 copies of Z and AZ (App. C,
+// "Constructing").  P.coarse is replaced only when every step succeeded.
+static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> ritz) {
+    cudaStream_t s = P.stream;
+    CoarseDev cd;
+    cd.k = k;
+    cd.ritz = std::move(ritz);
+    cd.Z64 = Z;
+    try {
+        cd.AZ64 = dalloc<double>((size_t)k * P.n);
+        for (int j = 0; j < k; ++j) apply_A<double>(P, cd.Z64 + (size_t)j * P.n, cd.AZ64 + (size_t)j * P.n, nullptr);
+        std::vector<double> E = gram_host(P, cd.Z64, k, cd.AZ64, k);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < i; ++j) {
+                const double v = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
+                E[(size_t)i * k + j] = E[(size_t)j * k + i] = v;
+            }
+        std::vector<double> Lf;
+        if (!cholesky_lower(E, k, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
+        const std::vector<double> Einv = spd_inverse_from_cholesky(Lf, k);
+        cd.Einv = dalloc<double>(Einv.size());
+        h2d(cd.Einv, Einv.data(), Einv.size() * 8, s);
+        cd.Z32 = dalloc<float>((size_t)k * P.n);
+        cd.AZ32 = dalloc<float>((size_t)k * P.n);
+        launch_convert_f64_to_f32(cd.Z64, cd.Z32, (int64_t)k * P.n, s);
+        launch_convert_f64_to_f32(cd.AZ64, cd.AZ32, (int64_t)k * P.n, s);
+        sync(s);
+    } catch (...) {
+        free_coarse(cd);
+        throw;
+    }
+    free_coarse(P.coarse);
+    P.coarse = cd;
+}
+
+// The a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) with its K interval columns
+// merged into r groups of consecutive intervals (interval i -> group floor(i r / K); a
+// merged column is the sum of its members, so observed temperature rows still sum to 1,
+// Q/U rows are 0).  Columns dependent on earlier ones (Cholesky pivot of Z^T Z below
+// 1e-10 of the largest kept pivot) are dropped -- intervals that see the same hit
+// fractions give equal columns -- and the kept columns are used as they are (not
+// orthonormalised).
+static void build_coarse_apriori(PlanHolder& P, int r) {
+    cudaStream_t s = P.stream;
+    if (r < 1 || r > KMAX || r > P.K) throw Error{MM_ERR_ARG, "r must be in [1, min(64, K)]"};
+    double* Z = dalloc<double>((size_t)r * P.n);
+    double* C = nullptr;
+    double* Zk = nullptr;
+    try {
+        launch_apriori(P, r, Z, s);
+        const std::vector<double> G = gram_host(P, Z, r, Z, r);
+        std::vector<double> W;
+        std::vector<int> kept;
+        if (!cholesky_drop(G, r, 1e-10, W, kept) || kept.empty())
+            throw Error{MM_ERR_NUMERIC, "a priori coarse space has no independent column"};
+        const int kk = (int)kept.size();
+        // select the kept columns (a 0/1 combination through the same lincomb kernel)
+        std::vector<double> Sel((size_t)r * kk, 0.0);
+        for (int c = 0; c < kk; ++c) Sel[(size_t)kept[(size_t)c] * kk + c] = 1.0;
+        C = dalloc<double>(Sel.size());
+        h2d(C, Sel.data(), Sel.size() * 8, s);
+        Zk = dalloc<double>((size_t)kk * P.n);
+        launch_lincomb<double>(Z, r, P.n, C, kk, Zk, s);
+        sync(s);
+        dfree(C);
+        C = nullptr;
+        dfree(Z);
+        Z = nullptr;
+        double* Zt = Zk;
+        Zk = nullptr;
+        install_coarse(P, Zt, kk, {});
+    } catch (...) {
+        dfree(Z);
+        dfree(C);
+        dfree(Zk);
+        throw;
+    }
+}
+
 template <typename T>
 static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol, int maxit) {
     cudaStream_t s = P.stream;
@@ -790,33 +872,9 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
             Y2 = nullptr;
             kcur = knew;
         }
-        free_coarse(P.coarse);
-        CoarseDev& cd = P.coarse;
-        cd.k = kcur;
-        cd.ritz = theta;
-        cd.Z64 = Y;
+        double* Zk = Y;
         Y = nullptr;
-        cd.AZ64 = dalloc<double>((size_t)kcur * P.n);
-        for (int j = 0; j < kcur; ++j) apply_A<double>(P, cd.Z64 + (size_t)j * P.n, cd.AZ64 + (size_t)j * P.n, nullptr);
-        // E = Z^T A Z, symmetrised, Cholesky in FP64 (App. C)
-        std::vector<double> E = gram_host(P, cd.Z64, kcur, cd.AZ64, kcur);
-        for (int i = 0; i < kcur; ++i)
-            for (int j = 0; j < i; ++j) {
-                const double v = 0.5 * (E[(size_t)i * kcur + j] + E[(size_t)j * kcur + i]);
-                E[(size_t)i * kcur + j] = E[(size_t)j * kcur + i] = v;
-            }
-        std::vector<double> Lf;
-        if (!cholesky_lower(E, kcur, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
-        // E^-1 = L^-T L^-1 (FP64): applying it inside PCG is then one k x k matvec spread
-        // over the block instead of two sequential triangular solves in one warp
-        const std::vector<double> Einv = spd_inverse_from_cholesky(Lf, kcur);
-        cd.Einv = dalloc<double>(Einv.size());
-        h2d(cd.Einv, Einv.data(), Einv.size() * 8, s);
-        cd.Z32 = dalloc<float>((size_t)kcur * P.n);
-        cd.AZ32 = dalloc<float>((size_t)kcur * P.n);
-        launch_convert_f64_to_f32(cd.Z64, cd.Z32, (int64_t)kcur * P.n, s);
-        launch_convert_f64_to_f32(cd.AZ64, cd.AZ32, (int64_t)kcur * P.n, s);
-        sync(s);
+        install_coarse(P, Zk, kcur, theta);
     } catch (...) {
         dfree(zstore);
         dfree(Y);
@@ -1627,11 +1685,18 @@ mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bp
     });
 }
 
+mm_status mm_build_coarse_apriori(mm_plan_t plan, int r) {
+    return guarded(plan, [&] { build_coarse_apriori(*get(plan), r); });
+}
+
 mm_status mm_coarse_info(mm_plan_t plan, int32_t* k_kept, double* ritz_values) {
     return guarded(plan, [&] {
         PlanHolder* P = get(plan);
         if (k_kept) *k_kept = P->coarse.k;
-        if (ritz_values) std::copy(P->coarse.ritz.begin(), P->coarse.ritz.end(), ritz_values);
+        if (ritz_values) {
+            const size_t m = std::min(P->coarse.ritz.size(), (size_t)P->coarse.k);
+            std::copy(P->coarse.ritz.begin(), P->coarse.ritz.begin() + (std::ptrdiff_t)m, ritz_values);
+        }
     });
 }
 

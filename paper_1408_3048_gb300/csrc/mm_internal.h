@@ -196,6 +196,9 @@ void launch_scatter_dot(const Plan& P, const T* z, T* w, const T* p, double* par
                         const int* done, cudaStream_t s);
 int scatter_blocks(const Plan& P);
 void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
+// merged a priori coarse space Z_S (Sec. 3.3.1), r groups of consecutive intervals, into
+// Z [r][n] FP64 (zeroed here)
+void launch_apriori(const Plan& P, int r, double* Z, cudaStream_t s);
 template <typename T>
 void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);

@@ -330,6 +330,50 @@ void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s) {
     note_launch();
 }
 
+// --------------------------------------------------- a priori coarse space (Sec. 3.3.1)
+// Z[g][p * NC] = (kept samples of pixel p in intervals of group g) / (all kept samples of
+// p), interval i in group (i r) / K; Q/U rows stay 0 (Z is zeroed by the caller).  One
+// warp per pixel; lanes count into per-warp shared counters (integer, order-free).
+constexpr int APRIORI_THREADS = 256;
+constexpr int APRIORI_RMAX = 64;
+
+template <int NC>
+__global__ void __launch_bounds__(APRIORI_THREADS) apriori_kernel(const int32_t* __restrict__ off,
+                                                                  const int32_t* __restrict__ tsort,
+                                                                  const int64_t* __restrict__ ioff, int K, int r,
+                                                                  int npix, int64_t n, double* __restrict__ Z) {
+    __shared__ int cnt[APRIORI_THREADS / 32][APRIORI_RMAX];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    for (int q = blockIdx.x * warps + wib; q < npix; q += gridDim.x * warps) {
+        for (int g = lane; g < r; g += 32) cnt[wib][g] = 0;
+        __syncwarp();
+        const int b = off[q], e = off[q + 1];
+        for (int j = b + lane; j < e; j += 32) {
+            const int i = interval_of(ioff, K, tsort[j]);
+            atomicAdd(&cnt[wib][(int)(((int64_t)i * r) / K)], 1);
+        }
+        __syncwarp();
+        const double hits = (double)(e - b);
+        for (int g = lane; g < r; g += 32) Z[(size_t)g * n + (int64_t)q * NC] = (double)cnt[wib][g] / hits;
+        __syncwarp();
+    }
+}
+
+void launch_apriori(const Plan& P, int r, double* Z, cudaStream_t s) {
+    if (r < 1 || r > APRIORI_RMAX) throw Error{MM_ERR_ARG, "r must be in [1, 64]"};
+    check_cuda(cudaMemsetAsync(Z, 0, (size_t)r * P.n * 8, s), "memset Z");
+    if (P.npix_obs == 0) return;
+    const int g = std::max(1, std::min((P.npix_obs + 7) / 8, P.num_sms * 8));
+    if (P.ncomp == 1)
+        apriori_kernel<1><<<g, APRIORI_THREADS, 0, s>>>(P.csr_off, P.tsort, P.ioff, P.K, r, P.npix_obs, P.n, Z);
+    else
+        apriori_kernel<3><<<g, APRIORI_THREADS, 0, s>>>(P.csr_off, P.tsort, P.ioff, P.K, r, P.npix_obs, P.n, Z);
+    check_cuda(cudaGetLastError(), "a priori coarse launch");
+    note_launch();
+}
+
 // ------------------------------------------------------------------------ M_BD apply
 template <typename T, int NC>
 __global__ void bd_apply_kernel(const T* __restrict__ bd, const T* __restrict__ r, T* __restrict__ z,

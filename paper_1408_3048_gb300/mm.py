@@ -30,7 +30,7 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
-           "mm_solve_batch", "mm_autotune_read", "mm_batch_config"]
+           "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori"]
 
 
 class mm_psd(ctypes.Structure):
@@ -93,6 +93,7 @@ _SIGS = {
     "mm_apply_A_batch": (I32, [P, ctypes.c_int, P, P]),
     "mm_solve_batch": (I32, [P, P, ctypes.c_int, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
     "mm_autotune_read": (I32, [P, P, P]),
+    "mm_build_coarse_apriori": (I32, [P, ctypes.c_int]),
     "mm_batch_config": (I32, [P, ctypes.c_int32, P, P, P]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
@@ -226,6 +227,10 @@ def mm_precond(plan, kind, precision, r, z):
 
 def mm_build_coarse(plan, k, precision, bprime, tol, maxit):
     _check(lib().mm_build_coarse(plan, int(k), precision, _ptr(bprime), float(tol), int(maxit)), plan)
+
+
+def mm_build_coarse_apriori(plan, r):
+    _check(lib().mm_build_coarse_apriori(plan, int(r)), plan)
 
 
 def mm_coarse_info(plan):
@@ -387,6 +392,12 @@ class Plan:
         self._sync_in()
         mm_build_coarse(self.handle, k, precision, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
+
+    def build_coarse_apriori(self, r):
+        """A priori coarse space Z_S merged into r interval groups; returns the kept k."""
+        self._sync_in()
+        mm_build_coarse_apriori(self.handle, r)
+        return mm_coarse_info(self.handle)[0]
 
     def coarse_vectors(self):
         k, _ = mm_coarse_info(self.handle)

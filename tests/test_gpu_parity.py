@@ -202,6 +202,36 @@ def test_two_level(case):
     assert np.linalg.norm(b1 - pr.A(m2.cpu().numpy())) / np.linalg.norm(b1) <= 1e-6
 
 
+def test_two_level_apriori(case):
+    # a priori coarse space Z_S (Sec. 3.3.1) merged into r interval groups
+    name, scan, pr, plan = case
+    K = pr.offsets.size - 1
+    r = min(K, 8)
+    Zo, kept = oprec.independent_columns(oprec.deflation_apriori_merged(pr, r))
+    kk = plan.build_coarse_apriori(r)
+    assert kk == len(kept)
+    Zl = plan.coarse_vectors()
+    # the library counts merged hits directly; the oracle sums member fractions
+    np.testing.assert_allclose(Zl, Zo, rtol=0, atol=1e-15)
+    bd = oprec.BlockJacobi(pr)
+    tl = oprec.TwoLevel(pr, bd, Zl)
+    d1 = _data(scan, 1)
+    ref = pcg(pr.A, tl.apply, pr.rhs(d1), 1e-6, 3000)
+    m, st, status = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL)
+    assert status == mm.MM_OK
+    assert abs(st["iters"] - ref.iters) <= 2, (st["iters"], ref.iters)
+    assert _rel(m.cpu().numpy(), ref.x) <= 1e-6
+    r_ = np.random.default_rng(6).standard_normal(pr.n)
+    z = plan.precond(_cuda(r_), mm.MM_PREC_TWOLEVEL, mm.MM_FP64).cpu().numpy()
+    assert _rel(z, tl.apply(r_)) <= 1e-9
+    mz = plan.precond(plan.apply_A(_cuda(Zl[:, 0])), mm.MM_PREC_TWOLEVEL, mm.MM_FP64).cpu().numpy()
+    assert _rel(mz, Zl[:, 0]) <= 1e-8
+    with pytest.raises(mm.MMError) as e:
+        plan.build_coarse_apriori(K + 1 if K < 64 else 65)
+    assert e.value.status == mm.MM_ERR_ARG
+    assert plan.build_coarse_apriori(r) == kk     # a failed build left the space usable
+
+
 def test_errors_are_reported():
     scan = tiny_scan()
     with pytest.raises(mm.MMError) as e:
