@@ -89,13 +89,19 @@ def lanczos_tridiagonal(alphas, betas):
     return T
 
 
-def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10):
+def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
     """Reading R8.  zs[j] = z_j, rzs[j] = r_j^T z_j for j = 0..m-1.
-    Returns (Z with orthonormal columns, the k smallest Ritz values)."""
+    Returns (Z with orthonormal columns, the k smallest Ritz values).  With eps_tol the
+    Ritz pairs kept are those with value below eps_tol (Sec. 5: |Re lambda_i| < eps_tol,
+    the paper uses 0.2), at most k of them, smallest first."""
     m = len(alphas)
     T = lanczos_tridiagonal(alphas, betas)
     theta, S = np.linalg.eigh(T)
     kk = min(k, m)
+    if eps_tol is not None:
+        kk = min(kk, int(np.sum(np.abs(theta) < eps_tol)))
+        if kk == 0:
+            raise ValueError("no Ritz value below eps_tol")
     V = np.stack([((-1.0) ** j) * zs[j] / np.sqrt(rzs[j]) for j in range(m)], axis=1)
     Y = V @ S[:, :kk]
     Q, R = np.linalg.qr(Y)

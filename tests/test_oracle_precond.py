@@ -106,6 +106,23 @@ def test_lanczos_vectors_are_minv_orthonormal(prob):
     assert np.linalg.norm(Rm[:, :-1]) <= 1e-8 * np.linalg.norm(V)
 
 
+def test_ritz_threshold_selection(prob):
+    # eps_tol keeps exactly the Ritz pairs below the threshold (at most k), which are the
+    # leading columns of the k-smallest selection
+    b = prob.rhs(np.random.default_rng(3).standard_normal(prob.nt))
+    bd = precond.BlockJacobi(prob)
+    res = pcg(prob.A, bd.apply, b, 1e-10, 500, record=True)
+    Zall, th = precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 64)
+    eps = 0.5 * (th[2] + th[3])
+    Ze, the = precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 64, eps_tol=eps)
+    assert len(the) == 3 and np.all(the < eps)
+    np.testing.assert_allclose(the, th[:3], rtol=0, atol=0)
+    np.testing.assert_allclose(np.abs(Ze.T @ Zall[:, :3]), np.eye(3), atol=1e-8)
+    assert len(precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 2, eps_tol=eps)[1]) == 2
+    with pytest.raises(ValueError):
+        precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 64, eps_tol=0.5 * th[0])
+
+
 def test_apriori_rows_sum_to_one(prob):
     Z = precond.deflation_apriori(prob)
     nc = prob.ncomp
