@@ -227,6 +227,24 @@ mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bp
                           double tol, int maxit);
 
 /*
+ * mm_build_coarse with the paper's selection rule (Sec. 5): the Ritz pairs kept are those
+ * with |theta_i| < eps_tol (the paper uses 0.2), at most kmax of them, smallest first.
+ * MM_ERR_STATE when no Ritz value lies below eps_tol (the previous coarse space, if any,
+ * stays); MM_ERR_ARG for eps_tol <= 0.  Other arguments as mm_build_coarse.
+ */
+mm_status mm_build_coarse_eps(mm_plan_t plan, int kmax, double eps_tol, int precision, const double* bprime,
+                              double tol, int maxit);
+
+/*
+ * Install a given coarse basis Z (host or device double[k * n], column j at Z[j*n ..]):
+ * AZ = A Z, E = Z^T A Z, E^-1 as for mm_build_coarse -- to reuse a basis saved from an
+ * earlier plan of the same pointing (mm_coarse_vectors) without its construction solve.
+ * The columns must be linearly independent (MM_ERR_NOT_SPD otherwise).  1 <= k <= 64.
+ * The paper has no counterpart beyond reusing a coarse space across solves.
+ */
+mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k);
+
+/*
  * Build the a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) instead: column j of the
  * unmerged Z_S holds, for each observed pixel, the fraction of its samples inside
  * stationary interval j (temperature rows; Q/U rows 0), so each temperature row sums to

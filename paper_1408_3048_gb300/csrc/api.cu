@@ -798,7 +798,7 @@ static void build_coarse_apriori(PlanHolder& P, int r) {
 }
 
 template <typename T>
-static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol, int maxit) {
+static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol, int maxit, double eps_tol = 0.0) {
     cudaStream_t s = P.stream;
     if (k < 1 || k > KMAX) throw Error{MM_ERR_ARG, "k must be in [1, 64]"};
     if (maxit < 1) throw Error{MM_ERR_ARG, "maxit must be >= 1"};
@@ -834,8 +834,22 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
         for (int j = 0; j < m; ++j) d[(size_t)j] = 1.0 / al[(size_t)j] + (j > 0 ? be[(size_t)j - 1] / al[(size_t)j - 1] : 0.0);
         for (int j = 0; j + 1 < m; ++j) e[(size_t)j] = std::sqrt(be[(size_t)j]) / al[(size_t)j];
         std::vector<double> theta, S;
-        const int kk = std::min(k, m);
+        int kk = std::min(k, m);
         tridiag_smallest(d, e, kk, theta, S);
+        if (eps_tol > 0.0) {
+            // keep the Ritz pairs with |theta| < eps_tol (Sec. 5), smallest first
+            int c = 0;
+            while (c < kk && std::fabs(theta[(size_t)c]) < eps_tol) ++c;
+            if (c == 0) throw Error{MM_ERR_STATE, "no Ritz value below eps_tol"};
+            if (c < kk) {
+                std::vector<double> S2((size_t)m * c);
+                for (int j = 0; j < m; ++j)
+                    for (int q = 0; q < c; ++q) S2[(size_t)j * c + q] = S[(size_t)j * kk + q];
+                S.swap(S2);
+                theta.resize((size_t)c);
+                kk = c;
+            }
+        }
         // Ritz vectors Y = sum_j (-1)^j z_j / sqrt(r_j^T z_j) S_j  (step 2-4)
         std::vector<double> Cs((size_t)m * kk);
         for (int j = 0; j < m; ++j) {
@@ -1682,6 +1696,33 @@ mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bp
             build_coarse<double>(*P, k, bprime, tol, maxit);
         else
             build_coarse<float>(*P, k, bprime, tol, maxit);
+    });
+}
+
+mm_status mm_build_coarse_eps(mm_plan_t plan, int kmax, double eps_tol, int precision, const double* bprime,
+                              double tol, int maxit) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!(eps_tol > 0.0)) throw Error{MM_ERR_ARG, "eps_tol must be > 0"};
+        if (prec_ok(precision) == MM_FP64)
+            build_coarse<double>(*P, kmax, bprime, tol, maxit, eps_tol);
+        else
+            build_coarse<float>(*P, kmax, bprime, tol, maxit, eps_tol);
+    });
+}
+
+mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (Z == nullptr || k < 1 || k > KMAX) throw Error{MM_ERR_ARG, "need non-null Z and 1 <= k <= 64"};
+        double* Zd = dalloc<double>((size_t)k * P->n);
+        try {
+            check_cuda(cudaMemcpyAsync(Zd, Z, (size_t)k * P->n * 8, cudaMemcpyDefault, P->stream), "copy Z");
+        } catch (...) {
+            dfree(Zd);
+            throw;
+        }
+        install_coarse(*P, Zd, k, {});
     });
 }
 

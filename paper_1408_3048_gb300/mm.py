@@ -30,7 +30,8 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_scatter", "mm_apply_A", "mm_rhs", "mm_precond", "mm_build_coarse", "mm_coarse_info",
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
-           "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori"]
+           "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
+           "mm_build_coarse_eps", "mm_coarse_import"]
 
 
 class mm_psd(ctypes.Structure):
@@ -94,6 +95,8 @@ _SIGS = {
     "mm_solve_batch": (I32, [P, P, ctypes.c_int, ctypes.POINTER(mm_solve_opts), P, ctypes.POINTER(mm_stats)]),
     "mm_autotune_read": (I32, [P, P, P]),
     "mm_build_coarse_apriori": (I32, [P, ctypes.c_int]),
+    "mm_build_coarse_eps": (I32, [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int]),
+    "mm_coarse_import": (I32, [P, P, ctypes.c_int]),
     "mm_batch_config": (I32, [P, ctypes.c_int32, P, P, P]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
@@ -227,6 +230,15 @@ def mm_precond(plan, kind, precision, r, z):
 
 def mm_build_coarse(plan, k, precision, bprime, tol, maxit):
     _check(lib().mm_build_coarse(plan, int(k), precision, _ptr(bprime), float(tol), int(maxit)), plan)
+
+
+def mm_build_coarse_eps(plan, kmax, eps_tol, precision, bprime, tol, maxit):
+    _check(lib().mm_build_coarse_eps(plan, int(kmax), float(eps_tol), precision, _ptr(bprime), float(tol),
+                                     int(maxit)), plan)
+
+
+def mm_coarse_import(plan, Z, k):
+    _check(lib().mm_coarse_import(plan, _ptr(Z), int(k)), plan)
 
 
 def mm_build_coarse_apriori(plan, r):
@@ -392,6 +404,19 @@ class Plan:
         self._sync_in()
         mm_build_coarse(self.handle, k, precision, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
+
+    def build_coarse_eps(self, eps_tol, kmax=64, precision=MM_FP64, bprime=None, tol=1e-6, maxit=1000):
+        """A posteriori coarse space from the Ritz pairs below eps_tol (at most kmax)."""
+        self._sync_in()
+        mm_build_coarse_eps(self.handle, kmax, eps_tol, precision, bprime, tol, maxit)
+        return mm_coarse_info(self.handle)
+
+    def coarse_import(self, Z):
+        """Install a coarse basis Z (numpy or torch, shape [n, k]); returns k."""
+        Zc = np.ascontiguousarray(np.asarray(Z.cpu() if hasattr(Z, "cpu") else Z, dtype=np.float64).T)
+        self._sync_in()
+        mm_coarse_import(self.handle, Zc, Zc.shape[0])
+        return mm_coarse_info(self.handle)[0]
 
     def build_coarse_apriori(self, r):
         """A priori coarse space Z_S merged into r interval groups; returns the kept k."""

@@ -202,6 +202,32 @@ def test_two_level(case):
     assert np.linalg.norm(b1 - pr.A(m2.cpu().numpy())) / np.linalg.norm(b1) <= 1e-6
 
 
+def test_coarse_threshold_and_import(case):
+    # eps_tol selection (Sec. 5) against the oracle's Lanczos, and a basis carried over
+    # to a second plan of the same scan gives the same two-level solve
+    name, scan, pr, plan = case
+    d0, d1 = _data(scan, 0), _data(scan, 1)
+    b0 = pr.rhs(d0)
+    bd = oprec.BlockJacobi(pr)
+    r0 = pcg(pr.A, bd.apply, b0, 1e-6, 3000, record=True)
+    _, th = oprec.ritz_coarse_space(r0.alphas, r0.betas, r0.zs, r0.rzs, 8)
+    eps = 0.5 * (th[2] + th[3])
+    kk, ritz = plan.build_coarse_eps(eps, kmax=64, precision=mm.MM_FP64, bprime=_cuda(b0), tol=1e-6, maxit=3000)
+    assert kk == 3
+    np.testing.assert_allclose(ritz[:3], th[:3], rtol=1e-6)
+    with pytest.raises(mm.MMError) as e:
+        plan.build_coarse_eps(0.5 * th[0], precision=mm.MM_FP64, bprime=_cuda(b0), tol=1e-6, maxit=3000)
+    assert e.value.status == mm.MM_ERR_STATE
+    assert plan.coarse_vectors().shape[1] == 3          # the failed build kept the space
+    m1, st1, _ = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL)
+    other = _plan(scan)
+    assert other.coarse_import(plan.coarse_vectors()) == 3
+    m2, st2, _ = other.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL)
+    assert st2["iters"] == st1["iters"]
+    assert _rel(m2.cpu().numpy(), m1.cpu().numpy()) <= 1e-12
+    other.close()
+
+
 def test_two_level_apriori(case):
     # a priori coarse space Z_S (Sec. 3.3.1) merged into r interval groups
     name, scan, pr, plan = case
