@@ -6,7 +6,9 @@ pcg          Preconditioned conjugate gradient for A x = b (Sec. 3.1).  Reading 
              beta_j = r_{j+1}^T z_{j+1} / r_j^T z_j for every preconditioner, stop when
              the recursive residual satisfies ||r_j||_2 / ||b||_2 <= tol (the relative
              residual that Sec. 5.1 plots and stops on).  The iteration count is the
-             number of products A p after the initial residual.
+             number of products A p after the initial residual.  An optional starting
+             vector x0 (the A-DEF2 variant of App. B starts from Z E^-1 Z^T b) gives
+             r_0 = b - A x0; the stopping test stays relative to ||b||.
 dense_solve  The GLS estimate of Eq. 3 by a dense Cholesky factorisation of A
              (tiny problems).
 """
@@ -26,10 +28,14 @@ class PCGResult:
         self.rzs = rzs                # r_j^T z_j
 
 
-def pcg(apply_A, apply_M, b, tol, maxit, record=False):
+def pcg(apply_A, apply_M, b, tol, maxit, record=False, x0=None):
     b = np.asarray(b, dtype=np.float64)
-    x = np.zeros_like(b)
-    r = b.copy()
+    if x0 is None:
+        x = np.zeros_like(b)
+        r = b.copy()
+    else:
+        x = np.asarray(x0, dtype=np.float64).copy()
+        r = b - apply_A(x)
     bn = np.linalg.norm(b)
     rel = [np.linalg.norm(r) / bn if bn > 0 else 0.0]
     alphas, betas, zs, rzs = [], [], [], []

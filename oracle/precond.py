@@ -77,6 +77,18 @@ class TwoLevel:
         """R y = y - A Z E^-1 Z^T y (Eq. 11)."""
         return y - self.AZ @ self.coarse(y)
 
+    def apply_adef2(self, r):
+        """M_2lvl^(alt) r = R^T M_BD r + Z E^-1 Z^T r (App. B, Eq. B.1, the A-DEF2 form);
+        R^T = I - Z E^-1 (A Z)^T because A is symmetric."""
+        r = np.asarray(r, dtype=np.float64)
+        y = self.bd.apply(r)
+        return y - self.Z @ scipy.linalg.lu_solve(self.lu, self.AZ.T @ y) + self.Z @ self.coarse(r)
+
+    def adef2_start(self, b):
+        """The starting vector x0 = Z E^-1 Z^T b that makes A-DEF2 equivalent to an SPD
+        preconditioner in exact arithmetic (App. B): Z^T r_0 = 0."""
+        return self.Z @ self.coarse(b)
+
 
 def lanczos_tridiagonal(alphas, betas):
     """T_m from m CG steps (alphas[0..m-1], betas[0..m-2])."""

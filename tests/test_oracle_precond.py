@@ -106,6 +106,32 @@ def test_lanczos_vectors_are_minv_orthonormal(prob):
     assert np.linalg.norm(Rm[:, :-1]) <= 1e-8 * np.linalg.norm(V)
 
 
+def test_adef2_spectrum_and_start(prob):
+    # App. B: M_2lvl A and M_2lvl^(alt) A have the same spectrum; from x0 = Z E^-1 Z^T b
+    # every A-DEF2 residual stays orthogonal to Z, and PCG reaches the dense solution
+    b = prob.rhs(np.random.default_rng(4).standard_normal(prob.nt))
+    bd = precond.BlockJacobi(prob)
+    res = pcg(prob.A, bd.apply, b, 1e-10, 500, record=True)
+    Z, _ = precond.ritz_coarse_space(res.alphas, res.betas, res.zs, res.rzs, 3)
+    tl = precond.TwoLevel(prob, bd, Z)
+    A = prob.dense_A()
+    I = np.eye(prob.n)
+    M1 = np.stack([tl.apply(I[:, j]) for j in range(prob.n)], axis=1)
+    M2 = np.stack([tl.apply_adef2(I[:, j]) for j in range(prob.n)], axis=1)
+    e1 = np.sort(np.linalg.eigvals(M1 @ A).real)
+    e2 = np.sort(np.linalg.eigvals(M2 @ A).real)
+    np.testing.assert_allclose(e2, e1, rtol=1e-7, atol=1e-7 * e1.max())
+    x0 = tl.adef2_start(b)
+    r0 = b - prob.A(x0)
+    assert np.linalg.norm(Z.T @ r0) <= 1e-10 * np.linalg.norm(b)
+    out = pcg(prob.A, tl.apply_adef2, b, 1e-10, 500, x0=x0)
+    assert out.converged
+    np.testing.assert_allclose(out.x, np.linalg.solve(A, b), rtol=1e-7, atol=1e-7 * np.abs(out.x).max())
+    # the deflated directions stay deflated along the way
+    r = b - prob.A(out.x)
+    assert np.linalg.norm(Z.T @ r) <= 1e-8 * np.linalg.norm(b)
+
+
 def test_ritz_threshold_selection(prob):
     # eps_tol keeps exactly the Ritz pairs below the threshold (at most k), which are the
     # leading columns of the k-smallest selection
