@@ -53,7 +53,7 @@ typedef enum {
 
 enum { MM_FP64 = 0, MM_FP32 = 1 };                 /* operator arithmetic               */
 enum { MM_WINDOW_GAUSS = 0, MM_WINDOW_RECT = 1 };  /* apodisation window (Eq. 28 / none) */
-enum { MM_PREC_BD = 0, MM_PREC_TWOLEVEL = 1 };     /* preconditioner kind               */
+enum { MM_PREC_BD = 0, MM_PREC_TWOLEVEL = 1, MM_PREC_ADEF2 = 2 };  /* preconditioner kind */
 enum { MM_SOLVE_FP64 = 0, MM_SOLVE_MIXED = 1 };    /* solver arithmetic                 */
 
 /* Noise PSD of one stationary piece, Eq. 19 with exponent alpha:
@@ -202,9 +202,11 @@ mm_status mm_apply_A_static(mm_plan_t plan, int precision, const void* x, void* 
 mm_status mm_rhs(mm_plan_t plan, const double* d, double* b);
 
 /*
- * z = M r with M = M_BD (Eq. 10; kind MM_PREC_BD) or M_2lvl (Eq. 12; MM_PREC_TWOLEVEL,
- * applied as in App. C: v = E^-1 Z^T r, z = M_BD (r - (AZ) v) + Z v).
- * r, z device [n] in `precision`.  TWOLEVEL needs mm_build_coarse first (MM_ERR_STATE).
+ * z = M r with M = M_BD (Eq. 10; kind MM_PREC_BD), M_2lvl (Eq. 12; MM_PREC_TWOLEVEL,
+ * applied as in App. C: v = E^-1 Z^T r, z = M_BD (r - (AZ) v) + Z v) or the A-DEF2 form
+ * of App. B (Eq. B.1; MM_PREC_ADEF2: y = M_BD r, z = y + Z E^-1 (Z^T r - (AZ)^T y)).
+ * r, z device [n] in `precision`.  The two-level kinds need a coarse space first
+ * (MM_ERR_STATE).
  */
 mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, void* z);
 
@@ -272,7 +274,9 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
  * Solve A m = P^T N^-1 d by PCG from m_0 = 0 (Sec. 3.1), stopping when the relative
  * residual ||b - A m||_2 / ||b||_2 <= tol (the convergence measure of Sec. 5.1).
  *   d       host or device double[nt] time-ordered data.
- *   kind    MM_PREC_BD or MM_PREC_TWOLEVEL.
+ *   kind    MM_PREC_BD, MM_PREC_TWOLEVEL or MM_PREC_ADEF2 (the latter starts from
+ *           x_0 = Z E^-1 Z^T b, which makes A-DEF2 equivalent to an SPD preconditioner in
+ *           exact arithmetic, App. B; the others from x_0 = 0).
  *   solver  MM_SOLVE_FP64: all arithmetic FP64, stopping on the recursive residual.
  *           MM_SOLVE_MIXED: FP32 gather / Toeplitz / scatter and FP32 vectors with FP64
  *           dot products and step scalars inside PCG, FP64 E factor and solve, and an
@@ -304,7 +308,7 @@ mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
 typedef struct {
     double tol;             /* relative residual target (required, >= 0)                  */
     int32_t maxit;          /* total PCG iterations (required, >= 1)                      */
-    int32_t kind;           /* MM_PREC_BD or MM_PREC_TWOLEVEL                              */
+    int32_t kind;           /* MM_PREC_BD, MM_PREC_TWOLEVEL or MM_PREC_ADEF2               */
     int32_t solver;         /* MM_SOLVE_FP64 or MM_SOLVE_MIXED                             */
     int32_t max_outer;      /* refinement steps (MIXED), default 20                        */
     double inner_tol_min;   /* lower bound of the inner FP32 tolerance (MIXED), default 3e-7

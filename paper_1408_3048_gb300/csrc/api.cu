@@ -590,6 +590,9 @@ struct PcgOutcome {
     double rr = 0.0, bb = 0.0;
 };
 
+// Coarse mode of the PCG kernels for a preconditioner kind: 0 M_BD, 1 M_2lvl, 2 A-DEF2.
+static int coarse_mode(int kind) { return kind == MM_PREC_BD ? 0 : (kind == MM_PREC_TWOLEVEL ? 1 : 2); }
+
 template <typename T>
 static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
     PcgArgs<T> a{};
@@ -628,15 +631,15 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
 
 // Runs PCG on the right-hand side already stored in pcg.r (as T); solution in pcg.x.
 template <typename T>
-static PcgOutcome run_pcg(PlanHolder& P, bool two, double tol, int maxit, T* zstore, int maxstore) {
+static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstore, int maxstore) {
     cudaStream_t s = P.stream;
-    PcgArgs<T> a = pcg_args<T>(P, two, maxit);
+    PcgArgs<T> a = pcg_args<T>(P, cm != 0, maxit);
     a.zstore = zstore;
     a.maxstore = maxstore;
     P.h_scal[0] = tol * tol;
     h2d(P.pcg.scal + SC_TOL2, P.h_scal, 8, s);
     const int nb = P.pcg.nblocks;
-    launch_pcg<T>(0, P.ncomp, two, a, nb, s);
+    launch_pcg<T>(0, P.ncomp, cm, a, nb, s);
     int launched = 0;
     int chunk = 4;
     PcgOutcome out;
@@ -657,7 +660,7 @@ static PcgOutcome run_pcg(PlanHolder& P, bool two, double tol, int maxit, T* zst
                                   P.pcg.scal + SC_PQ, P.pcg.flags + F_DONE, s);
             prof_end(P, sl);
             sl = prof_begin(P, f64 ? ST_PCG64 : ST_PCG32);
-            launch_pcg<T>(1, P.ncomp, two, a, nb, s);
+            launch_pcg<T>(1, P.ncomp, cm, a, nb, s);
             prof_end(P, sl);
         }
         launched += c;
@@ -819,7 +822,7 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
     double* Y2 = nullptr;
     double* C = nullptr;
     try {
-        const PcgOutcome o = run_pcg<T>(P, false, tol, maxit, zstore, maxit + 1);
+        const PcgOutcome o = run_pcg<T>(P, 0, tol, maxit, zstore, maxit + 1);
         if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED)
             throw Error{(mm_status)o.status, "first solve of the coarse construction failed"};
         const int m = o.iters;   // alphas 0..m-1, betas 0..m-2, z_0..z_{m-1}
@@ -901,9 +904,10 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
 // -------------------------------------------------------------------------- solve
 static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
     if (!(so.tol >= 0.0) || so.maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
-    if (so.kind != MM_PREC_BD && so.kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
+    if (so.kind != MM_PREC_BD && so.kind != MM_PREC_TWOLEVEL && so.kind != MM_PREC_ADEF2)
+        throw Error{MM_ERR_ARG, "bad preconditioner kind"};
     if (so.solver != MM_SOLVE_FP64 && so.solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
-    if (so.kind == MM_PREC_TWOLEVEL && P.coarse.k == 0)
+    if (so.kind != MM_PREC_BD && P.coarse.k == 0)
         throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
 }
 
@@ -933,7 +937,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
     cudaStream_t s = P.stream;
     const double tol = so.tol;
     const int maxit = so.maxit;
-    const bool two = so.kind == MM_PREC_TWOLEVEL;
+    const int cm = coarse_mode(so.kind);
     const int max_outer = so.max_outer > 0 ? so.max_outer : 20;
     const double inner_min = so.inner_tol_min > 0.0 ? so.inner_tol_min : 3e-7;
     int status = MM_OK;
@@ -941,7 +945,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
     const double bn = std::sqrt(bb);
     if (so.solver == MM_SOLVE_FP64) {
         check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
-        const PcgOutcome o = run_pcg<double>(P, two, tol, maxit, nullptr, 0);
+        const PcgOutcome o = run_pcg<double>(P, cm, tol, maxit, nullptr, 0);
         if (o.status != MM_OK) status = o.status;
         check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
         stats.iters = o.iters;
@@ -976,7 +980,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
         double tol_in = 0.5 * tol * bn / std::sqrt(rr);
         tol_in = std::min(0.5, std::max(tol_in, inner_min));
         if (outer == 0 && so.first_inner_tol > 0.0) tol_in = so.first_inner_tol;
-        const PcgOutcome o = run_pcg<float>(P, two, tol_in, maxit - total, nullptr, 0);
+        const PcgOutcome o = run_pcg<float>(P, cm, tol_in, maxit - total, nullptr, 0);
         if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
             status = o.status;
             break;
@@ -1671,19 +1675,21 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
     return guarded(plan, [&] {
         PlanHolder* P = get(plan);
         if (!r || !z) throw Error{MM_ERR_ARG, "null vector"};
-        if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL) throw Error{MM_ERR_ARG, "bad preconditioner kind"};
-        const bool two = kind == MM_PREC_TWOLEVEL;
+        if (kind != MM_PREC_BD && kind != MM_PREC_TWOLEVEL && kind != MM_PREC_ADEF2)
+            throw Error{MM_ERR_ARG, "bad preconditioner kind"};
+        const int cm = coarse_mode(kind);
+        const bool two = cm != 0;
         if (two && P->coarse.k == 0) throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
         if (prec_ok(precision) == MM_FP64) {
             PcgArgs<double> a = pcg_args<double>(*P, two, 0);
             a.r = const_cast<double*>(static_cast<const double*>(r));
             a.z = static_cast<double*>(z);
-            launch_pcg<double>(2, P->ncomp, two, a, P->pcg.nblocks, P->stream);
+            launch_pcg<double>(2, P->ncomp, cm, a, P->pcg.nblocks, P->stream);
         } else {
             PcgArgs<float> a = pcg_args<float>(*P, two, 0);
             a.r = const_cast<float*>(static_cast<const float*>(r));
             a.z = static_cast<float*>(z);
-            launch_pcg<float>(2, P->ncomp, two, a, P->pcg.nblocks, P->stream);
+            launch_pcg<float>(2, P->ncomp, cm, a, P->pcg.nblocks, P->stream);
         }
         sync(P->stream);
     });

@@ -2,8 +2,10 @@
 // persistent cooperative kernel per iteration:
 //
 //   alpha = rho / p^T q;  x += alpha p;  r -= alpha q;  stop if ||r|| <= tol ||b||
-//   z = M r  (M_BD of Eq. 10, or M_2lvl of Eq. 12 applied as in App. C:
-//             v = E^-1 Z^T r by the FP64 Cholesky factor of E, z = M_BD (r - AZ v) + Z v)
+//   z = M r  (M_BD of Eq. 10; M_2lvl of Eq. 12 applied as in App. C:
+//             v = E^-1 Z^T r with the FP64 E^-1, z = M_BD (r - AZ v) + Z v; or the
+//             A-DEF2 form of App. B: y = M_BD r, v = E^-1 (Z^T r - (AZ)^T y),
+//             z = y + Z v, started from x_0 = Z E^-1 Z^T b)
 //   rho' = r^T z;  beta = rho' / rho;  p = z + beta p
 //
 // Dot products are accumulated in FP64 per block (fixed thread order), written as block
@@ -81,18 +83,23 @@ __device__ __forceinline__ void block_pixels(int npix, int& lo, int& hi) {
     if (lo > hi) lo = hi;
 }
 
-// Z^T r over this block's elements -> part[blk][S_COARSE + j] (a preconditioner input,
-// not a CG dot product: lanes accumulate in T, the reductions above them in FP64)
-template <typename T>
+// Z^T r (CM 1) or Z^T r - (AZ)^T y with y = M_BD r already in a.z (CM 2) over this
+// block's elements -> part[blk][S_COARSE + j] (a preconditioner input, not a CG dot
+// product: lanes accumulate in T, the reductions above them in FP64)
+template <typename T, int CM = 1>
 __device__ void coarse_partials(const PcgArgs<T>& a, const T* r, int64_t e0, int64_t e1) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < a.k; j += nw) {
         const T* zj = a.Z + (size_t)j * a.n;
+        const T* azj = a.AZ + (size_t)j * a.n;
         // per-lane partial in T (a few dozen terms: for T = float this keeps the FP64 pipe,
         // which GB300 runs at 1/64 of the FP32 rate, for the cross-lane / block sums)
         T sl = (T)0;
 #pragma unroll 8
-        for (int64_t i = e0 + l; i < e1; i += 32) sl += __ldg(zj + i) * r[i];
+        for (int64_t i = e0 + l; i < e1; i += 32) {
+            sl += __ldg(zj + i) * r[i];
+            if constexpr (CM == 2) sl -= __ldg(azj + i) * a.z[i];
+        }
         double* slot = a.partial + (size_t)blockIdx.x * PSTRIDE + S_COARSE + j;
         if constexpr (sizeof(T) == 4) {
             float hi = sl, lo = 0.f;
@@ -140,11 +147,12 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
     __syncthreads();
 }
 
-// z = M_BD (r - AZ v) + Z v (or M_BD r) on this block's pixels; returns partial r^T z.
-template <typename T, int NC, bool TWO>
+// z = M_BD r (CM 0), M_BD (r - AZ v) + Z v (CM 1) or y + Z v with y = M_BD r in a.z
+// (CM 2) on this block's pixels; returns partial r^T z.
+template <typename T, int NC, int CM>
 __device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0, int p1) {
     __shared__ T vt[KMAX];
-    if constexpr (TWO) {
+    if constexpr (CM != 0) {
         if (threadIdx.x < a.k) vt[threadIdx.x] = (T)v_sh[threadIdx.x];
         __syncthreads();
     }
@@ -158,7 +166,23 @@ __device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int 
             t0[c] = t[c];
             zc[c] = (T)0;
         }
-        if constexpr (TWO) {
+        if constexpr (CM == 2) {
+#pragma unroll 8
+            for (int j = 0; j < a.k; ++j) {
+                const T vj = vt[j];
+                const T* zz = a.Z + (size_t)j * a.n + e;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) zc[c] += __ldg(zz + c) * vj;
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T out = a.z[e + c] + zc[c];
+                a.z[e + c] = out;
+                rz.add(t0[c], out);
+            }
+            continue;
+        }
+        if constexpr (CM == 1) {
 #pragma unroll 8
             for (int j = 0; j < a.k; ++j) {
                 const T vj = vt[j];
@@ -189,9 +213,27 @@ __device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int 
     return rz;
 }
 
+// y = M_BD r into a.z on this block's pixels (the first step of the A-DEF2 form).
+template <typename T, int NC>
+__device__ void bd_into_z(const PcgArgs<T>& a, int p0, int p1) {
+    for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+        const int64_t e = (int64_t)q * NC;
+        if constexpr (NC == 1) {
+            a.z[e] = a.bd[q] * a.r[e];
+        } else {
+            const T* m = a.bd + 6 * (int64_t)q;
+            const T r0 = a.r[e], r1 = a.r[e + 1], r2 = a.r[e + 2];
+            a.z[e] = m[0] * r0 + m[1] * r1 + m[2] * r2;
+            a.z[e + 1] = m[1] * r0 + m[3] * r1 + m[4] * r2;
+            a.z[e + 2] = m[2] * r0 + m[4] * r1 + m[5] * r2;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------ init kernel
-// r = b is already in a.r.  x = 0, z = M r, p = z, rho = r^T z, bb = r^T r.
-template <typename T, int NC, bool TWO>
+// r = b is already in a.r.  x = 0 (CM 2: x = Z E^-1 Z^T b, r = b - AZ E^-1 Z^T b),
+// z = M r, p = z, rho = r^T z, bb = b^T b.
+template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     __shared__ double sh[32];
     __shared__ double v_sh[KMAX];
@@ -205,11 +247,30 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     }
     const double bb = block_total(bacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = bb;
-    if constexpr (TWO) coarse_partials(a, a.r, e0, e1);
+    if constexpr (CM != 0) coarse_partials<T, 1>(a, a.r, e0, e1);
     if (!grid_sync(a.bar, a.flags)) return;
     const double bbt = grid_total(a.partial, S_RR, sh);
-    if constexpr (TWO) coarse_solve(a, v_sh);
-    const DotAcc<T> rzacc = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    if constexpr (CM != 0) coarse_solve(a, v_sh);
+    if constexpr (CM == 2) {
+        // x0 = Z v, r0 = b - AZ v with v = E^-1 Z^T b (every block holds the same v)
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+            T xi = (T)0, ri = a.r[i];
+            for (int j = 0; j < a.k; ++j) {
+                const T vj = (T)v_sh[j];
+                xi += __ldg(a.Z + (size_t)j * a.n + i) * vj;
+                ri -= __ldg(a.AZ + (size_t)j * a.n + i) * vj;
+            }
+            a.x[i] = xi;
+            a.r[i] = ri;
+        }
+        bd_into_z<T, NC>(a, p0, p1);
+        // every block has read the first coarse partials before they are overwritten
+        if (!grid_sync(a.bar, a.flags)) return;
+        coarse_partials<T, 2>(a, a.r, e0, e1);
+        if (!grid_sync(a.bar, a.flags)) return;
+        coarse_solve(a, v_sh);
+    }
+    const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
     __syncthreads();
     for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
         a.p[i] = a.z[i];
@@ -240,7 +301,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
 }
 
 // ------------------------------------------------------------------- iteration kernel
-template <typename T, int NC, bool TWO>
+template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     __shared__ double sh[32];
     __shared__ double v_sh[KMAX];
@@ -270,9 +331,15 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     }
     const double rr = block_total(racc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = rr;
-    if constexpr (TWO) {
+    if constexpr (CM == 1) {
         __syncthreads();
-        coarse_partials(a, a.r, e0, e1);
+        coarse_partials<T, 1>(a, a.r, e0, e1);
+    }
+    if constexpr (CM == 2) {
+        __syncthreads();
+        bd_into_z<T, NC>(a, p0, p1);
+        __syncthreads();
+        coarse_partials<T, 2>(a, a.r, e0, e1);
     }
     if (!grid_sync(a.bar, a.flags)) return;
     const double rrt = grid_total(a.partial, S_RR, sh);
@@ -302,8 +369,8 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
         return;
     }
     // phase C: z = M r, r^T z
-    if constexpr (TWO) coarse_solve(a, v_sh);
-    const DotAcc<T> rzacc = apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    if constexpr (CM != 0) coarse_solve(a, v_sh);
+    const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
     const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags)) return;
@@ -333,22 +400,26 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
 
 // --------------------------------------------------------------- stand-alone M_2lvl
 // Used by mm_precond: the same device functions as in PCG, launched cooperatively.
-template <typename T, int NC, bool TWO>
+template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) precond_kernel(PcgArgs<T> a) {
     __shared__ double v_sh[KMAX];
     int p0, p1;
     block_pixels(a.npix, p0, p1);
     const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
-    if constexpr (TWO) {
-        coarse_partials(a, a.r, e0, e1);
+    if constexpr (CM == 2) {
+        bd_into_z<T, NC>(a, p0, p1);
+        __syncthreads();
+    }
+    if constexpr (CM != 0) {
+        coarse_partials<T, CM>(a, a.r, e0, e1);
         if (!grid_sync(a.bar, a.flags)) return;
         coarse_solve(a, v_sh);
     }
-    (void)apply_precond<T, NC, TWO>(a, v_sh, p0, p1);
+    (void)apply_precond<T, NC, CM>(a, v_sh, p0, p1);
 }
 
 // ----------------------------------------------------------------------- launchers
-template <typename T, int NC, bool TWO>
+template <typename T>
 static void coop(void (*kern)(PcgArgs<T>), const PcgArgs<T>& a, int nblocks, cudaStream_t s) {
     void* args[] = {(void*)&a};
     check_cuda(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblocks), dim3(PCG_THREADS), args,
@@ -358,29 +429,31 @@ static void coop(void (*kern)(PcgArgs<T>), const PcgArgs<T>& a, int nblocks, cud
 }
 
 template <typename T>
-void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks, cudaStream_t s) {
-#define MM_PCG_CASE(NC, TWO)                                                       \
-    if (ncomp == NC && two == TWO) {                                               \
-        if (which == 0) coop<T, NC, TWO>(pcg_init_kernel<T, NC, TWO>, a, nblocks, s); \
-        else if (which == 1) coop<T, NC, TWO>(pcg_iter_kernel<T, NC, TWO>, a, nblocks, s); \
-        else coop<T, NC, TWO>(precond_kernel<T, NC, TWO>, a, nblocks, s);          \
-        return;                                                                    \
+void launch_pcg(int which, int ncomp, int cm, const PcgArgs<T>& a, int nblocks, cudaStream_t s) {
+#define MM_PCG_CASE(NC, CM)                                                 \
+    if (ncomp == NC && cm == CM) {                                          \
+        if (which == 0) coop<T>(pcg_init_kernel<T, NC, CM>, a, nblocks, s); \
+        else if (which == 1) coop<T>(pcg_iter_kernel<T, NC, CM>, a, nblocks, s); \
+        else coop<T>(precond_kernel<T, NC, CM>, a, nblocks, s);              \
+        return;                                                             \
     }
-    MM_PCG_CASE(1, false)
-    MM_PCG_CASE(1, true)
-    MM_PCG_CASE(3, false)
-    MM_PCG_CASE(3, true)
+    MM_PCG_CASE(1, 0)
+    MM_PCG_CASE(1, 1)
+    MM_PCG_CASE(1, 2)
+    MM_PCG_CASE(3, 0)
+    MM_PCG_CASE(3, 1)
+    MM_PCG_CASE(3, 2)
 #undef MM_PCG_CASE
-    throw Error{MM_ERR_ARG, "launch_pcg: bad ncomp"};
+    throw Error{MM_ERR_ARG, "launch_pcg: bad ncomp or coarse mode"};
 }
-template void launch_pcg<double>(int, int, bool, const PcgArgs<double>&, int, cudaStream_t);
-template void launch_pcg<float>(int, int, bool, const PcgArgs<float>&, int, cudaStream_t);
+template void launch_pcg<double>(int, int, int, const PcgArgs<double>&, int, cudaStream_t);
+template void launch_pcg<float>(int, int, int, const PcgArgs<float>&, int, cudaStream_t);
 
 // One block per SM: enough threads for the map-sized vectors, and few block partials
 // for the reductions.
 int pcg_max_blocks(int num_sms) {
     int per_sm = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_iter_kernel<double, 3, true>,
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_iter_kernel<double, 3, 2>,
                                                              PCG_THREADS, 0),
                "occupancy");
     if (per_sm < 1) throw Error{MM_ERR_CUDA, "PCG kernel does not fit on an SM"};

@@ -133,7 +133,7 @@ template <> struct DotAcc<float> {
 };
 
 template <typename T>
-void launch_pcg(int which, int ncomp, bool two, const PcgArgs<T>& a, int nblocks, cudaStream_t s);
+void launch_pcg(int which, int ncomp, int cm, const PcgArgs<T>& a, int nblocks, cudaStream_t s);  // cm: 0 M_BD, 1 M_2lvl, 2 A-DEF2
 int pcg_max_blocks(int num_sms);
 
 void launch_dot64(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t s);

@@ -19,7 +19,7 @@ MM_OK, MM_ERR_ARG, MM_ERR_CUDA, MM_ERR_OOM, MM_ERR_NOT_SPD = 0, 1, 2, 3, 4
 MM_ERR_NOT_CONVERGED, MM_ERR_NUMERIC, MM_ERR_TIMEOUT, MM_ERR_STATE = 5, 6, 7, 8
 MM_FP64, MM_FP32 = 0, 1
 MM_WINDOW_GAUSS, MM_WINDOW_RECT = 0, 1
-MM_PREC_BD, MM_PREC_TWOLEVEL = 0, 1
+MM_PREC_BD, MM_PREC_TWOLEVEL, MM_PREC_ADEF2 = 0, 1, 2
 MM_SOLVE_FP64, MM_SOLVE_MIXED = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 4: "MM_ERR_NOT_SPD",

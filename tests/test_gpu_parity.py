@@ -228,6 +228,31 @@ def test_coarse_threshold_and_import(case):
     other.close()
 
 
+def test_adef2(case):
+    # the A-DEF2 form of App. B on the library's a posteriori space, from its starting
+    # vector, against the oracle's operator and PCG
+    name, scan, pr, plan = case
+    d0, d1 = _data(scan, 0), _data(scan, 1)
+    kk, _ = plan.build_coarse(8, mm.MM_FP64, bprime=_cuda(pr.rhs(d0)), tol=1e-6, maxit=3000)
+    Zl = plan.coarse_vectors()
+    bd = oprec.BlockJacobi(pr)
+    tl = oprec.TwoLevel(pr, bd, Zl)
+    r = np.random.default_rng(9).standard_normal(pr.n)
+    z = plan.precond(_cuda(r), mm.MM_PREC_ADEF2, mm.MM_FP64).cpu().numpy()
+    assert _rel(z, tl.apply_adef2(r)) <= 1e-9
+    z32 = plan.precond(_cuda(r, torch.float32), mm.MM_PREC_ADEF2, mm.MM_FP32).cpu().numpy()
+    assert _rel(z32, tl.apply_adef2(r)) <= 1e-4
+    b1 = pr.rhs(d1)
+    ref = pcg(pr.A, tl.apply_adef2, b1, 1e-6, 3000, x0=tl.adef2_start(b1))
+    m, st, status = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_ADEF2)
+    assert status == mm.MM_OK
+    assert abs(st["iters"] - ref.iters) <= 2, (st["iters"], ref.iters)
+    assert _rel(m.cpu().numpy(), ref.x) <= 1e-6
+    m2, st2, status2 = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_ADEF2, solver=mm.MM_SOLVE_MIXED)
+    assert status2 == mm.MM_OK
+    assert np.linalg.norm(b1 - pr.A(m2.cpu().numpy())) / np.linalg.norm(b1) <= 1e-6
+
+
 def test_two_level_apriori(case):
     # a priori coarse space Z_S (Sec. 3.3.1) merged into r interval groups
     name, scan, pr, plan = case
