@@ -16,6 +16,16 @@ give Ritz vectors V_m s with Lanczos vectors v_j = (-1)^j z_j / sqrt(r_j^T z_j)
 (z_j = M_BD r_j, the preconditioned CG residuals).  The selected vectors are
 orthonormalised (Euclidean QR) and columns with |R_jj| < 1e-10 max |R_jj| dropped.
 Reading R9: E is factored by LU with partial pivoting (as App. C does).
+
+Arnoldi route (App. A, Algorithm 1; the paper's own Z_D source): the basic Arnoldi
+process on B = M_BD A from w_1 = r_0 / ||r_0||, r_0 = M_BD b' (x_0 = 0), until the GMRES
+residual min_y ||beta e_1 - Hbar_j y|| falls to tol * beta, m steps, or breakdown.  The
+projections h_ij = (B w_j, w_i) are taken by classical Gram-Schmidt as in Algorithm 1,
+with one re-orthogonalisation pass (its coefficients added to h_ij; equal in exact
+arithmetic).  Ritz pairs: eigenpairs (lambda_i, v_i) of H_m, y_i = W_m v_i (Eq. A.4);
+selected when |Re lambda_i| < eps_tol (Sec. 5), at most k, smallest Re first; a complex
+pair contributes the real and imaginary parts of one member's vector; then the same
+orthonormalisation and dropping as above.
 """
 import numpy as np
 import scipy.linalg
@@ -122,6 +132,65 @@ def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
     return Q[:, keep], theta[:kk]
 
 
+def arnoldi(apply_B, r0, m, tol=0.0):
+    """Basic Arnoldi (Algorithm 1).  Returns (W [n x (j+1)], Hbar [(j+1) x j], beta,
+    gmres_rel) after j <= m steps."""
+    r0 = np.asarray(r0, dtype=np.float64)
+    beta = np.linalg.norm(r0)
+    W = [r0 / beta]
+    H = np.zeros((m + 1, m))
+    rel = 1.0
+    j = 0
+    while j < m:
+        v = apply_B(W[j])
+        Wm = np.stack(W, axis=1)
+        h = Wm.T @ v
+        v = v - Wm @ h
+        h2 = Wm.T @ v
+        v = v - Wm @ h2
+        H[: j + 1, j] = h + h2
+        H[j + 1, j] = np.linalg.norm(v)
+        j += 1
+        e1 = np.zeros(j + 1)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[: j + 1, :j], e1, rcond=None)[0]
+        rel = np.linalg.norm(e1 - H[: j + 1, :j] @ y) / beta
+        if H[j, j - 1] == 0.0 or rel <= tol:
+            W.append(v / H[j, j - 1] if H[j, j - 1] != 0.0 else np.zeros_like(v))
+            break
+        W.append(v / H[j, j - 1])
+    return np.stack(W, axis=1), H[: j + 1, :j], beta, rel
+
+
+def arnoldi_coarse_space(W, H, k, eps_tol, drop_rtol=1e-10):
+    """Ritz selection from an Arnoldi run (see the module note).  Returns (Z with
+    orthonormal columns, the selected Ritz values)."""
+    j = H.shape[1]
+    lam, V = np.linalg.eig(H[:j, :j])
+    order = np.argsort(lam.real, kind="stable")
+    cols, vals = [], []
+    taken = np.zeros(j, dtype=bool)
+    for i in order:
+        if taken[i] or not abs(lam[i].real) < eps_tol or len(vals) >= k:
+            continue
+        y = W[:, :j] @ V[:, i]
+        taken[i] = True
+        if abs(lam[i].imag) <= 1e-12 * abs(lam[i]):
+            cols.append(y.real)
+            vals.append(lam[i].real)
+        else:
+            cols += [y.real, y.imag]
+            vals += [lam[i].real, lam[i].real]
+            pair = np.argmin(np.abs(lam - np.conj(lam[i])) + taken * np.inf)
+            taken[pair] = True
+    if not cols:
+        raise ValueError("no Ritz value below eps_tol")
+    Q, R = np.linalg.qr(np.stack(cols, axis=1))
+    d = np.abs(np.diag(R))
+    keep = d >= drop_rtol * d.max()
+    return Q[:, keep], np.asarray(vals)
+
+
 def deflation_apriori(prob):
     """Z_S of Eq. 16-17 (the a priori coarse space of Sec. 3.3.1): column j = fraction
     of each pixel's hits inside interval j, Q/U rows zero; each T row sums to 1."""
@@ -173,4 +242,5 @@ def independent_columns(Z, drop_rtol=1e-10):
 
 
 __all__ = ["BlockJacobi", "TwoLevel", "lanczos_tridiagonal", "ritz_coarse_space",
-           "deflation_apriori", "deflation_apriori_merged", "independent_columns"]
+           "arnoldi", "arnoldi_coarse_space", "deflation_apriori", "deflation_apriori_merged",
+           "independent_columns"]

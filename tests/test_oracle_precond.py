@@ -106,6 +106,44 @@ def test_lanczos_vectors_are_minv_orthonormal(prob):
     assert np.linalg.norm(Rm[:, :-1]) <= 1e-8 * np.linalg.norm(V)
 
 
+def test_arnoldi_relation_and_ritz_residuals(prob):
+    # Algorithm 1 / Eq. A.2: B W_m = W_{m+1} Hbar_m with orthonormal W; Eq. A.4: the
+    # residual of a Ritz pair equals |h_{m+1,m} e_m^T v_i|
+    bd = precond.BlockJacobi(prob)
+    B = lambda x: bd.apply(prob.A(x))
+    b = prob.rhs(np.random.default_rng(8).standard_normal(prob.nt))
+    m = min(12, prob.n - 1)
+    W, H, beta, rel = precond.arnoldi(B, bd.apply(b), m)
+    j = H.shape[1]
+    assert j == m and beta > 0
+    np.testing.assert_allclose(W.T @ W, np.eye(j + 1), atol=1e-10)
+    BW = np.stack([B(W[:, c]) for c in range(j)], axis=1)
+    np.testing.assert_allclose(BW, W @ H, atol=1e-10 * np.abs(BW).max())
+    lam, V = np.linalg.eig(H[:j, :j])
+    for i in range(j):
+        y = W[:, :j] @ V[:, i]
+        res = np.linalg.norm(B(y.real) + 1j * B(y.imag) - lam[i] * y)
+        assert res == pytest.approx(abs(H[j, j - 1] * V[j - 1, i]), rel=1e-6, abs=1e-10)
+    # GMRES stopping: the residual estimate is the true left-preconditioned residual
+    W2, H2, beta2, rel2 = precond.arnoldi(B, bd.apply(b), prob.n, tol=1e-8)
+    j2 = H2.shape[1]
+    e1 = np.zeros(j2 + 1)
+    e1[0] = beta2
+    x = W2[:, :j2] @ np.linalg.lstsq(H2, e1, rcond=None)[0]
+    assert rel2 <= 1e-8
+    assert np.linalg.norm(bd.apply(b) - B(x)) / beta2 == pytest.approx(rel2, rel=1e-3, abs=1e-12)
+    # a full-dimension run reproduces the spectrum of M_BD A: the selected pairs are
+    # the smallest eigenpairs, orthonormalised
+    W3, H3, _, _ = precond.arnoldi(B, bd.apply(b), prob.n)
+    Z, vals = precond.arnoldi_coarse_space(W3, H3, 3, eps_tol=np.inf)
+    lam_true = np.sort(np.linalg.eigvals(bd.dense() @ prob.dense_A()).real)
+    np.testing.assert_allclose(np.sort(vals)[:3], lam_true[:3], rtol=1e-6)
+    np.testing.assert_allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-10)
+    # eps_tol keeps only the pairs below the threshold
+    _, v2 = precond.arnoldi_coarse_space(W3, H3, 64, eps_tol=0.5 * (lam_true[1] + lam_true[2]))
+    assert len(v2) == 2
+
+
 def test_adef2_spectrum_and_start(prob):
     # App. B: M_2lvl A and M_2lvl^(alt) A have the same spectrum; from x0 = Z E^-1 Z^T b
     # every A-DEF2 residual stays orthogonal to Z, and PCG reaches the dense solution
