@@ -238,6 +238,24 @@ mm_status mm_build_coarse_eps(mm_plan_t plan, int kmax, double eps_tol, int prec
                               double tol, int maxit);
 
 /*
+ * The a posteriori coarse space from the paper's own Ritz source (App. A, Algorithm 1):
+ * the basic Arnoldi process on B = M_BD A from w_1 = r_0/||r_0||, r_0 = M_BD b', in FP64
+ * (classical Gram-Schmidt with one re-orthogonalisation pass), run until the GMRES
+ * residual min ||beta e_1 - Hbar y|| <= tol beta, maxit steps or breakdown; the Ritz
+ * pairs of H_m (Eq. A.4; Hessenberg QR and inverse iteration on the host) with
+ * |Re lambda| < eps_tol (Sec. 5; the paper uses 0.2), at most kmax of them, smallest
+ * real part first -- a complex pair contributes the real and imaginary parts of one
+ * member's vector -- then Euclidean orthonormalisation with dropping and AZ, E, E^-1 as
+ * for mm_build_coarse.  mm_coarse_info returns the selected real parts.  The basis
+ * W_m lives in HBM (at most maxit + 1 columns of n doubles, grown on demand).
+ *   bprime  device double[n] or NULL (the b of the last mm_solve).
+ * Errors: MM_ERR_STATE when no Ritz value lies below eps_tol (previous space kept),
+ * MM_ERR_NUMERIC if the Hessenberg QR fails, MM_ERR_ARG for bad arguments.
+ */
+mm_status mm_build_coarse_arnoldi(mm_plan_t plan, int kmax, double eps_tol, const double* bprime, double tol,
+                                  int maxit);
+
+/*
  * Install a given coarse basis Z (host or device double[k * n], column j at Z[j*n ..]):
  * AZ = A Z, E = Z^T A Z, E^-1 as for mm_build_coarse -- to reuse a basis saved from an
  * earlier plan of the same pointing (mm_coarse_vectors) without its construction solve.

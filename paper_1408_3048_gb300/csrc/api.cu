@@ -756,6 +756,210 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
     P.coarse = cd;
 }
 
+// Orthonormalises the kc columns of Y (FP64 [kc][n], device) twice by Cholesky of the
+// Gram matrix (CholQR2), dropping in the first pass columns whose pivot is below 1e-10
+// of the largest kept one; Y is replaced, kc updated.
+static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc) {
+    cudaStream_t s = P.stream;
+    for (int pass = 0; pass < 2; ++pass) {
+        const std::vector<double> G = gram_host(P, Y, kc, Y, kc);
+        std::vector<double> W;
+        std::vector<int> kept;
+        if (!cholesky_drop(G, kc, pass == 0 ? 1e-10 : 0.0, W, kept) || kept.empty())
+            throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
+        const int knew = (int)kept.size();
+        double* C = dalloc<double>(W.size());
+        double* Y2 = nullptr;
+        try {
+            h2d(C, W.data(), W.size() * 8, s);
+            Y2 = dalloc<double>((size_t)knew * P.n);
+            launch_lincomb<double>(Y, kc, P.n, C, knew, Y2, s);
+            sync(s);
+        } catch (...) {
+            dfree(C);
+            dfree(Y2);
+            throw;
+        }
+        dfree(C);
+        dfree(Y);
+        Y = Y2;
+        kc = knew;
+    }
+}
+
+// The a posteriori coarse space from the paper's own Ritz source (App. A, Algorithm 1):
+// the basic Arnoldi process on B = M_BD A from w_1 = r_0 / ||r_0||, r_0 = M_BD b'
+// (x_0 = 0), in FP64 on the device (classical Gram-Schmidt as in Algorithm 1 with one
+// re-orthogonalisation pass), until the GMRES residual min ||beta e_1 - Hbar y|| (Givens
+// updates on the host) is <= tol beta, maxit steps, or breakdown.  The Ritz pairs of H_m
+// (Eq. A.4) with |Re lambda| < eps_tol (Sec. 5), at most kmax, smallest Re first, give
+// y = W_m v (a complex pair: the real and imaginary parts of one member), then CholQR2
+// with dropping and the coarse operators.
+static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const double* bprime, double tol,
+                                 int maxit) {
+    cudaStream_t s = P.stream;
+    if (kmax < 1 || kmax > KMAX) throw Error{MM_ERR_ARG, "kmax must be in [1, 64]"};
+    if (maxit < 1 || !(eps_tol > 0.0)) throw Error{MM_ERR_ARG, "need maxit >= 1 and eps_tol > 0"};
+    if (P.tz64.logn == 0) throw Error{MM_ERR_ARG, "the Arnoldi construction needs the FP64 Toeplitz block"};
+    const double* bsrc = bprime;
+    if (bsrc == nullptr) {
+        if (!P.have_b) throw Error{MM_ERR_STATE, "no right-hand side: pass bprime or call mm_solve first"};
+        bsrc = P.b64;
+    }
+    const int64_t n = P.n;
+    const int mcap = (int)std::min<int64_t>(maxit, n);
+    double* W = nullptr;
+    double* hv = nullptr;
+    double* Y = nullptr;
+    int wcap = std::min(mcap, 63) + 1;   // basis columns allocated; doubled on demand
+    try {
+        W = dalloc<double>((size_t)wcap * n);
+        hv = dalloc<double>((size_t)mcap + 1);
+        double* v = P.r64;       // scratch [n]
+        double* t = P.x64;       // scratch [n]
+        // w_1 = M_BD b' / ||M_BD b'||
+        launch_bd_apply<double>(P, bsrc, v, s);
+        const double beta = std::sqrt(dot64(P, v, v));
+        if (!(beta > 0.0)) throw Error{MM_ERR_ARG, "M_BD b' is zero"};
+        std::vector<double> sc = {1.0 / beta};
+        h2d(hv, sc.data(), 8, s);
+        launch_lincomb<double>(v, 1, n, hv, 1, W, s);
+        std::vector<double> H((size_t)(mcap + 1) * mcap, 0.0);   // Hbar, row-major (mcap + 1) x mcap
+        std::vector<double> gc, gs, g = {beta};                  // Givens of the GMRES update
+        int j = 0;
+        while (j < mcap) {
+            if (j + 2 > wcap) {
+                const int ncap = std::min(2 * wcap, mcap + 1);
+                double* W2 = dalloc<double>((size_t)ncap * n);
+                check_cuda(cudaMemcpyAsync(W2, W, (size_t)wcap * n * 8, cudaMemcpyDeviceToDevice, s), "grow W");
+                sync(s);
+                dfree(W);
+                W = W2;
+                wcap = ncap;
+            }
+            double* wj = W + (size_t)j * n;
+            apply_A<double>(P, wj, P.ax64, nullptr);
+            launch_bd_apply<double>(P, P.ax64, v, s);
+            std::vector<double> h((size_t)j + 1, 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                const std::vector<double> hp = gram_host(P, W, j + 1, v, 1);
+                h2d(hv, hp.data(), hp.size() * 8, s);
+                launch_lincomb<double>(W, j + 1, n, hv, 1, t, s);
+                launch_sub(v, t, v, n, s);
+                for (int i = 0; i <= j; ++i) h[(size_t)i] += hp[(size_t)i];
+            }
+            const double hn = std::sqrt(dot64(P, v, v));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * mcap + j] = h[(size_t)i];
+            H[(size_t)(j + 1) * mcap + j] = hn;
+            // GMRES residual: previous rotations on the new column, then a new one
+            std::vector<double> col(h);
+            col.push_back(hn);
+            for (int i = 0; i < j; ++i) {
+                const double a = col[(size_t)i], b = col[(size_t)i + 1];
+                col[(size_t)i] = gc[(size_t)i] * a + gs[(size_t)i] * b;
+                col[(size_t)i + 1] = -gs[(size_t)i] * a + gc[(size_t)i] * b;
+            }
+            const double rr = std::hypot(col[(size_t)j], col[(size_t)j + 1]);
+            const double cj = rr > 0.0 ? col[(size_t)j] / rr : 1.0, sj = rr > 0.0 ? col[(size_t)j + 1] / rr : 0.0;
+            gc.push_back(cj);
+            gs.push_back(sj);
+            g.push_back(-sj * g[(size_t)j]);
+            g[(size_t)j] = cj * g[(size_t)j];
+            ++j;
+            const bool stop = hn == 0.0 || std::fabs(g[(size_t)j]) <= tol * beta;
+            if (hn > 0.0) {
+                sc[0] = 1.0 / hn;
+                h2d(hv, sc.data(), 8, s);
+                launch_lincomb<double>(v, 1, n, hv, 1, W + (size_t)j * n, s);
+            }
+            if (stop) break;
+        }
+        sync(s);
+        // Ritz pairs of the square H_j
+        std::vector<double> Hj((size_t)j * j);
+        for (int r = 0; r < j; ++r)
+            for (int c = 0; c < j; ++c) Hj[(size_t)r * j + c] = H[(size_t)r * mcap + c];
+        std::vector<std::complex<double>> lam;
+        if (!hessenberg_eigenvalues(Hj, j, lam)) throw Error{MM_ERR_NUMERIC, "Hessenberg QR did not converge"};
+        std::vector<int> order((size_t)j);
+        for (int i = 0; i < j; ++i) order[(size_t)i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[(size_t)a].real() < lam[(size_t)b].real(); });
+        std::vector<char> taken((size_t)j, 0);
+        std::vector<std::vector<double>> cols;   // coefficient columns over W_j
+        std::vector<double> vals;
+        for (int i : order) {
+            if (taken[(size_t)i] || !(std::fabs(lam[(size_t)i].real()) < eps_tol) || (int)vals.size() >= kmax) continue;
+            taken[(size_t)i] = 1;
+            std::vector<std::complex<double>> ev = hessenberg_eigenvector(Hj, j, lam[(size_t)i]);
+            const bool real = std::fabs(lam[(size_t)i].imag()) <= 1e-12 * std::abs(lam[(size_t)i]);
+            if (real) {
+                // rotate the largest component onto the real axis, keep the real part
+                size_t im = 0;
+                for (size_t q = 1; q < ev.size(); ++q)
+                    if (std::abs(ev[q]) > std::abs(ev[im])) im = q;
+                const std::complex<double> ph = std::abs(ev[im]) / ev[im];
+                std::vector<double> c((size_t)j);
+                for (int q = 0; q < j; ++q) c[(size_t)q] = (ev[(size_t)q] * ph).real();
+                cols.push_back(c);
+                vals.push_back(lam[(size_t)i].real());
+            } else {
+                std::vector<double> cr((size_t)j), ci((size_t)j);
+                for (int q = 0; q < j; ++q) {
+                    cr[(size_t)q] = ev[(size_t)q].real();
+                    ci[(size_t)q] = ev[(size_t)q].imag();
+                }
+                cols.push_back(cr);
+                cols.push_back(ci);
+                vals.push_back(lam[(size_t)i].real());
+                vals.push_back(lam[(size_t)i].real());
+                int pair = -1;
+                double best = 0.0;
+                for (int q = 0; q < j; ++q) {
+                    if (taken[(size_t)q]) continue;
+                    const double dd = std::abs(lam[(size_t)q] - std::conj(lam[(size_t)i]));
+                    if (pair < 0 || dd < best) {
+                        pair = q;
+                        best = dd;
+                    }
+                }
+                if (pair >= 0) taken[(size_t)pair] = 1;
+            }
+        }
+        if (cols.empty()) throw Error{MM_ERR_STATE, "no Ritz value below eps_tol"};
+        if ((int)cols.size() > KMAX) cols.resize(KMAX), vals.resize(KMAX);
+        const int kk = (int)cols.size();
+        std::vector<double> C((size_t)j * kk);
+        for (int q = 0; q < j; ++q)
+            for (int c = 0; c < kk; ++c) C[(size_t)q * kk + c] = cols[(size_t)c][(size_t)q];
+        double* Cd = dalloc<double>(C.size());
+        Y = dalloc<double>((size_t)kk * n);
+        try {
+            h2d(Cd, C.data(), C.size() * 8, s);
+            launch_lincomb<double>(W, j, n, Cd, kk, Y, s);
+            sync(s);
+        } catch (...) {
+            dfree(Cd);
+            throw;
+        }
+        dfree(Cd);
+        dfree(W);
+        W = nullptr;
+        dfree(hv);
+        hv = nullptr;
+        int kc = kk;
+        orthonormalise_drop(P, Y, kc);
+        double* Zk = Y;
+        Y = nullptr;
+        vals.resize((size_t)kc);
+        install_coarse(P, Zk, kc, vals);
+    } catch (...) {
+        dfree(W);
+        dfree(hv);
+        dfree(Y);
+        throw;
+    }
+}
+
 // The a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) with its K interval columns
 // merged into r groups of consecutive intervals (interval i -> group floor(i r / K); a
 // merged column is the sum of its members, so observed temperature rows still sum to 1,
@@ -1730,6 +1934,11 @@ mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k) {
         }
         install_coarse(*P, Zd, k, {});
     });
+}
+
+mm_status mm_build_coarse_arnoldi(mm_plan_t plan, int kmax, double eps_tol, const double* bprime, double tol,
+                                  int maxit) {
+    return guarded(plan, [&] { build_coarse_arnoldi(*get(plan), kmax, eps_tol, bprime, tol, maxit); });
 }
 
 mm_status mm_build_coarse_apriori(mm_plan_t plan, int r) {

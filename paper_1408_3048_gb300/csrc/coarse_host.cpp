@@ -207,4 +207,140 @@ std::vector<double> spd_inverse_from_cholesky(const std::vector<double>& L, int 
     return inv;
 }
 
+using cplx = std::complex<double>;
+
+// Givens rotation (c real, s complex) with [c s; -conj(s) c] [a; b] = [r; 0].
+static void givens(cplx a, cplx b, double& c, cplx& s) {
+    const double na = std::abs(a), nb = std::abs(b);
+    if (nb == 0.0) {
+        c = 1.0;
+        s = 0.0;
+        return;
+    }
+    if (na == 0.0) {
+        c = 0.0;
+        s = std::conj(b) / nb;
+        return;
+    }
+    const double r = std::hypot(na, nb);
+    c = na / r;
+    s = (a / na) * std::conj(b) / r;
+}
+
+bool hessenberg_eigenvalues(const std::vector<double>& Hin, int n, std::vector<cplx>& lam) {
+    std::vector<cplx> A((size_t)n * n);
+    for (size_t i = 0; i < A.size(); ++i) A[i] = Hin[i];
+    auto at = [&](int i, int j) -> cplx& { return A[(size_t)i * n + j]; };
+    lam.assign((size_t)n, cplx(0.0));
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, sweeps = 0;
+    std::vector<double> cs((size_t)n);
+    std::vector<cplx> sn((size_t)n);
+    while (hi >= 0) {
+        if (hi == 0) {
+            lam[0] = at(0, 0);
+            break;
+        }
+        // start of the unreduced block ending at hi
+        int l = hi;
+        while (l > 0) {
+            const double scale = std::abs(at(l, l)) + std::abs(at(l - 1, l - 1));
+            if (std::abs(at(l, l - 1)) <= eps * (scale > 0.0 ? scale : 1.0)) {
+                at(l, l - 1) = 0.0;
+                break;
+            }
+            --l;
+        }
+        if (l == hi) {
+            lam[(size_t)hi] = at(hi, hi);
+            --hi;
+            sweeps = 0;
+            continue;
+        }
+        if (++sweeps > 60) return false;
+        // Wilkinson shift: the eigenvalue of the trailing 2 x 2 block nearer its last
+        // diagonal entry; every 11th sweep an exceptional shift breaks cycles
+        cplx mu;
+        const cplx a = at(hi - 1, hi - 1), b = at(hi - 1, hi), c = at(hi, hi - 1), d = at(hi, hi);
+        if (sweeps % 11 == 0) {
+            mu = d + cplx(std::abs(c), 0.0);
+        } else {
+            const cplx half = 0.5 * (a + d);
+            const cplx disc = std::sqrt(0.25 * (a - d) * (a - d) + b * c);
+            const cplx m1 = half + disc, m2 = half - disc;
+            mu = std::abs(m1 - d) < std::abs(m2 - d) ? m1 : m2;
+        }
+        // one QR step on rows / columns l..hi: A - mu I = Q R, A <- R Q + mu I
+        for (int k = l; k <= hi; ++k) at(k, k) -= mu;
+        for (int k = l; k < hi; ++k) {
+            double ck;
+            cplx sk;
+            givens(at(k, k), at(k + 1, k), ck, sk);
+            cs[(size_t)k] = ck;
+            sn[(size_t)k] = sk;
+            for (int j = k; j <= hi; ++j) {
+                const cplx x = at(k, j), y = at(k + 1, j);
+                at(k, j) = ck * x + sk * y;
+                at(k + 1, j) = -std::conj(sk) * x + ck * y;
+            }
+        }
+        for (int k = l; k < hi; ++k) {
+            const double ck = cs[(size_t)k];
+            const cplx sk = sn[(size_t)k];
+            const int top = std::min(k + 2, hi);
+            for (int i = l; i <= top; ++i) {
+                const cplx x = at(i, k), y = at(i, k + 1);
+                at(i, k) = ck * x + std::conj(sk) * y;
+                at(i, k + 1) = -sk * x + ck * y;
+            }
+        }
+        for (int k = l; k <= hi; ++k) at(k, k) += mu;
+    }
+    return true;
+}
+
+std::vector<cplx> hessenberg_eigenvector(const std::vector<double>& Hin, int n, cplx lam) {
+    double hnorm = 0.0;
+    for (double v : Hin) hnorm = std::max(hnorm, std::abs(v));
+    // a tiny offset keeps H - lam I invertible when lam is exact to rounding
+    const cplx shift = lam + cplx(1e-13 * (hnorm > 0.0 ? hnorm : 1.0), 0.0);
+    std::vector<cplx> U((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) U[(size_t)i * n + j] = Hin[(size_t)i * n + j] - (i == j ? shift : cplx(0.0));
+    // Hessenberg LU with partial pivoting between neighbouring rows: P_k L_k records
+    std::vector<cplx> mult((size_t)n, cplx(0.0));
+    std::vector<char> swapped((size_t)n, 0);
+    for (int k = 0; k + 1 < n; ++k) {
+        cplx* r0 = &U[(size_t)k * n];
+        cplx* r1 = &U[(size_t)(k + 1) * n];
+        if (std::abs(r1[k]) > std::abs(r0[k])) {
+            for (int j = k; j < n; ++j) std::swap(r0[j], r1[j]);
+            swapped[(size_t)k] = 1;
+        }
+        const cplx m = r0[k] != cplx(0.0) ? r1[k] / r0[k] : cplx(0.0);
+        mult[(size_t)k] = m;
+        for (int j = k; j < n; ++j) r1[j] -= m * r0[j];
+    }
+    for (int i = 0; i < n; ++i)
+        if (U[(size_t)i * n + i] == cplx(0.0)) U[(size_t)i * n + i] = cplx(1e-300, 0.0);
+    std::vector<cplx> x((size_t)n, cplx(1.0, 0.0));
+    for (int it = 0; it < 3; ++it) {
+        // apply the row operations to the right-hand side, then back substitution
+        for (int k = 0; k + 1 < n; ++k) {
+            if (swapped[(size_t)k]) std::swap(x[(size_t)k], x[(size_t)k + 1]);
+            x[(size_t)k + 1] -= mult[(size_t)k] * x[(size_t)k];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            cplx v = x[(size_t)i];
+            for (int j = i + 1; j < n; ++j) v -= U[(size_t)i * n + j] * x[(size_t)j];
+            x[(size_t)i] = v / U[(size_t)i * n + i];
+        }
+        double nrm = 0.0;
+        for (const cplx& v : x) nrm += std::norm(v);
+        nrm = std::sqrt(nrm);
+        for (cplx& v : x) v /= nrm;
+    }
+    return x;
+}
+
 }  // namespace mm

@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <complex>
 #include <vector>
 
 namespace mm {
@@ -20,5 +21,15 @@ bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::v
 bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L);
 // E^-1 (row-major, symmetric) from the lower Cholesky factor L of E: L^-T L^-1.
 std::vector<double> spd_inverse_from_cholesky(const std::vector<double>& L, int k);
+
+// Eigenvalues of a real upper Hessenberg matrix H (row-major n x n) by the shifted QR
+// algorithm in complex arithmetic (Givens rotations, Wilkinson shifts, deflation on
+// negligible subdiagonals); false if an eigenvalue needs more than 60 sweeps.
+bool hessenberg_eigenvalues(const std::vector<double>& H, int n, std::vector<std::complex<double>>& lam);
+
+// Unit eigenvector of H for the (computed) eigenvalue lam by inverse iteration with a
+// pivoted Hessenberg LU of H - lam I (O(n^2) per solve).
+std::vector<std::complex<double>> hessenberg_eigenvector(const std::vector<double>& H, int n,
+                                                         std::complex<double> lam);
 
 }  // namespace mm

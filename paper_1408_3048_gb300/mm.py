@@ -31,7 +31,7 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
            "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
-           "mm_build_coarse_eps", "mm_coarse_import"]
+           "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi"]
 
 
 class mm_psd(ctypes.Structure):
@@ -97,6 +97,7 @@ _SIGS = {
     "mm_build_coarse_apriori": (I32, [P, ctypes.c_int]),
     "mm_build_coarse_eps": (I32, [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int]),
     "mm_coarse_import": (I32, [P, P, ctypes.c_int]),
+    "mm_build_coarse_arnoldi": (I32, [P, ctypes.c_int, ctypes.c_double, P, ctypes.c_double, ctypes.c_int]),
     "mm_batch_config": (I32, [P, ctypes.c_int32, P, P, P]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
@@ -235,6 +236,11 @@ def mm_build_coarse(plan, k, precision, bprime, tol, maxit):
 def mm_build_coarse_eps(plan, kmax, eps_tol, precision, bprime, tol, maxit):
     _check(lib().mm_build_coarse_eps(plan, int(kmax), float(eps_tol), precision, _ptr(bprime), float(tol),
                                      int(maxit)), plan)
+
+
+def mm_build_coarse_arnoldi(plan, kmax, eps_tol, bprime, tol, maxit):
+    _check(lib().mm_build_coarse_arnoldi(plan, int(kmax), float(eps_tol), _ptr(bprime), float(tol), int(maxit)),
+           plan)
 
 
 def mm_coarse_import(plan, Z, k):
@@ -409,6 +415,12 @@ class Plan:
         """A posteriori coarse space from the Ritz pairs below eps_tol (at most kmax)."""
         self._sync_in()
         mm_build_coarse_eps(self.handle, kmax, eps_tol, precision, bprime, tol, maxit)
+        return mm_coarse_info(self.handle)
+
+    def build_coarse_arnoldi(self, eps_tol, kmax=64, bprime=None, tol=1e-6, maxit=1000):
+        """A posteriori coarse space from Arnoldi on M_BD A (Algorithm 1); returns (k, values)."""
+        self._sync_in()
+        mm_build_coarse_arnoldi(self.handle, kmax, eps_tol, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
 
     def coarse_import(self, Z):

@@ -228,6 +228,32 @@ def test_coarse_threshold_and_import(case):
     other.close()
 
 
+def test_coarse_arnoldi(case):
+    # the paper's Ritz source (Algorithm 1 on M_BD A) with eps_tol selection
+    name, scan, pr, plan = case
+    d0, d1 = _data(scan, 0), _data(scan, 1)
+    b0 = pr.rhs(d0)
+    bd = oprec.BlockJacobi(pr)
+    B = lambda x: bd.apply(pr.A(x))
+    W, H, _, _ = oprec.arnoldi(B, bd.apply(b0), 400, tol=1e-8)
+    lam = np.sort(np.linalg.eigvals(H[:H.shape[1], :]).real)
+    eps = 0.5 * (lam[2] + lam[3])
+    Zo, vo = oprec.arnoldi_coarse_space(W, H, 64, eps)
+    kk, vals = plan.build_coarse_arnoldi(eps, kmax=64, bprime=_cuda(b0), tol=1e-8, maxit=400)
+    assert kk == Zo.shape[1] == 3
+    np.testing.assert_allclose(np.sort(vals), np.sort(vo), rtol=1e-6)
+    Zl = plan.coarse_vectors()
+    np.testing.assert_allclose(Zl.T @ Zl, np.eye(kk), atol=1e-10)
+    assert np.linalg.norm(Zl - Zo @ (Zo.T @ Zl)) <= 1e-5 * np.sqrt(kk)   # same span
+    ref = pcg(pr.A, oprec.TwoLevel(pr, bd, Zo).apply, pr.rhs(d1), 1e-6, 3000)
+    m, st, status = plan.solve(_cuda(d1), tol=1e-6, maxit=3000, kind=mm.MM_PREC_TWOLEVEL)
+    assert status == mm.MM_OK and abs(st["iters"] - ref.iters) <= 2, (st["iters"], ref.iters)
+    assert _rel(m.cpu().numpy(), ref.x) <= 1e-6
+    with pytest.raises(mm.MMError) as e:
+        plan.build_coarse_arnoldi(0.5 * lam[0], bprime=_cuda(b0), tol=1e-8, maxit=400)
+    assert e.value.status == mm.MM_ERR_STATE
+
+
 def test_adef2(case):
     # the A-DEF2 form of App. B on the library's a posteriori space, from its starting
     # vector, against the oracle's operator and PCG
