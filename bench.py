@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="iteration counts of block-Jacobi and two-level PCG over Toeplitz bandwidths "
+                         "and knee frequencies on the 2^24-sample workload (one JSON line per case; no "
+                         "bench line)")
     ap.add_argument("--profile", action="store_true",
                     help="build, warm up, then run one step between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off); prints a one-line JSON summary only")
@@ -422,7 +426,11 @@ def run_ours(a, rank, world, local_rank):
                             0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)[0])):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        kc = build()
+        try:
+            kc = build()
+        except mm.MMError as e:
+            coarse_variants[name] = {"error": str(e)}
+            continue
         torch.cuda.synchronize()
         tb = time.perf_counter() - t
         _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
@@ -431,10 +439,11 @@ def run_ours(a, rank, world, local_rank):
                                  "fp64_iters": s64["iters"], "mixed_s": smx["ms_total"] / 1e3,
                                  "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
     # the A-DEF2 form (App. B) on the last coarse space
+    plan.build_coarse_eps(0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)
     _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_FP64, out=m)
     _, smx, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_MIXED, out=m)
     coarse_variants["aposteriori_eps0.2_adef2"] = {
-        "k": coarse_variants["aposteriori_eps0.2"]["k"], "fp64_s": s64["ms_total"] / 1e3, "fp64_iters": s64["iters"],
+        "k": coarse_variants.get("aposteriori_eps0.2", {}).get("k"), "fp64_s": s64["ms_total"] / 1e3, "fp64_iters": s64["iters"],
         "mixed_s": smx["ms_total"] / 1e3, "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
 
     if rank != 0:
@@ -491,8 +500,59 @@ def run_ours(a, rank, world, local_rank):
     plan.close()
 
 
+def run_sweep():
+    """Bandwidth and knee-frequency sweeps (the paper's Sec. 5 studies of lambda_T and
+    f_knee, on the synthetic 2^24-sample polarised scan): iterations and times to 1e-6 of
+    FP64 block-Jacobi, two-level a priori (Z_S, 32 interval groups) and two-level a
+    posteriori (Ritz values below eps_tol = 0.2) PCG, and of the mixed-precision two-level
+    solve."""
+    import torch
+    from paper_1408_3048_gb300 import mm, synth
+    base = synth.config(CONFIG)
+    sky = synth.sky_map(base.npix_sky, base.ncomp, 1000 + CONFIG)
+    cases = [(lam, 1.0) for lam in (1024, 2048, 4096, 8192, 16384)] + [(4096, f) for f in (0.25, 4.0)]
+    for lam, fk in cases:
+        psds = np.array(base.psds, dtype=np.float64).reshape(-1, 3).copy()
+        psds[:, 1] *= fk
+        scan = synth.config(CONFIG)
+        scan.lam = lam
+        scan.psds = psds
+        d0 = synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, psds, scan.fsamp, 2200))
+        d1 = synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, psds, scan.fsamp, 2201))
+        plan = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, psds, lam, scan.fsamp)
+        dc0, dc1 = torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()
+        m = torch.empty(plan.n, dtype=torch.float64, device="cuda")
+        out = {"lambda": lam, "fknee_scale": fk}
+        if plan.fft_block_f64:
+            _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_BD, mm.MM_SOLVE_FP64, out=m)
+            out["bd_fp64"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3}
+        b0 = plan.rhs(dc0) if plan.fft_block_f64 else None
+        for name, build in (("apriori_r32", lambda: plan.build_coarse_apriori(K_COARSE)),
+                            ("aposteriori_eps0.2", lambda: plan.build_coarse_eps(
+                                0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=5000)[0])):
+            try:
+                k = build()
+            except mm.MMError as e:
+                out[name] = {"error": str(e)}
+                continue
+            rec = {"k": k}
+            if plan.fft_block_f64:
+                _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
+                rec["fp64"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3}
+            _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, out=m)
+            rec["mixed"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3, "rel_resid": st["rel_resid"]}
+            out[name] = rec
+        print(json.dumps(out), flush=True)
+        plan.close()
+        del dc0, dc1, m
+        torch.cuda.empty_cache()
+
+
 def main():
     a = parse()
+    if a.sweep:
+        run_sweep()
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

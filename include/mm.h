@@ -270,10 +270,13 @@ mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k);
  * stationary interval j (temperature rows; Q/U rows 0), so each temperature row sums to
  * 1.  Its K columns are merged into r groups of consecutive intervals (interval i joins
  * group floor(i r / K); merged column = sum of its members, rows still sum to 1), as the
- * paper allows to reduce the coarse dimension.  Columns dependent on earlier ones
- * (Cholesky pivot of Z^T Z below 1e-10 times the largest kept pivot; intervals that see
- * the same hit fractions give equal columns) are dropped; the kept columns are used as
- * they are.  Then AZ, E and E^-1 as for mm_build_coarse.  No solve is needed.
+ * paper allows to reduce the coarse dimension.  The merged columns are replaced by an
+ * orthonormal basis of their range (Cholesky QR twice; columns whose pivot is below
+ * 1e-10 times the largest kept one are dropped -- intervals that see the same hit
+ * fractions give equal columns).  M_2lvl depends on Z only through its range, and the
+ * orthonormal basis keeps E = Z^T A Z as well conditioned as A on that range (raw
+ * hit-fraction columns of an evenly covered patch are nearly parallel).  Then AZ, E and
+ * E^-1 as for mm_build_coarse.  No solve is needed.
  *   r       1 <= r <= min(64, K).
  * Errors: MM_ERR_ARG for r out of range, MM_ERR_NOT_SPD when E is not positive definite.
  */
@@ -284,8 +287,8 @@ mm_status mm_build_coarse_apriori(mm_plan_t plan, int r);
 mm_status mm_coarse_info(mm_plan_t plan, int32_t* k_kept, double* ritz_values);
 
 /* The coarse basis Z (FP64), column j at Z[j*n .. j*n + n), host or device
- * double[k_kept * n]: orthonormal for the a posteriori space, the merged hit fractions
- * for the a priori one.  MM_ERR_STATE before a coarse space was built. */
+ * double[k_kept * n], orthonormal (for the a priori space: a basis of the range of the
+ * merged hit fractions).  MM_ERR_STATE before a coarse space was built. */
 mm_status mm_coarse_vectors(mm_plan_t plan, double* Z);
 
 /*

@@ -738,9 +738,17 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
                 const double v = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
                 E[(size_t)i * k + j] = E[(size_t)j * k + i] = v;
             }
-        std::vector<double> Lf;
-        if (!cholesky_lower(E, k, Lf)) throw Error{MM_ERR_NOT_SPD, "coarse operator E is not positive definite"};
-        const std::vector<double> Einv = spd_inverse_from_cholesky(Lf, k);
+        std::vector<double> Lf, Einv;
+        if (cholesky_lower(E, k, Lf)) {
+            Einv = spd_inverse_from_cholesky(Lf, k);
+        } else {
+            // E is SPD in exact arithmetic but can be numerically indefinite when Z holds
+            // near-null vectors of A (the a priori Z_S contains the temperature ones
+            // vector, Eq. 15): invert by LU with partial pivoting as App. C does
+            double ratio = 0.0;
+            if (!lu_inverse(E, k, Einv, &ratio) || !(ratio > 1e-15))
+                throw Error{MM_ERR_NOT_SPD, "coarse operator E is singular"};
+        }
         cd.Einv = dalloc<double>(Einv.size());
         h2d(cd.Einv, Einv.data(), Einv.size() * 8, s);
         cd.Z32 = dalloc<float>((size_t)k * P.n);
@@ -963,43 +971,24 @@ static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const 
 // The a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) with its K interval columns
 // merged into r groups of consecutive intervals (interval i -> group floor(i r / K); a
 // merged column is the sum of its members, so observed temperature rows still sum to 1,
-// Q/U rows are 0).  Columns dependent on earlier ones (Cholesky pivot of Z^T Z below
-// 1e-10 of the largest kept pivot) are dropped -- intervals that see the same hit
-// fractions give equal columns -- and the kept columns are used as they are (not
-// orthonormalised).
+// Q/U rows are 0), then replaced by an orthonormal basis of its range (CholQR2, columns
+// whose Gram-Cholesky pivot is below 1e-10 of the largest kept one dropped: intervals
+// that see the same hit fractions give equal columns).  M_2lvl depends on Z only through
+// its range, and raw hit-fraction columns of a scan that covers the patch evenly are
+// nearly parallel, which leaves E = Z^T A Z numerically singular; the orthonormal basis
+// keeps E as well conditioned as A is on that range.
 static void build_coarse_apriori(PlanHolder& P, int r) {
-    cudaStream_t s = P.stream;
     if (r < 1 || r > KMAX || r > P.K) throw Error{MM_ERR_ARG, "r must be in [1, min(64, K)]"};
     double* Z = dalloc<double>((size_t)r * P.n);
-    double* C = nullptr;
-    double* Zk = nullptr;
     try {
-        launch_apriori(P, r, Z, s);
-        const std::vector<double> G = gram_host(P, Z, r, Z, r);
-        std::vector<double> W;
-        std::vector<int> kept;
-        if (!cholesky_drop(G, r, 1e-10, W, kept) || kept.empty())
-            throw Error{MM_ERR_NUMERIC, "a priori coarse space has no independent column"};
-        const int kk = (int)kept.size();
-        // select the kept columns (a 0/1 combination through the same lincomb kernel)
-        std::vector<double> Sel((size_t)r * kk, 0.0);
-        for (int c = 0; c < kk; ++c) Sel[(size_t)kept[(size_t)c] * kk + c] = 1.0;
-        C = dalloc<double>(Sel.size());
-        h2d(C, Sel.data(), Sel.size() * 8, s);
-        Zk = dalloc<double>((size_t)kk * P.n);
-        launch_lincomb<double>(Z, r, P.n, C, kk, Zk, s);
-        sync(s);
-        dfree(C);
-        C = nullptr;
-        dfree(Z);
+        launch_apriori(P, r, Z, P.stream);
+        int kc = r;
+        orthonormalise_drop(P, Z, kc);
+        double* Zt = Z;
         Z = nullptr;
-        double* Zt = Zk;
-        Zk = nullptr;
-        install_coarse(P, Zt, kk, {});
+        install_coarse(P, Zt, kc, {});
     } catch (...) {
         dfree(Z);
-        dfree(C);
-        dfree(Zk);
         throw;
     }
 }

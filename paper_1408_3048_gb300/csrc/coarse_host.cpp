@@ -343,4 +343,43 @@ std::vector<cplx> hessenberg_eigenvector(const std::vector<double>& Hin, int n, 
     return x;
 }
 
+bool lu_inverse(const std::vector<double>& E, int k, std::vector<double>& inv, double* min_pivot_ratio) {
+    // Gauss-Jordan on [E | I] with partial pivoting (the LU route of App. C)
+    std::vector<double> a(E);
+    inv.assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) inv[(size_t)i * k + i] = 1.0;
+    double maxabs = 0.0;
+    for (double v : E) maxabs = std::max(maxabs, std::fabs(v));
+    double minpiv = 1e300;
+    for (int c = 0; c < k; ++c) {
+        int p = c;
+        for (int r = c + 1; r < k; ++r)
+            if (std::fabs(a[(size_t)r * k + c]) > std::fabs(a[(size_t)p * k + c])) p = r;
+        const double piv = a[(size_t)p * k + c];
+        minpiv = std::min(minpiv, std::fabs(piv));
+        if (piv == 0.0) return false;
+        if (p != c) {
+            for (int j = 0; j < k; ++j) {
+                std::swap(a[(size_t)p * k + j], a[(size_t)c * k + j]);
+                std::swap(inv[(size_t)p * k + j], inv[(size_t)c * k + j]);
+            }
+        }
+        for (int j = 0; j < k; ++j) {
+            a[(size_t)c * k + j] /= piv;
+            inv[(size_t)c * k + j] /= piv;
+        }
+        for (int r = 0; r < k; ++r) {
+            if (r == c) continue;
+            const double f = a[(size_t)r * k + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < k; ++j) {
+                a[(size_t)r * k + j] -= f * a[(size_t)c * k + j];
+                inv[(size_t)r * k + j] -= f * inv[(size_t)c * k + j];
+            }
+        }
+    }
+    if (min_pivot_ratio) *min_pivot_ratio = maxabs > 0.0 ? minpiv / maxabs : 0.0;
+    return true;
+}
+
 }  // namespace mm

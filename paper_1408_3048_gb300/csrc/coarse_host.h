@@ -22,6 +22,10 @@ bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L)
 // E^-1 (row-major, symmetric) from the lower Cholesky factor L of E: L^-T L^-1.
 std::vector<double> spd_inverse_from_cholesky(const std::vector<double>& L, int k);
 
+// E^-1 by Gauss-Jordan elimination with partial pivoting; false on an exactly zero
+// pivot.  *min_pivot_ratio (may be null) = smallest |pivot| / max |E_ij|.
+bool lu_inverse(const std::vector<double>& E, int k, std::vector<double>& inv, double* min_pivot_ratio);
+
 // Eigenvalues of a real upper Hessenberg matrix H (row-major n x n) by the shifted QR
 // algorithm in complex arithmetic (Givens rotations, Wilkinson shifts, deflation on
 // negligible subdiagonals); false if an eigenvalue needs more than 60 sweeps.
