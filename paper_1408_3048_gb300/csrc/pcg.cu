@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
             a.x[i] = xi;
             a.r[i] = ri;
         }
+        __syncthreads();   // bd_into_z reads whole pixels of r written element-wise above
         bd_into_z<T, NC>(a, p0, p1);
         // every block has read the first coarse partials before they are overwritten
         if (!grid_sync(a.bar, a.flags)) return;
