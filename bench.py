@@ -307,13 +307,28 @@ def run_reference(a, rank, world):
 
 
 # -------------------------------------------------------------------- GPU arm
+def replica_realisations(rank):
+    """Noise realisations of one rank: 0 builds the coarse space, 1 + rank is solved (each
+    replica solves its own realisation; no data crosses ranks)."""
+    return [0, 1 + rank]
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of x (float) over the ranks; the collective is timing only."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     from paper_1408_3048_gb300 import mm
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    scan, (d0, d1) = make_inputs([0, 1 + rank])
+    scan, (d0, d1) = make_inputs(replica_realisations(rank))
     plan = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
                    scan.lam, scan.fsamp, stream=stream)
     dc0 = torch.from_numpy(d0).to(dev)
@@ -372,10 +387,7 @@ def run_ours(a, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     launches = (mm.mm_launch_count() - n0) // max(a.steps, 1)
     clk = clocks.stop()
-    t_max = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    ms_step = float(t_max.item()) / a.steps
+    ms_step = max_over_ranks(ms_total, world, dev) / a.steps
     st = stats[-1]
     err_vs_fp64 = float(torch.linalg.norm(m - m_ref64) / torch.linalg.norm(m_ref64))
 
