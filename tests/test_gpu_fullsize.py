@@ -85,6 +85,7 @@ def test_temperature_2e27_mixed_precision_error_vs_oracle():
 
 
 def test_differentiable_2e29_solve_and_gradient():
+    # (takes a few minutes: 2^29 samples, five plans)
     # 1024 x 768 grid, 64 detectors x 2^23 samples, lambda 8192, two-level k = 64:
     # properties that hold at any size (the oracle cannot run this size)
     scan = synth.config(5)
@@ -118,4 +119,21 @@ def test_differentiable_2e29_solve_and_gradient():
 
     fd = (loss(d + h * e) - loss(d - h * e)) / (2 * h)
     assert fd == pytest.approx(float(dd @ e), rel=1e-3)
+    # noise-PSD gradient (f_knee, alpha of PSD 0) against central differences of
+    # re-planned problems, relative step 1e-4 (the loss depends on m only, so the
+    # perturbed solves need no coarse space)
+    psds = np.array(scan.psds, dtype=np.float64).reshape(-1, 3)
+    for comp in (1, 2):
+        th = psds[0, comp]
+        hp = 1e-4 * th
+        Ls = []
+        for sgn in (1.0, -1.0):
+            ps = psds.copy()
+            ps[0, comp] = th + sgn * hp
+            p2 = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, ps, scan.lam,
+                         scan.fsamp, stream=plan.stream)
+            m2, _, _ = p2.solve(d, tol=1e-11, maxit=20000, kind=mm.MM_PREC_BD, solver=mm.MM_SOLVE_MIXED)
+            Ls.append(0.5 * float(torch.sum((m2 - mref) ** 2)))
+            p2.close()
+        assert (Ls[0] - Ls[1]) / (2 * hp) == pytest.approx(float(dp[0][comp]), rel=1e-3)
     plan.close()
