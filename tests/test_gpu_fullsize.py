@@ -137,3 +137,32 @@ def test_differentiable_2e29_solve_and_gradient():
             p2.close()
         assert (Ls[0] - Ls[1]) / (2 * hp) == pytest.approx(float(dp[0][comp]), rel=1e-3)
     plan.close()
+
+
+@pytest.fixture(scope="module")
+def realisations_2e24():
+    scan = synth.config(2)
+    sky = synth.sky_map(scan.npix_sky, scan.ncomp, 1002)
+    return np.stack([synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds,
+                                                                  scan.fsamp, 2400 + r)) for r in range(64)])
+
+
+@pytest.mark.parametrize("lam", [1024, 16384])
+def test_batched_2e24_64_realisations(lam, realisations_2e24):
+    # the batched Monte-Carlo workload: 64 noise realisations of the 2^24-sample polarised
+    # scan in one batched solve; every checked column's true residual, recomputed with the
+    # FP64 operator (a separate code path from the batched FP32 one), meets the
+    # tolerance, and one column's map matches its single-RHS mixed solve
+    scan = synth.config(2)
+    scan.lam = lam
+    plan = _plan(scan, stream=torch.cuda.Stream())
+    Dc = torch.from_numpy(realisations_2e24).cuda()
+    M, st, status = plan.solve_batch(Dc, tol=1e-6, maxit=5000)
+    assert status == mm.MM_OK and all(x["converged"] == 1 for x in st)
+    for r in (0, 17, 63):
+        b = plan.rhs(Dc[r].contiguous())
+        res = b - plan.apply_A(M[r].contiguous())
+        assert float(torch.linalg.norm(res) / torch.linalg.norm(b)) <= 1e-6
+    m1, _, _ = plan.solve(Dc[5].contiguous(), tol=1e-6, maxit=5000, solver=mm.MM_SOLVE_MIXED)
+    assert float(torch.linalg.norm(M[5] - m1) / torch.linalg.norm(m1)) <= 1e-4
+    plan.close()
