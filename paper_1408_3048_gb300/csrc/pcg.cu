@@ -64,8 +64,18 @@ __device__ double block_total(DotAcc<double> acc, double* sh) {
 // shuffle tree), valid in every thread.  Call with all threads.
 __device__ double grid_total(const double* part, int slot, double* sh) {
     if (threadIdx.x < 32) {
+        // each lane issues its (up to 8) loads before adding them in block order
         double s = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * PSTRIDE + slot);
+        for (unsigned base = 0; base < gridDim.x; base += 256) {
+            double v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const unsigned b = base + threadIdx.x + 32u * t;
+                v[t] = b < gridDim.x ? __ldcg(part + (size_t)b * PSTRIDE + slot) : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) s += v[t];
+        }
         s = warp_sum64(s);
         if (threadIdx.x == 0) sh[0] = s;
     }
@@ -121,28 +131,46 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = w; j < a.k; j += nw) {
         const double* col = a.partial + S_COARSE + j;
+        // each lane issues its (up to 8) loads before adding them in block order
         if constexpr (sizeof(T) == 4) {
             float hi = 0.f, lo = 0.f;
-            for (unsigned b = l; b < gridDim.x; b += 32) {
-                const float2 p = __ldcg(reinterpret_cast<const float2*>(col + (size_t)b * PSTRIDE));
-                pair_add(hi, lo, p.x, p.y);
+            for (unsigned base = 0; base < gridDim.x; base += 256) {
+                float2 v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const unsigned b = base + l + 32u * t;
+                    v[t] = b < gridDim.x ? __ldcg(reinterpret_cast<const float2*>(col + (size_t)b * PSTRIDE))
+                                         : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) pair_add(hi, lo, v[t].x, v[t].y);
             }
             warp_pair_reduce(hi, lo);
             if (l == 0) u_sh[j] = (double)hi + (double)lo;
         } else {
             double s = 0.0;
-            for (unsigned b = l; b < gridDim.x; b += 32) s += __ldcg(col + (size_t)b * PSTRIDE);
+            for (unsigned base = 0; base < gridDim.x; base += 256) {
+                double v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const unsigned b = base + l + 32u * t;
+                    v[t] = b < gridDim.x ? __ldcg(col + (size_t)b * PSTRIDE) : 0.0;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) s += v[t];
+            }
             s = warp_sum64(s);
             if (l == 0) u_sh[j] = s;
         }
     }
     __syncthreads();
-    for (int i = w; i < a.k; i += nw) {
-        const double* row = a.Einv + (size_t)i * a.k;
+    // one thread per row of E^-1 (k <= 64 threads; a short FP64 FMA chain each rather
+    // than warp trees, whose FP64 shuffles and adds occupy GB300's narrow FP64 pipe)
+    if (threadIdx.x < a.k) {
+        const double* row = a.Einv + (size_t)threadIdx.x * a.k;
         double s = 0.0;
-        for (int j = l; j < a.k; j += 32) s += __ldg(row + j) * u_sh[j];
-        s = warp_sum64(s);
-        if (l == 0) v_sh[i] = s;
+        for (int j = 0; j < a.k; ++j) s = fma(__ldg(row + j), u_sh[j], s);
+        v_sh[threadIdx.x] = s;
     }
     __syncthreads();
 }
