@@ -748,6 +748,12 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
             double ratio = 0.0;
             if (!lu_inverse(E, k, Einv, &ratio) || !(ratio > 1e-15))
                 throw Error{MM_ERR_NOT_SPD, "coarse operator E is singular"};
+            // symmetric like E (the PCG kernels read E^-1 by columns)
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < i; ++j) {
+                    const double v = 0.5 * (Einv[(size_t)i * k + j] + Einv[(size_t)j * k + i]);
+                    Einv[(size_t)i * k + j] = Einv[(size_t)j * k + i] = v;
+                }
         }
         cd.Einv = dalloc<double>(Einv.size());
         h2d(cd.Einv, Einv.data(), Einv.size() * 8, s);

@@ -165,11 +165,12 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
     }
     __syncthreads();
     // one thread per row of E^-1 (k <= 64 threads; a short FP64 FMA chain each rather
-    // than warp trees, whose FP64 shuffles and adds occupy GB300's narrow FP64 pipe)
+    // than warp trees, whose FP64 shuffles and adds occupy GB300's narrow FP64 pipe).
+    // E^-1 is symmetric: thread i reads column i, so a warp's loads for one j coalesce.
     if (threadIdx.x < a.k) {
-        const double* row = a.Einv + (size_t)threadIdx.x * a.k;
         double s = 0.0;
-        for (int j = 0; j < a.k; ++j) s = fma(__ldg(row + j), u_sh[j], s);
+#pragma unroll 8
+        for (int j = 0; j < a.k; ++j) s = fma(__ldg(a.Einv + (size_t)j * a.k + threadIdx.x), u_sh[j], s);
         v_sh[threadIdx.x] = s;
     }
     __syncthreads();
@@ -263,7 +264,7 @@ __device__ void bd_into_z(const PcgArgs<T>& a, int p0, int p1) {
 // z = M r, p = z, rho = r^T z, bb = b^T b.
 template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
-    __shared__ double sh[32];
+    __shared__ double sh[40];   // [0] total, [1 + w] per-warp sums (up to 32 warps)
     __shared__ double v_sh[KMAX];
     int p0, p1;
     block_pixels(a.npix, p0, p1);
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
 // ------------------------------------------------------------------- iteration kernel
 template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
-    __shared__ double sh[32];
+    __shared__ double sh[40];   // [0] total, [1 + w] per-warp sums (up to 32 warps)
     __shared__ double v_sh[KMAX];
     if (*(volatile int*)&a.flags[F_DONE]) return;
     int p0, p1;
@@ -493,7 +494,7 @@ int pcg_max_blocks(int num_sms) {
 // Deterministic FP64 dot: per-block partials then one block sums them in order.
 template <typename TA, typename TB>
 __global__ void dot_partial_kernel(const TA* a, const TB* b, int64_t n, double* part) {
-    __shared__ double sh[32];
+    __shared__ double sh[40];   // [0] total, [1 + w] per-warp sums (up to 32 warps)
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s += (double)a[i] * (double)b[i];

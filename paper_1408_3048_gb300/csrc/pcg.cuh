@@ -5,7 +5,7 @@
 
 namespace mm {
 
-constexpr int PCG_THREADS = 512;
+constexpr int PCG_THREADS = 1024;
 constexpr int KMAX = 64;          // largest coarse dimension
 constexpr int DOT_BLOCKS = 304;   // blocks of the stand-alone dot / vector kernels
 
