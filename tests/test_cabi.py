@@ -39,3 +39,40 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert h.value is None
     assert L.mm_apply_A(None, 0, None, None) == mm.MM_ERR_ARG
     L.mm_destroy(None)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without libmm.so every entry point raises instead of computing
+    from paper_1408_3048_gb300 import mm
+    import pytest
+    monkeypatch.setattr(mm, "LIBPATH", str(tmp_path / "absent" / "libmm.so"))
+    monkeypatch.setattr(mm, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        mm.lib()
+    with pytest.raises(RuntimeError):
+        mm.mm_version()
+
+
+def test_invalid_plans_are_rejected_on_the_host():
+    # argument checks that run before any device work (CPU): bad ncomp, lambda >= the
+    # shortest interval, non-increasing offsets
+    import numpy as np
+    from paper_1408_3048_gb300 import mm
+    L = mm.lib()
+    pix = np.zeros(100, dtype=np.int32)
+    off = np.array([0, 50, 100], dtype=np.int64)
+    ipsd = np.zeros(2, dtype=np.int32)
+    psd = (mm.mm_psd * 1)(mm.mm_psd(1.0, 1.0, 1.0))
+
+    def plan(lam=10, ncomp=1, pix_=pix, off_=off):
+        o = mm.mm_opts(ncomp=ncomp, lambda_=lam, window=0, fsamp=100.0, rcond_min=1e-6)
+        h = ctypes.c_void_p()
+        st = L.mm_plan(ctypes.byref(h), pix_.ctypes.data, pix_.size, 4, None, off_.ctypes.data, off_.size - 1,
+                       ipsd.ctypes.data, psd, 1, ctypes.byref(o))
+        if h.value:
+            L.mm_destroy(h)
+        return st
+
+    assert plan(ncomp=2) == mm.MM_ERR_ARG
+    assert plan(lam=50) == mm.MM_ERR_ARG
+    assert plan(off_=np.array([0, 60, 50, 100], dtype=np.int64)) == mm.MM_ERR_ARG

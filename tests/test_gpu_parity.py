@@ -416,3 +416,37 @@ def test_long_band_uses_cluster_blocks(lam):
     z32 = plan.apply_ninv(tc, mm.MM_FP32).cpu().numpy()
     assert _rel(z32, pr.Ninv(tc.double().cpu().numpy(), route="fft")) <= 2e-5
     plan.close()
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_white_noise_is_binned_map(ncomp):
+    # white noise with lambda = 0 (N diagonal, Sec. 2): the GLS map is the per-pixel
+    # noise-weighted binned map, written here directly from the data (no oracle), and
+    # M_BD is A^-1, so PCG converges in one step.  Intervals include a single sample.
+    rng = np.random.default_rng(30 + ncomp)
+    npix, nt = 40, 5000
+    pix = rng.integers(0, npix, nt).astype(np.int32)
+    offsets = np.array([0, 1, 7, 1200, 3000, nt], dtype=np.int64)
+    sig = np.array([1.0, 0.5, 2.0])
+    ipsd = np.array([0, 1, 2, 0, 1], dtype=np.int32)
+    psds = [(s, 0.0, 1.0) for s in sig]
+    phi = rng.uniform(0, np.pi, nt)
+    w = np.stack([np.cos(2 * phi), np.sin(2 * phi)], axis=1) if ncomp == 3 else None
+    d = rng.standard_normal(nt)
+    plan = mm.Plan(pix, npix, w, offsets, ipsd, psds, 0, 100.0)
+    m, st, status = plan.solve(_cuda(d), tol=1e-12, maxit=10)
+    assert status == mm.MM_OK and st["iters"] <= 1
+    inv = np.repeat(1.0 / sig[ipsd] ** 2, np.diff(offsets))
+    o2s, _ = plan.pixels()
+    mh = m.cpu().numpy().reshape(-1, ncomp)
+    for q, p in enumerate(o2s):
+        sel = pix == p
+        if ncomp == 1:
+            ref = np.sum(inv[sel] * d[sel]) / np.sum(inv[sel])
+            assert abs(mh[q, 0] - ref) <= 1e-12 * max(1.0, abs(ref))
+        else:
+            W = np.column_stack([np.ones(sel.sum()), w[sel]])
+            Bp = (W * inv[sel, None]).T @ W
+            ref = np.linalg.solve(Bp, (W * inv[sel, None]).T @ d[sel])
+            np.testing.assert_allclose(mh[q], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    plan.close()
