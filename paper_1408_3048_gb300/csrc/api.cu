@@ -1610,15 +1610,23 @@ static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_op
         check_cuda(cudaEventRecord(P.ev0, s), "event");
         std::vector<double> bb(Rc), rr(Rc);
         std::vector<int> iters(Rc, 0), outer(Rc, 0), fp64(Rc, 0);
-        // b_r = P^T N^-1 d_r (FP64)
+        // the group's data on the device (host data copied once; the FP64 residuals read it
+        // again every refinement step)
+        const double* Dg = D + (size_t)c0 * nt;
+        double* Dtmp = nullptr;
+        if (!d_dev) {
+            Dtmp = dalloc<double>((size_t)Rc * nt);
+            h2d(Dtmp, Dg, (size_t)Rc * nt * 8, s);
+            Dg = Dtmp;
+        }
+        std::unique_ptr<double, void (*)(double*)> dguard(Dtmp, [](double* q) { dfree(q); });
+        // b_r = P^T N^-1 d_r in FP32 for all columns in one batched Toeplitz launch (it seeds
+        // the first inner solve and scales the residual; the FP64 residuals come from the
+        // data, residual64)
+        launch_toeplitz_any<float>(P, P.tz32, nullptr, Dg, nullptr, Rc, (int64_t)nt, bt.tod, (int64_t)nt, nullptr, s);
+        launch_batch_scatter(P, bt.tod, bt.z, Rc, nullptr, s);
+        launch_convert_f32_to_f64(bt.z, bt.b64, (int64_t)Rc * n, s);
         for (int r = 0; r < Rc; ++r) {
-            const double* dr = D + (size_t)(c0 + r) * nt;
-            if (!d_dev) {
-                h2d(P.dbuf, dr, nt * 8, s);
-                dr = P.dbuf;
-            }
-            launch_toeplitz<double>(P, P.tz64, dr, nullptr, P.tod64, nullptr, s);
-            launch_scatter<double>(P, P.tod64, bt.b64 + (size_t)r * n, nullptr, s);
             bb[(size_t)r] = dot64(P, bt.b64 + (size_t)r * n, bt.b64 + (size_t)r * n);
             rr[(size_t)r] = bb[(size_t)r];
         }
@@ -1661,8 +1669,7 @@ static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_op
                 fp64[(size_t)r] += 1;
                 double* x64 = bt.x64 + (size_t)r * n;
                 launch_axpy_host(x64, bt.x + (size_t)r * n, nrm[(size_t)r], (int64_t)n, s);
-                apply_A<double>(P, x64, P.ax64, nullptr);
-                launch_sub(bt.b64 + (size_t)r * n, P.ax64, bt.r64 + (size_t)r * n, P.n, s);
+                residual64(P, Dg + (size_t)r * nt, x64, bt.r64 + (size_t)r * n);
                 rr[(size_t)r] = dot64(P, bt.r64 + (size_t)r * n, bt.r64 + (size_t)r * n);
             }
             total += mx;

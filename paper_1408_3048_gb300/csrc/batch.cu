@@ -342,7 +342,9 @@ __device__ void batch_totals(const double* part, int stride, int slot0, int coun
 }
 
 // Block partial of sum_i a_r[i] b_r[i] for every RHS r, i over this block's elements:
-// exact products accumulated as FP32 pairs, stored as a pair in the slot.
+// exact products accumulated as FP32 pairs, stored as a pair in the slot.  Warp w owns
+// the RHS w, w + nw, ...; each lane issues a group of 8 loads before accumulating them in
+// element order (the same order as one at a time).
 __device__ void batch_dots(const float* A_, const float* B_, int64_t n, int64_t e0, int64_t e1, int R,
                            double* part_row, const unsigned char* active) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -351,7 +353,18 @@ __device__ void batch_dots(const float* A_, const float* B_, int64_t n, int64_t 
         if (active[r]) {
             const float* a = A_ + (size_t)r * n;
             const float* b = B_ + (size_t)r * n;
-            for (int64_t i = e0 + l; i < e1; i += 32) acc.add(a[i], b[i]);
+            for (int64_t base = e0 + l; base < e1; base += 32 * 8) {
+                float va[8], vb[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int64_t i = base + 32 * t;
+                    va[t] = i < e1 ? a[i] : 0.f;
+                    vb[t] = i < e1 ? b[i] : 0.f;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (base + 32 * t < e1) acc.add(va[t], vb[t]);
+            }
         }
         float hi = acc.hi, lo = acc.lo;
 #pragma unroll
@@ -364,11 +377,17 @@ __device__ void batch_dots(const float* A_, const float* B_, int64_t n, int64_t 
     }
 }
 
+// z_r = M_BD r_r for every running RHS on this block's pixels; (RHS, pixel) pairs are
+// spread over the threads so that all loads of a block are in flight together.
 template <int NC>
-__device__ void batch_bd(const BatchPcgArgs& a, int p0, int p1, int r) {
-    const float* rv = a.r + (size_t)r * a.n;
-    float* zv = a.z + (size_t)r * a.n;
-    for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+__device__ void batch_bd_all(const BatchPcgArgs& a, int p0, int p1, int R, const unsigned char* active) {
+    const int np = p1 - p0;
+    for (int idx = threadIdx.x; idx < R * np; idx += blockDim.x) {
+        const int r = idx / np;
+        if (!active[r]) continue;
+        const int q = p0 + (idx - r * np);
+        const float* rv = a.r + (size_t)r * a.n;
+        float* zv = a.z + (size_t)r * a.n;
         if constexpr (NC == 1) {
             zv[q] = a.bd[q] * rv[q];
         } else {
@@ -395,6 +414,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     __shared__ double sh[BATCH_RMAX];
     __shared__ double sh2[BATCH_RMAX];
     __shared__ unsigned char act[BATCH_RMAX];
+    __shared__ float coef[BATCH_RMAX];
     if (*(volatile int*)&a.flags[F_DONE]) return;
     int p0, p1;
     block_range(a.npix, p0, p1);
@@ -404,16 +424,18 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     for (int r = threadIdx.x; r < R; r += blockDim.x) act[r] = a.state[r] == 0;
     __syncthreads();
     if (which == 0) {
-        for (int r = 0; r < R; ++r) {
-            float* x = a.x + (size_t)r * a.n;
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) x[i] = 0.f;
-            batch_bd<NC>(a, p0, p1, r);
+        // (every RHS is running here: the host resets the states before this launch)
+        const int len = (int)(e1 - e0);   // one block's elements: far below 2^31 / R
+        for (int idx = threadIdx.x; idx < R * len; idx += blockDim.x) {
+            const int r = idx / len;
+            a.x[(size_t)r * a.n + e0 + (idx - r * len)] = 0.f;
         }
+        batch_bd_all<NC>(a, p0, p1, R, act);
         __syncthreads();
-        for (int r = 0; r < R; ++r) {
-            const float* z = a.z + (size_t)r * a.n;
-            float* p = a.p + (size_t)r * a.n;
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) p[i] = z[i];
+        for (int idx = threadIdx.x; idx < R * len; idx += blockDim.x) {
+            const int r = idx / len;
+            const size_t o = (size_t)r * a.n + e0 + (idx - r * len);
+            a.p[o] = a.z[o];
         }
         batch_dots(a.r, a.r, a.n, e0, e1, R, prow, act);
         batch_dots(a.r, a.z, a.n, e0, e1, R, prow + BATCH_RMAX, act);
@@ -436,17 +458,19 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     batch_dots(a.p, a.q, a.n, e0, e1, R, prow, act);
     if (!grid_sync(a.bar, a.flags)) return;
     batch_totals(a.partial, BATCH_PSTRIDE, 0, R, sh);
-    // phase B: x += alpha p, r -= alpha q (active RHS only); r^T r
-    for (int r = 0; r < R; ++r) {
-        if (!act[r]) continue;
-        const float al = (float)(a.rho[r] / sh[r]);
-        float* x = a.x + (size_t)r * a.n;
-        float* rv = a.r + (size_t)r * a.n;
-        const float* p = a.p + (size_t)r * a.n;
-        const float* q = a.q + (size_t)r * a.n;
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-            x[i] += al * p[i];
-            rv[i] -= al * q[i];
+    // phase B: x += alpha p, r -= alpha q (active RHS only; (RHS, element) pairs spread
+    // over the threads); r^T r
+    for (int r = threadIdx.x; r < R; r += blockDim.x) coef[r] = act[r] ? (float)(a.rho[r] / sh[r]) : 0.f;
+    __syncthreads();
+    {
+        const int len = (int)(e1 - e0);
+        for (int idx = threadIdx.x; idx < R * len; idx += blockDim.x) {
+            const int r = idx / len;
+            if (!act[r]) continue;
+            const size_t o = (size_t)r * a.n + e0 + (idx - r * len);
+            const float al = coef[r];
+            a.x[o] += al * a.p[o];
+            a.r[o] -= al * a.q[o];
         }
     }
     __syncthreads();
@@ -473,20 +497,23 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     }
     __syncthreads();
     // phase C: z = M_BD r, r^T z for the RHS still running
-    for (int r = 0; r < R; ++r)
-        if (act[r]) batch_bd<NC>(a, p0, p1, r);
+    batch_bd_all<NC>(a, p0, p1, R, act);
     __syncthreads();
     batch_dots(a.r, a.z, a.n, e0, e1, R, prow + 2 * BATCH_RMAX, act);
     if (!grid_sync(a.bar, a.flags)) return;
     batch_totals(a.partial, BATCH_PSTRIDE, 2 * BATCH_RMAX, R, sh);
     bool any = false;
-    for (int r = 0; r < R; ++r) {
-        if (!act[r]) continue;
-        any = true;
-        const float be = (float)(sh[r] / a.rho[r]);
-        float* p = a.p + (size_t)r * a.n;
-        const float* z = a.z + (size_t)r * a.n;
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) p[i] = z[i] + be * p[i];
+    for (int r = 0; r < R; ++r) any = any || act[r];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) coef[r] = act[r] ? (float)(sh[r] / a.rho[r]) : 0.f;
+    __syncthreads();
+    {
+        const int len = (int)(e1 - e0);
+        for (int idx = threadIdx.x; idx < R * len; idx += blockDim.x) {
+            const int r = idx / len;
+            if (!act[r]) continue;
+            const size_t o = (size_t)r * a.n + e0 + (idx - r * len);
+            a.p[o] = a.z[o] + coef[r] * a.p[o];
+        }
     }
     // every block has read rho and F_ITER above; block 0 publishes the new values after a
     // final barrier so no block can see them early
