@@ -325,6 +325,24 @@ mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int k
 mm_status mm_profile(mm_plan_t plan, int enable);
 mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
 
+/*
+ * Residual history of the last PCG solve on this plan (mm_solve, mm_solve_ex, the adjoint
+ * solve of mm_grad, or the block-Jacobi solve inside an a posteriori mm_build_coarse*):
+ * the relative recursive residual ||r_j||_2 / ||b||_2 after each product A p, the
+ * convergence measure Sec. 5.1 plots.  Entry 0 is the start (1 for x_0 = 0; the A-DEF2
+ * start of App. B is not counted: its entry 0 is also 1), entry j the residual after the
+ * j-th product.  MM_SOLVE_MIXED concatenates its inner FP32 solves: their recursive
+ * residuals, relative to the inner right-hand side r / ||r||, are scaled by the FP64
+ * ||r|| / ||b|| of the refinement step they belong to, so each inner run starts at the
+ * true residual and the entries estimate the true residual to FP32 accuracy.
+ *   max        capacity of rel_resid (entries written: min(max, *count)).
+ *   rel_resid  host double[max], may be NULL.
+ *   count      host, may be NULL: number of entries, stats.iters + 1 (0 before any
+ *              solve; fewer when a solve ran past 2^20 products, which are not kept).
+ * Errors: MM_ERR_ARG for max < 0.  The batched solver keeps no history.
+ */
+mm_status mm_solve_history(mm_plan_t plan, int32_t max, double* rel_resid, int32_t* count);
+
 /* Options of mm_solve_ex.  Zero-initialise and set what you need; 0 selects the default. */
 typedef struct {
     double tol;             /* relative residual target (required, >= 0)                  */

@@ -148,6 +148,13 @@ struct PlanHolder : Plan {
     bool autotune = false;      // measured block / batched-kernel choice (mm_opts.autotune)
     float tuned_ms64[16] = {};  // timed candidates by logn - 8 (0: not tried)
     float tuned_ms32[16] = {};
+    // Residual history of the last solve: PCG run j wrote r^T r of its steps to
+    // pcg.hist_rr[off ..]; relative residual = sqrt(rr / bb) * scale (mm_solve_history).
+    struct HistRun {
+        int off, iters;
+        double bb, scale;
+    };
+    std::vector<HistRun> hist_runs;
 };
 
 static void free_tz(ToeplitzDev& t) {
@@ -630,12 +637,26 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
 }
 
 // Runs PCG on the right-hand side already stored in pcg.r (as T); solution in pcg.x.
+// The scalar history of this run goes to the history arrays from entry hist_off on.
 template <typename T>
-static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstore, int maxstore) {
+static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstore, int maxstore,
+                          int hist_off = 0) {
     cudaStream_t s = P.stream;
     PcgArgs<T> a = pcg_args<T>(P, cm != 0, maxit);
     a.zstore = zstore;
     a.maxstore = maxstore;
+    if (a.hist_rr != nullptr) {
+        if (hist_off >= a.maxhist) {
+            a.hist_alpha = a.hist_beta = a.hist_rz = a.hist_rr = nullptr;
+            a.maxhist = 0;
+        } else {
+            a.hist_alpha += hist_off;
+            a.hist_beta += hist_off;
+            a.hist_rz += hist_off;
+            a.hist_rr += hist_off;
+            a.maxhist -= hist_off;
+        }
+    }
     P.h_scal[0] = tol * tol;
     h2d(P.pcg.scal + SC_TOL2, P.h_scal, 8, s);
     const int nb = P.pcg.nblocks;
@@ -684,6 +705,8 @@ static double dot64(PlanHolder& P, const double* a, const double* b) {
 }
 
 // ------------------------------------------------------------------- coarse space
+constexpr int MAX_HISTORY = 1 << 20;   // residual-history entries kept for a solve
+
 static void ensure_history(PlanHolder& P, int m) {
     PcgDev& g = P.pcg;
     if (g.maxhist >= m + 1) return;
@@ -1016,12 +1039,14 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
         launch_convert_f64_to_f32(bsrc, static_cast<float*>(P.pcg.r), P.n, s);
     }
     ensure_history(P, maxit);
+    P.hist_runs.clear();
     T* zstore = static_cast<T*>(dmalloc((size_t)(maxit + 1) * P.n * sizeof(T)));
     double* Y = nullptr;
     double* Y2 = nullptr;
     double* C = nullptr;
     try {
         const PcgOutcome o = run_pcg<T>(P, 0, tol, maxit, zstore, maxit + 1);
+        P.hist_runs.assign(1, PlanHolder::HistRun{0, o.iters, o.bb, 1.0});   // the last PCG run
         if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED)
             throw Error{(mm_status)o.status, "first solve of the coarse construction failed"};
         const int m = o.iters;   // alphas 0..m-1, betas 0..m-2, z_0..z_{m-1}
@@ -1142,9 +1167,14 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
     int status = MM_OK;
     const double bb = dot64(P, P.b64, P.b64);
     const double bn = std::sqrt(bb);
+    // residual history: each PCG run of this solve writes from its own offset, one spare
+    // entry after the previous run's last (at most maxit steps and max_outer runs in all)
+    ensure_history(P, (int)std::min<int64_t>((int64_t)maxit + max_outer + 1, MAX_HISTORY));
+    P.hist_runs.clear();
     if (so.solver == MM_SOLVE_FP64) {
         check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
-        const PcgOutcome o = run_pcg<double>(P, cm, tol, maxit, nullptr, 0);
+        const PcgOutcome o = run_pcg<double>(P, cm, tol, maxit, nullptr, 0, 0);
+        P.hist_runs.push_back({0, o.iters, o.bb, 1.0});
         if (o.status != MM_OK) status = o.status;
         check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
         stats.iters = o.iters;
@@ -1179,7 +1209,9 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
         double tol_in = 0.5 * tol * bn / std::sqrt(rr);
         tol_in = std::min(0.5, std::max(tol_in, inner_min));
         if (outer == 0 && so.first_inner_tol > 0.0) tol_in = so.first_inner_tol;
-        const PcgOutcome o = run_pcg<float>(P, cm, tol_in, maxit - total, nullptr, 0);
+        const PcgOutcome o = run_pcg<float>(P, cm, tol_in, maxit - total, nullptr, 0, total + outer);
+        // the inner right-hand side is r / ||r||: its residuals scale by ||r|| / ||b||
+        P.hist_runs.push_back({total + outer, o.iters, o.bb, std::sqrt(rr) / bn});
         if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED) {
             status = o.status;
             break;
@@ -1757,6 +1789,10 @@ mm_status mm_plan(mm_plan_t* out, const int32_t* pix, int64_t nt, int32_t npix_s
         g_last_error = "host allocation failed";
         destroy_plan(P);
         return MM_ERR_OOM;
+    } catch (const std::exception& e) {   // nothing may leave an extern "C" function
+        g_last_error = e.what();
+        destroy_plan(P);
+        return MM_ERR_ARG;
     }
 }
 
@@ -1964,6 +2000,30 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z) {
         if (P->coarse.k == 0) throw Error{MM_ERR_STATE, "no coarse space"};
         if (Z == nullptr) throw Error{MM_ERR_ARG, "null output"};
         check_cuda(cudaMemcpy(Z, P->coarse.Z64, (size_t)P->coarse.k * P->n * 8, cudaMemcpyDefault), "copy Z");
+    });
+}
+
+mm_status mm_solve_history(mm_plan_t plan, int32_t max, double* rel_resid, int32_t* count) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (max < 0) throw Error{MM_ERR_ARG, "max must be >= 0"};
+        std::vector<double> out;
+        if (!P->hist_runs.empty() && P->pcg.hist_rr != nullptr) {
+            const PlanHolder::HistRun& last = P->hist_runs.back();
+            const int len = std::min(last.off + last.iters + 1, P->pcg.maxhist);
+            std::vector<double> h((size_t)std::max(len, 0));
+            d2h(h.data(), P->pcg.hist_rr, h.size() * 8, P->stream);
+            sync(P->stream);
+            // entry 0 of the first run, then steps 1..iters of every run
+            for (size_t r = 0; r < P->hist_runs.size(); ++r) {
+                const PlanHolder::HistRun& run = P->hist_runs[r];
+                for (int j = r == 0 ? 0 : 1; j <= run.iters && run.off + j < len; ++j)
+                    out.push_back(run.bb == 0.0 ? 0.0 : std::sqrt(h[(size_t)(run.off + j)] / run.bb) * run.scale);
+            }
+        }
+        if (count) *count = (int32_t)out.size();
+        if (rel_resid) std::copy(out.begin(), out.begin() + (std::ptrdiff_t)std::min<size_t>((size_t)max, out.size()),
+                                 rel_resid);
     });
 }
 

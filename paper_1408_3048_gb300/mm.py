@@ -31,7 +31,7 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
            "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
-           "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi"]
+           "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi", "mm_solve_history"]
 
 
 class mm_psd(ctypes.Structure):
@@ -101,6 +101,7 @@ _SIGS = {
     "mm_batch_config": (I32, [P, ctypes.c_int32, P, P, P]),
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
+    "mm_solve_history": (I32, [P, I32, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
     "mm_destroy": (None, [P]),
     "mm_version": (ctypes.c_char_p, []),
@@ -280,6 +281,15 @@ def mm_profile_read(plan):
     n = np.zeros(8, dtype=np.int64)
     _check(lib().mm_profile_read(plan, ms.ctypes.data, n.ctypes.data), plan)
     return ms, n
+
+
+def mm_solve_history(plan):
+    """||r_j|| / ||b|| after each product A p of the last solve (numpy float64)."""
+    cnt = ctypes.c_int32()
+    _check(lib().mm_solve_history(plan, 0, None, ctypes.byref(cnt)), plan)
+    h = np.zeros(max(cnt.value, 1), dtype=np.float64)
+    _check(lib().mm_solve_history(plan, cnt.value, h.ctypes.data, ctypes.byref(cnt)), plan)
+    return h[: cnt.value]
 
 
 def mm_solve_ex(plan, d, opts, m, raise_on_error=True):
@@ -506,6 +516,10 @@ class Plan:
 
     def profile(self, enable=True):
         mm_profile(self.handle, enable)
+
+    def solve_history(self):
+        """Relative recursive residual after each A p of the last solve (Sec. 5.1)."""
+        return mm_solve_history(self.handle)
 
     def profile_read(self):
         """{stage: (total ms, launches)} per kernel and precision."""

@@ -38,6 +38,8 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert L.mm_plan(ctypes.byref(h), None, 0, 0, None, None, 0, None, None, 0, None) == mm.MM_ERR_ARG
     assert h.value is None
     assert L.mm_apply_A(None, 0, None, None) == mm.MM_ERR_ARG
+    n = ctypes.c_int32(-1)
+    assert L.mm_solve_history(None, 0, None, ctypes.byref(n)) == mm.MM_ERR_ARG
     L.mm_destroy(None)
 
 

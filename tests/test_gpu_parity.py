@@ -163,6 +163,51 @@ def test_solve_mixed_reaches_tolerance(case):
     assert st["rel_resid"] == pytest.approx(rel, rel=1e-5, abs=1e-12)
 
 
+def test_residual_history(case):
+    """||r_j|| / ||b|| per step (the Sec. 5.1 convergence measure) against the oracle's
+    PCG on the same system: equal start, the stopping rule on the last two entries, and
+    the oracle's values wherever the two runs take the same number of steps."""
+    name, scan, pr, plan = case
+    d = _data(scan)
+    tol = 1e-6
+    ref = pcg(pr.A, oprec.BlockJacobi(pr).apply, pr.rhs(d), tol, 3000)
+    m, st, status = plan.solve(_cuda(d), tol=tol, maxit=3000)
+    h = plan.solve_history()
+    assert status == mm.MM_OK and h.shape == (st["iters"] + 1,)
+    assert h[0] == 1.0 and h[-1] <= tol * (1 + 1e-12) and h[-2] > tol * (1 - 1e-12)
+    assert h[-1] == pytest.approx(st["rel_resid_rec"], rel=1e-12)
+    ro = np.asarray(ref.rel_hist)
+    j = min(10, len(h), len(ro))
+    np.testing.assert_allclose(h[:j], ro[:j], rtol=1e-6)
+    if len(h) == len(ro):
+        assert np.max(np.abs(np.log10(h / ro))) <= 0.1
+    # mixed: inner FP32 runs concatenated, each scaled to the outer FP64 residual
+    m, st, status = plan.solve(_cuda(d), tol=tol, maxit=5000, solver=mm.MM_SOLVE_MIXED)
+    h = plan.solve_history()
+    assert status == mm.MM_OK and h.shape == (st["iters"] + 1,)
+    assert h[0] == 1.0 and np.all(np.isfinite(h)) and h[-1] <= tol
+    j = min(5, len(h), len(ro))
+    np.testing.assert_allclose(h[:j], ro[:j], rtol=1e-2)   # FP32 operators, same iteration
+
+
+def test_nan_data_is_reported():
+    """A NaN sample reaches b and the first reduction: both solvers stop with
+    MM_ERR_NUMERIC, and the plan solves the repaired data afterwards."""
+    scan = tiny_scan(ncomp=3)
+    plan = _plan(scan)
+    d = _data(scan)
+    bad = slice(len(d) // 2, len(d) // 2 + 8)
+    d[bad] = np.nan
+    for solver in (mm.MM_SOLVE_FP64, mm.MM_SOLVE_MIXED):
+        m, st, status = plan.solve(_cuda(d), tol=1e-6, maxit=100, solver=solver, raise_on_error=False)
+        assert status == mm.MM_ERR_NUMERIC, (solver, status)
+        assert st["converged"] == 0
+    d[bad] = 0.0
+    m, st, status = plan.solve(_cuda(d), tol=1e-6, maxit=1000)
+    assert status == mm.MM_OK and np.all(np.isfinite(plan.solve_history()))
+    plan.close()
+
+
 def test_two_level(case):
     name, scan, pr, plan = case
     k = 8 if pr.n < 2000 else 16
