@@ -15,6 +15,12 @@ from oracle import adjoint as oadj
 from oracle import noise as onoise
 from oracle import pointing as opoint
 
+try:
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+except ImportError:   # the deterministic cases below still run
+    given = None
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "paper_1408_3048_gb300", "csrc")
 CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
@@ -106,6 +112,20 @@ def test_rows_match_the_oracle(host, sigma, fknee, alpha, L, lam, window):
     ref = onoise.toeplitz_row(sigma, fknee, alpha, L, 100.0, lam, window)
     assert t.shape == ref.shape
     assert np.abs(t - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+if given is not None:
+    @settings(max_examples=60, deadline=None)
+    @given(st.floats(0.3, 3.0), st.floats(0.0, 3.0), st.floats(0.5, 3.0), st.integers(3, 16), st.data())
+    def test_random_rows_match_the_oracle(host, sigma, fknee, alpha, logL, data):
+        L = 2 ** logL
+        lam = data.draw(st.integers(0, min(L // 2 - 1, 2000)))
+        window = data.draw(st.sampled_from([onoise.WINDOW_GAUSS, onoise.WINDOW_RECT]))
+        t = host(f"row {sigma!r} {fknee!r} {alpha!r} {L} 100.0 {lam} {window}")
+        ref = onoise.toeplitz_row(sigma, fknee, alpha, L, 100.0, lam, window)
+        assert np.abs(t - ref).max() <= 1e-13 * np.abs(ref).max()
+        pos = bool(host(f"sympos {len(t)} {_nums(t)}")[0])
+        assert pos == onoise.is_positive_definite(ref)
 
 
 @pytest.mark.parametrize("sigma,fknee,alpha,L,lam", [r for r in ROWS if r[1] > 0])

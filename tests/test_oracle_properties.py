@@ -1,0 +1,130 @@
+"""Property tests of the oracle on random tiny problems (hypothesis; CPU only).
+
+Random pointings (any pixel hit any number of times, unobserved and ill-conditioned
+I/Q/U pixels included), random interval partitions with lengths from 8 samples, one or
+two noise PSDs, and half bandwidths from 0 up to the shortest interval.  On each the
+algebraic facts the paper fixes must hold: P and P^T are adjoint (Eq. 2, Sec. 2), the
+matrix-free A equals the dense P^T N^-1 P (Eq. 5, 8), it is symmetric positive definite
+(Sec. 3.1), white noise makes the GLS map the hit-weighted binned map (M_BD = A^-1,
+Sec. 3.2), PCG reaches the dense solution (Eq. 3), and the two-level operator satisfies
+R A Z = 0 and M_2lvl A Z = Z (Eq. 11, 13) for any coarse basis.
+"""
+import numpy as np
+import pytest
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import HealthCheck, assume, given, settings
+from hypothesis import strategies as st
+
+from oracle import precond, toeplitz
+from oracle.pcg import dense_solve, pcg
+from oracle.system import Problem
+
+SETTINGS = settings(max_examples=50, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+
+
+@st.composite
+def problems(draw, white=False):
+    ncomp = draw(st.sampled_from([1, 3]))
+    npix = draw(st.integers(2, 12))
+    lengths = draw(st.lists(st.integers(8, 60), min_size=1, max_size=4))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    rng = np.random.default_rng(seed)
+    nt = int(sum(lengths))
+    pix = rng.integers(0, npix, size=nt)
+    weights = None
+    if ncomp == 3:
+        phi = rng.uniform(0.0, np.pi, size=nt)
+        weights = np.stack([np.cos(2 * phi), np.sin(2 * phi)], axis=1)
+    npsd = draw(st.integers(1, 2))
+    psds = [(draw(st.floats(0.5, 2.0)), 0.0 if white else draw(st.floats(0.0, 2.0)), draw(st.floats(1.0, 2.0)))
+            for _ in range(npsd)]
+    lam = draw(st.integers(0, min(lengths) - 1))
+    offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    ipsd = rng.integers(0, npsd, size=len(lengths))
+    pr = Problem(pix, npix, weights, offsets, ipsd, psds, 100.0, lam, ncomp)
+    assume(pr.n > 0)
+    return pr, rng
+
+
+@SETTINGS
+@given(problems())
+def test_operators_match_their_dense_forms(arg):
+    pr, rng = arg
+    x = rng.standard_normal(pr.n)
+    y = rng.standard_normal(pr.nt)
+    Pd = pr.dense_P()
+    Nd = toeplitz.dense_ninv(pr.offsets, pr.interval_psd, pr.rows)
+    # P and P^T are adjoint and equal their dense matrices
+    assert abs(y @ pr.P(x) - pr.PT(y) @ x) <= 1e-12 * (np.abs(y).sum() * np.abs(x).max() * 3 + 1)
+    np.testing.assert_allclose(pr.P(x), Pd @ x, rtol=1e-13, atol=1e-13)
+    # the banded N^-1 is symmetric and equals its dense block-diagonal Toeplitz form
+    assert np.array_equal(Nd, Nd.T)
+    np.testing.assert_allclose(pr.Ninv(y), Nd @ y, rtol=1e-12, atol=1e-12 * np.abs(Nd).sum(axis=1).max())
+    # A x = P^T N^-1 P x by both Toeplitz routes, symmetric positive definite
+    A = Pd.T @ Nd @ Pd
+    scale = np.abs(A).sum(axis=1).max() * np.abs(x).max()
+    np.testing.assert_allclose(pr.A(x), A @ x, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(pr.A(x, route="fft"), A @ x, rtol=0, atol=1e-9 * scale)
+    v = rng.standard_normal(pr.n)
+    assert v @ pr.A(v) > 0
+    assert abs(v @ pr.A(x) - x @ pr.A(v)) <= 1e-12 * scale * np.abs(v).sum()
+
+
+@SETTINGS
+@given(problems(white=True))
+def test_white_noise_gls_is_the_binned_map(arg):
+    pr, rng = arg
+    d = rng.standard_normal(pr.nt)
+    m = dense_solve(pr.dense_A(), pr.rhs(d))
+    # brute force: per observed pixel, sum over its samples of w w^T / sigma_t^2 m = w d / sigma_t^2
+    sig2 = np.empty(pr.nt)
+    for i in range(pr.offsets.size - 1):
+        sig2[pr.offsets[i]:pr.offsets[i + 1]] = pr.psds[pr.interval_psd[i]][0] ** 2
+    ref = np.empty(pr.n)
+    for q in range(pr.npix_obs):
+        ts = np.flatnonzero(pr.pix_c == q)
+        if pr.ncomp == 1:
+            W = np.ones((ts.size, 1))
+        else:
+            W = np.stack([np.ones(ts.size), pr.weights[ts, 0], pr.weights[ts, 1]], axis=1)
+        Bq = (W / sig2[ts, None]).T @ W
+        ref[q * pr.ncomp:(q + 1) * pr.ncomp] = np.linalg.solve(Bq, (W / sig2[ts, None]).T @ d[ts])
+    np.testing.assert_allclose(m, ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+    # M_BD is A^-1 here: PCG converges in one step
+    res = pcg(pr.A, precond.BlockJacobi(pr).apply, pr.rhs(d), 1e-8, 10)
+    assert res.converged and res.iters == 1
+
+
+@SETTINGS
+@given(problems())
+def test_pcg_reaches_the_dense_solution(arg):
+    pr, rng = arg
+    b = pr.rhs(rng.standard_normal(pr.nt))
+    assume(np.linalg.norm(b) > 0)
+    res = pcg(pr.A, precond.BlockJacobi(pr).apply, b, 1e-11, 50 * pr.n + 50)
+    assert res.converged
+    assert np.linalg.norm(b - pr.A(res.x)) <= 1e-9 * np.linalg.norm(b)
+    assert res.rel_hist[0] == 1.0 and res.rel_hist[-1] <= 1e-11
+    A = pr.dense_A()
+    m = dense_solve(A, b)
+    # forward error within the condition number times the residual
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(res.x - m) <= 1e-8 * kappa * np.linalg.norm(m) + 1e-300
+
+
+@SETTINGS
+@given(problems(), st.integers(1, 4))
+def test_two_level_identities_for_any_coarse_basis(arg, k):
+    pr, rng = arg
+    assume(pr.n > k)
+    bd = precond.BlockJacobi(pr)
+    Z = rng.standard_normal((pr.n, k))
+    tl = precond.TwoLevel(pr, bd, Z)
+    A = pr.dense_A()
+    assume(np.linalg.cond(Z.T @ A @ Z) < 1e10)
+    AZ = A @ Z
+    RAZ = np.stack([tl.deflate(AZ[:, j]) for j in range(k)], axis=1)
+    assert np.linalg.norm(RAZ) <= 1e-8 * np.linalg.norm(AZ)
+    MAZ = np.stack([tl.apply(AZ[:, j]) for j in range(k)], axis=1)
+    assert np.linalg.norm(MAZ - Z) <= 1e-8 * np.linalg.norm(Z)
