@@ -2,7 +2,7 @@
 
 Random pointings (any pixel hit any number of times, unobserved and ill-conditioned
 I/Q/U pixels included), random interval partitions with lengths from 8 samples, one or
-two noise PSDs, and half bandwidths from 0 up to the shortest interval.  On each the
+two noise PSDs, and half bandwidths from 0 up to half the shortest interval.  On each the
 algebraic facts the paper fixes must hold: P and P^T are adjoint (Eq. 2, Sec. 2), the
 matrix-free A equals the dense P^T N^-1 P (Eq. 5, 8), it is symmetric positive definite
 (Sec. 3.1), white noise makes the GLS map the hit-weighted binned map (M_BD = A^-1,
@@ -20,7 +20,7 @@ from oracle import precond, toeplitz
 from oracle.pcg import dense_solve, pcg
 from oracle.system import Problem
 
-SETTINGS = settings(max_examples=50, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+SETTINGS = settings(max_examples=50, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
 
 
 @st.composite
@@ -39,7 +39,9 @@ def problems(draw, white=False):
     npsd = draw(st.integers(1, 2))
     psds = [(draw(st.floats(0.5, 2.0)), 0.0 if white else draw(st.floats(0.0, 2.0)), draw(st.floats(1.0, 2.0)))
             for _ in range(npsd)]
-    lam = draw(st.integers(0, min(lengths) - 1))
+    # lambda <= L/2, where every row of a 1/f PSD with alpha <= 2 is positive definite;
+    # beyond, the periodic row wraps and the symbol check rejects it (from ~0.84 L on)
+    lam = draw(st.integers(0, min(lengths) // 2))
     offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
     ipsd = rng.integers(0, npsd, size=len(lengths))
     pr = Problem(pix, npix, weights, offsets, ipsd, psds, 100.0, lam, ncomp)
