@@ -14,7 +14,10 @@ tridiagonal T_m built from the CG step scalars,
     T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},   T_{j,j+1} = sqrt(beta_j)/alpha_j,
 give Ritz vectors V_m s with Lanczos vectors v_j = (-1)^j z_j / sqrt(r_j^T z_j)
 (z_j = M_BD r_j, the preconditioned CG residuals).  The selected vectors are
-orthonormalised (Euclidean QR) and columns with |R_jj| < 1e-10 max |R_jj| dropped.
+orthonormalised (Euclidean QR) and columns with |R_jj| < 1e-10 max |R_jj|, or with
+|R_jj| <= 1e-6 of the column's own norm, dropped (reading R16: the paper says nothing on
+dependent coarse columns; a part orthogonal to the kept ones below 1e-6 of the column is
+taken as dependence, the resolution of a Gram-matrix orthonormalisation).
 Reading R9: E is factored by LU with partial pivoting (as App. C does).
 
 Arnoldi route (App. A, Algorithm 1; the paper's own Z_D source): the basic Arnoldi
@@ -29,6 +32,8 @@ orthonormalisation and dropping as above.
 """
 import numpy as np
 import scipy.linalg
+
+OWN_NORM_RTOL = 1e-6   # reading R16: dependence threshold relative to a column's own norm
 
 
 class BlockJacobi:
@@ -128,7 +133,7 @@ def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
     Y = V @ S[:, :kk]
     Q, R = np.linalg.qr(Y)
     d = np.abs(np.diag(R))
-    keep = d >= drop_rtol * d.max()
+    keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
     return Q[:, keep], theta[:kk]
 
 
@@ -185,9 +190,10 @@ def arnoldi_coarse_space(W, H, k, eps_tol, drop_rtol=1e-10):
             taken[pair] = True
     if not cols:
         raise ValueError("no Ritz value below eps_tol")
-    Q, R = np.linalg.qr(np.stack(cols, axis=1))
+    Y = np.stack(cols, axis=1)
+    Q, R = np.linalg.qr(Y)
     d = np.abs(np.diag(R))
-    keep = d >= drop_rtol * d.max()
+    keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
     return Q[:, keep], np.asarray(vals)
 
 
@@ -222,9 +228,10 @@ def deflation_apriori_merged(prob, r):
 
 def independent_columns(Z, drop_rtol=1e-10):
     """Columns of Z in order, skipping each column whose component orthogonal to the
-    kept ones has norm < drop_rtol times the largest such norm kept so far (or is 0):
-    Z_S has dependent columns whenever intervals see the same hit fractions, and E =
-    Z^T A Z must be invertible (Eq. 12).  Gram-Schmidt, projected twice."""
+    kept ones has norm < drop_rtol times the largest such norm kept so far, or at most
+    OWN_NORM_RTOL times the column's own norm: Z_S has dependent columns whenever
+    intervals see the same hit fractions, and E = Z^T A Z must be invertible (Eq. 12).
+    Gram-Schmidt, projected twice."""
     Z = np.asarray(Z, dtype=np.float64)
     Q = np.zeros((Z.shape[0], 0))
     kept, maxpiv = [], 0.0
@@ -233,7 +240,7 @@ def independent_columns(Z, drop_rtol=1e-10):
         for _ in range(2):
             v -= Q @ (Q.T @ v)
         piv = np.linalg.norm(v)
-        if piv == 0.0 or piv < drop_rtol * maxpiv:
+        if piv < drop_rtol * maxpiv or piv <= OWN_NORM_RTOL * np.linalg.norm(Z[:, j]):
             continue
         kept.append(j)
         Q = np.column_stack([Q, v / piv])

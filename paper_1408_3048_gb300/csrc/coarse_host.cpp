@@ -125,9 +125,11 @@ void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e
 }
 
 // Cholesky G = R^T R (G k x k row-major, symmetric).  Column j is dropped (keep[j] =
-// false) when its pivot sqrt(g_jj - ...) is < drop_rtol * max kept pivot so far
-// (drop_rtol = 0: never drop; a non-positive pivot then fails).  Returns the inverse
-// factor Rinv restricted to kept columns as a k x kk matrix W with Y_kept = Y W.
+// false) when its pivot sqrt(g_jj - ...) is < drop_rtol * max kept pivot so far or
+// <= GRAM_RESOLUTION * sqrt(g_jj) (drop_rtol = 0: never drop; a non-positive pivot then
+// fails).  Returns the inverse factor Rinv restricted to kept columns as a k x kk matrix
+// W with Y_kept = Y W.
+static constexpr double GRAM_RESOLUTION = 1e-6;
 bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
                    std::vector<int>& kept) {
     std::vector<double> R((size_t)k * k, 0.0);   // upper, only kept rows/cols filled
@@ -146,7 +148,12 @@ bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::v
             s -= v * v;
         }
         const double piv = s > 0.0 ? std::sqrt(s) : 0.0;
-        if (drop_rtol > 0.0 && (piv < drop_rtol * maxpiv || piv == 0.0)) continue;
+        // s = G_jj - sum v^2 carries a rounding error of a few k eps G_jj, so the Gram
+        // matrix resolves the orthogonal part of column j only down to ~sqrt(k eps) of the
+        // column's norm: below GRAM_RESOLUTION of its own norm it counts as dependent
+        // (an exact duplicate would otherwise survive on the sign of that rounding).
+        const double own = std::sqrt(std::max(G[(size_t)j * k + j], 0.0));
+        if (drop_rtol > 0.0 && (piv < drop_rtol * maxpiv || piv <= GRAM_RESOLUTION * own)) continue;
         if (!(piv > 0.0)) return false;
         for (size_t a = 0; a < kept.size(); ++a) R[(size_t)kept[a] * k + j] = col[a];
         R[(size_t)j * k + j] = piv;

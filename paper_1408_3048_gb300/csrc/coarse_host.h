@@ -13,7 +13,9 @@ namespace mm {
 void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e, int k,
                       std::vector<double>& theta, std::vector<double>& S);
 
-// Cholesky of a Gram matrix with column dropping; W (k x kept) maps Y to orthonormal Y W.
+// Cholesky of a Gram matrix with column dropping (pivot < drop_rtol * largest kept pivot,
+// or <= 1e-6 of the column's own norm, the Gram matrix's resolution); W (k x kept) maps Y
+// to orthonormal Y W.
 bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
                    std::vector<int>& kept);
 
