@@ -370,12 +370,14 @@ mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts
  *
  * mm_solve_batch: solves A m_r = P^T N^-1 d_r for r < R (any R >= 1, processed 64 at a
  * time) with per-right-hand-side PCG scalars and stopping (Sec. 3.1 per column), block-
- * Jacobi preconditioner, MM_SOLVE_MIXED only: FP64 right-hand sides and refinement
- * residuals per column, batched FP32 inner PCG replayed from a captured CUDA graph when
- * the plan's stream is not the legacy default stream.  D host or device double[R][nt],
- * M host or device double[R][n], st host mm_stats[R] or NULL (ms_total is the batch time
- * divided by the columns of its group of 64).  MM_ERR_NOT_CONVERGED if any column missed
- * tol (all maps are still written).
+ * Jacobi preconditioner, MM_SOLVE_MIXED only: right-hand sides formed in one batched FP32
+ * launch (they seed the first inner solve and scale the residual), FP64 refinement
+ * residuals P^T N^-1 (d_r - P m_r) per column, batched FP32 inner PCG replayed from a
+ * captured CUDA graph when the plan's stream is not the legacy default stream.  D host or
+ * device double[R][nt], M host or device double[R][n], st host mm_stats[R] or NULL
+ * (ms_total is the batch time divided by the columns of its group of 64).
+ * MM_ERR_NUMERIC if a column's data holds NaN or Inf (that column: converged 0, rel_resid
+ * NaN), else MM_ERR_NOT_CONVERGED if any column missed tol; all maps are still written.
  */
 mm_status mm_apply_A_batch(mm_plan_t plan, int R, const float* X, float* Y);
 mm_status mm_solve_batch(mm_plan_t plan, const double* D, int R, const mm_solve_opts* opts, double* M,

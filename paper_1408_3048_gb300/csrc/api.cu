@@ -1720,13 +1720,19 @@ static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_op
             x.iters = iters[(size_t)r];
             x.outer = outer[(size_t)r];
             x.fp64_products = fp64[(size_t)r];
-            x.rel_resid = bb[(size_t)r] > 0 ? std::sqrt(rr[(size_t)r] / bb[(size_t)r]) : 0.0;
-            x.converged = x.rel_resid <= so.tol;
+            // NaN or Inf in a column's data reaches its b (and it then never runs) or its
+            // residual: reported, never taken for a converged zero map
+            const bool finite = std::isfinite(bb[(size_t)r]) && std::isfinite(rr[(size_t)r]);
+            x.rel_resid = !finite ? std::nan("")
+                                  : (bb[(size_t)r] > 0 ? std::sqrt(rr[(size_t)r] / bb[(size_t)r]) : 0.0);
+            x.converged = finite && x.rel_resid <= so.tol;
             x.ms_total = ms / Rc;
-            if (!x.converged) overall = MM_ERR_NOT_CONVERGED;
+            if (!finite) overall = MM_ERR_NUMERIC;
+            else if (!x.converged && overall == MM_OK) overall = MM_ERR_NOT_CONVERGED;
             if (st) st[c0 + r] = x;
         }
     }
+    if (overall == MM_ERR_NUMERIC) throw Error{MM_ERR_NUMERIC, "NaN or Inf in a right-hand side or residual"};
     if (overall != MM_OK) throw Error{(mm_status)overall, "some right-hand sides did not reach tol"};
 }
 

@@ -75,6 +75,25 @@ def test_batched_solve_reaches_tol_per_column(name):
     single.close()
 
 
+def test_batched_nan_column_is_reported():
+    """NaN samples in one column's data: MM_ERR_NUMERIC, that column not converged with a
+    NaN residual (never a converged zero map), the other columns still solved to tol."""
+    scan = CASES["P"]()
+    pr = oracle_problem(scan)
+    D = _data(scan, 3, 300)
+    D[1, 5000:5008] = np.nan
+    plan = _plan(scan, stream=torch.cuda.Stream())
+    M, st, status = plan.solve_batch(torch.from_numpy(D).cuda(), tol=1e-6, maxit=5000, raise_on_error=False)
+    assert status == mm.MM_ERR_NUMERIC
+    assert st[1]["converged"] == 0 and np.isnan(st[1]["rel_resid"])
+    Mh = M.cpu().numpy()
+    for r in (0, 2):
+        b = pr.rhs(D[r])
+        assert st[r]["converged"] == 1, r
+        assert np.linalg.norm(b - pr.A(Mh[r])) / np.linalg.norm(b) <= 1e-6, r
+    plan.close()
+
+
 def test_batched_solve_graph_and_direct_paths_agree_and_groups():
     scan = CASES["P"]()
     R = 70                                 # two groups of at most 64 columns
