@@ -329,9 +329,9 @@ mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
  * Residual history of the last PCG solve on this plan (mm_solve, mm_solve_ex, the adjoint
  * solve of mm_grad, or the block-Jacobi solve inside an a posteriori mm_build_coarse*):
  * the relative recursive residual ||r_j||_2 / ||b||_2 after each product A p, the
- * convergence measure Sec. 5.1 plots.  Entry 0 is the start (1 for x_0 = 0; the A-DEF2
- * start of App. B is not counted: its entry 0 is also 1), entry j the residual after the
- * j-th product.  MM_SOLVE_MIXED concatenates its inner FP32 solves: their recursive
+ * convergence measure Sec. 5.1 plots.  Entry 0 is the start (1 for x_0 = 0, 0 when
+ * b = 0; the A-DEF2 start of App. B is not counted: its entry 0 is also 1), entry j the
+ * residual after the j-th product.  MM_SOLVE_MIXED concatenates its inner FP32 solves: their recursive
  * residuals, relative to the inner right-hand side r / ||r||, are scaled by the FP64
  * ||r|| / ||b|| of the refinement step they belong to, so each inner run starts at the
  * true residual and the entries estimate the true residual to FP32 accuracy.

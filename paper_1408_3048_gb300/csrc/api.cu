@@ -150,6 +150,8 @@ struct PlanHolder : Plan {
     float tuned_ms32[16] = {};
     // Residual history of the last solve: PCG run j wrote r^T r of its steps to
     // pcg.hist_rr[off ..]; relative residual = sqrt(rr / bb) * scale (mm_solve_history).
+    // A run with bb = 0 took no step: its entry 0 is `scale` itself (the relative
+    // residual of x_0 = 0: 0 for b = 0, else 1).
     struct HistRun {
         int off, iters;
         double bb, scale;
@@ -1046,7 +1048,7 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
     double* C = nullptr;
     try {
         const PcgOutcome o = run_pcg<T>(P, 0, tol, maxit, zstore, maxit + 1);
-        P.hist_runs.assign(1, PlanHolder::HistRun{0, o.iters, o.bb, 1.0});   // the last PCG run
+        P.hist_runs.assign(1, PlanHolder::HistRun{0, o.iters, o.bb, o.bb == 0.0 ? 0.0 : 1.0});   // the last PCG run
         if (o.status != MM_OK && o.status != MM_ERR_NOT_CONVERGED)
             throw Error{(mm_status)o.status, "first solve of the coarse construction failed"};
         const int m = o.iters;   // alphas 0..m-1, betas 0..m-2, z_0..z_{m-1}
@@ -1174,7 +1176,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
     if (so.solver == MM_SOLVE_FP64) {
         check_cuda(cudaMemcpyAsync(P.pcg.r, P.b64, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
         const PcgOutcome o = run_pcg<double>(P, cm, tol, maxit, nullptr, 0, 0);
-        P.hist_runs.push_back({0, o.iters, o.bb, 1.0});
+        P.hist_runs.push_back({0, o.iters, o.bb, o.bb == 0.0 ? 0.0 : 1.0});
         if (o.status != MM_OK) status = o.status;
         check_cuda(cudaMemcpyAsync(xout, P.pcg.x, (size_t)P.n * 8, cudaMemcpyDeviceToDevice, s), "copy x");
         stats.iters = o.iters;
@@ -1228,6 +1230,8 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
             break;
         }
     }
+    // no inner solve ran (b = 0, or tol >= 1): the history is the start alone
+    if (P.hist_runs.empty()) P.hist_runs.push_back({0, 0, 0.0, bb > 0.0 ? 1.0 : 0.0});
     stats.iters = total;
     stats.outer = outer;
     stats.fp64_products = fp64;
@@ -2024,7 +2028,7 @@ mm_status mm_solve_history(mm_plan_t plan, int32_t max, double* rel_resid, int32
             for (size_t r = 0; r < P->hist_runs.size(); ++r) {
                 const PlanHolder::HistRun& run = P->hist_runs[r];
                 for (int j = r == 0 ? 0 : 1; j <= run.iters && run.off + j < len; ++j)
-                    out.push_back(run.bb == 0.0 ? 0.0 : std::sqrt(h[(size_t)(run.off + j)] / run.bb) * run.scale);
+                    out.push_back(run.bb == 0.0 ? run.scale : std::sqrt(h[(size_t)(run.off + j)] / run.bb) * run.scale);
             }
         }
         if (count) *count = (int32_t)out.size();
