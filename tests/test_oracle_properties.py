@@ -130,3 +130,61 @@ def test_two_level_identities_for_any_coarse_basis(arg, k):
     assert np.linalg.norm(RAZ) <= 1e-8 * np.linalg.norm(AZ)
     MAZ = np.stack([tl.apply(AZ[:, j]) for j in range(k)], axis=1)
     assert np.linalg.norm(MAZ - Z) <= 1e-8 * np.linalg.norm(Z)
+
+
+@st.composite
+def one_over_f_problems(draw):
+    """problems() with f_knee > 0 for every PSD (the PSD derivatives need it)."""
+    pr, rng = draw(problems())
+    psds = [(s, max(fk, 0.1), a) for (s, fk, a) in pr.psds]
+    pr = Problem(pr.pix, pr.npix_sky, pr.weights, pr.offsets, pr.interval_psd, psds, pr.fsamp, pr.lam, pr.ncomp)
+    assume(pr.n > 0)
+    return pr, rng
+
+
+@SETTINGS
+@given(one_over_f_problems())
+def test_data_gradient_is_exact_for_the_linear_map(arg):
+    """m(d) = A^-1 P^T N^-1 d is linear in d, so for L = g^T m the adjoint gradient
+    dL/dd = N^-1 P A^-1 g (A and N^-1 symmetric) gives g^T (m(d + e) - m(d)) exactly."""
+    pr, rng = arg
+    A = pr.dense_A()
+    d, e = rng.standard_normal(pr.nt), rng.standard_normal(pr.nt)
+    m0 = dense_solve(A, pr.rhs(d))
+    m1 = dense_solve(A, pr.rhs(d + e))
+    g = rng.standard_normal(pr.n)
+    from oracle import adjoint
+    dLdd, _ = adjoint.gradients(pr, d, m0, g, dense=True)
+    lhs, rhs = g @ (m1 - m0), dLdd @ e
+    assert abs(lhs - rhs) <= 1e-7 * np.linalg.cond(A) * 1e-3 * (np.abs(g) @ np.abs(m1 - m0) + abs(rhs)) + 1e-12
+
+
+@settings(max_examples=25, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(one_over_f_problems())
+def test_psd_gradient_matches_central_differences(arg):
+    """dL/d(sigma, f_knee, alpha) of L = 1/2 ||m - m_ref||^2 (the adjoint of R14) against
+    central differences of problems rebuilt with the perturbed PSD."""
+    pr, rng = arg
+    d = rng.standard_normal(pr.nt)
+    mref = rng.standard_normal(pr.n)
+
+    def loss(psds):
+        q = Problem(pr.pix, pr.npix_sky, pr.weights, pr.offsets, pr.interval_psd, psds, pr.fsamp, pr.lam, pr.ncomp)
+        m = dense_solve(q.dense_A(), q.rhs(d))
+        return 0.5 * np.sum((m - mref) ** 2), m
+
+    L0, m = loss(pr.psds)
+    from oracle import adjoint
+    _, G = adjoint.gradients(pr, d, m, m - mref, dense=True)
+    kappa = np.linalg.cond(pr.dense_A())
+    th = np.array(pr.psds, dtype=np.float64)
+    for p in range(th.shape[0]):
+        for c in range(3):
+            h = 1e-5 * th[p, c]
+            tp, tm = th.copy(), th.copy()
+            tp[p, c] += h
+            tm[p, c] -= h
+            fd = (loss([tuple(v) for v in tp])[0] - loss([tuple(v) for v in tm])[0]) / (2 * h)
+            # the difference quotient's own rounding floor: kappa eps L / h
+            floor = 10 * kappa * np.finfo(float).eps * L0 / h
+            assert fd == pytest.approx(G[p, c], rel=1e-4, abs=1e-6 * np.abs(G).max() + floor), (p, c)
