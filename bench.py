@@ -39,6 +39,8 @@ CONFIG = 2
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
 WORKLOAD = ("polarised I/Q/U raster, 256x256 patch, 16 detectors x 2^20 = 2^24 samples, 256 uneven "
             "intervals, 1/f noise fknee U[0.1,2] Hz alpha U[1,2], lambda=4096, tol 1e-6, two-level k=32")
+METRIC = "time-to-solution @1e-6 resid (2-level mixed vs FP64 BJ, 1 GPU); A·x HBM GB/s"
+L2_NOTE = "inputs larger than L2 (d 134 MB, pointing 335 MB)"
 
 
 def parse():
@@ -275,29 +277,31 @@ def oracle_time_to_solution(steps, iters, sample_iters=2):
 
 
 def oracle_iterations():
+    """(two-level iteration count, its source, the golden record) of the oracle's own solve."""
     if os.path.exists(GOLDEN):
         with open(GOLDEN) as f:
             g = json.load(f)
-        return int(g["iters_2lvl"]), "oracle two-level PCG iteration count (tests/golden/c2_oracle.json)"
-    return None, None
+        return int(g["iters_2lvl"]), "oracle two-level PCG iteration count (tests/golden/c2_oracle.json)", g
+    return None, None, None
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    iters, src = oracle_iterations()
+    iters, src, g = oracle_iterations()
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count file missing"}))
         return
     vals, info = oracle_time_to_solution(a.warmup + a.steps, iters)
     v = float(np.mean(vals[a.warmup:]))
     line = {
-        "impl": "reference", "metric": "time-to-solution @1e-6 resid, two-level (FP64 CPU oracle)",
+        "impl": "reference", "metric": METRIC,
         "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD},
+        "config": {"workload": WORKLOAD, "nt": 1 << 24, "n": int(g["n"]), "npix_obs": int(g["npix_obs"]),
+                   "k_kept": int(g["k_kept"]), "l2": L2_NOTE, "parallelism": "one host process (FP64 oracle)"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: b = P^T N^-1 d plus 2 two-level PCG iterations of the full "
                                    f"workload, extrapolated to {iters} iterations ({src})"},
@@ -472,13 +476,13 @@ def run_ours(a, rank, world, local_rank):
         t_ax = (ax[key]["toeplitz_ms"] + ax[key]["scatter_ms"]) * 1e-3
         axgbs[key] = (nt * (4 + 2 * sz) + 2 * n * sz) / t_ax / 1e9
     line = {
-        "metric": "time-to-solution @1e-6 resid (2-level mixed vs FP64 BJ, 1 GPU); A·x HBM GB/s",
+        "metric": METRIC,
         "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nt": nt, "n": n, "npix_obs": plan.npix_obs, "k_kept": kk,
                    "fft_block_f64": plan.fft_block_f64, "fft_block_f32": plan.fft_block_f32,
-                   "l2": "inputs larger than L2 (d 134 MB, pointing 335 MB)",
+                   "l2": L2_NOTE,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
         "solve": {"iters": st["iters"], "outer": st["outer"], "fp64_products": st["fp64_products"],
@@ -496,7 +500,7 @@ def run_ours(a, rank, world, local_rank):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(nt * 8), "d2h_bytes_per_step": int(n * 8)},
     }
     if world == 1 and not a.no_cpu_baseline:
-        iters, src = oracle_iterations()
+        iters, src, _ = oracle_iterations()
         if iters is None:
             iters, src = st_2f["iters"], "FP64 two-level PCG iteration count of this run"
         try:
