@@ -138,6 +138,28 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+_DT = {MM_FP64: "float64", MM_FP32: "float32"}
+
+
+def _expect(a, dtype, n, what):
+    """Reject, before the C call, an array whose element type or size differs from what the
+    call reads or writes: a plain pointer carries neither, and a float32 buffer passed for
+    doubles would be read past its end.  dtype None (an unknown precision code) leaves the
+    type to the library, which rejects the code itself."""
+    if a is None:
+        return
+    if isinstance(a, np.ndarray):
+        dt, cnt = a.dtype.name, a.size
+    elif hasattr(a, "data_ptr"):
+        dt, cnt = str(a.dtype).rsplit(".", 1)[-1], a.numel()
+    else:
+        raise TypeError(f"{what}: unsupported array type {type(a)}")
+    if dtype is not None and dt != dtype:
+        raise TypeError(f"{what}: expected {dtype} elements, got {dt}")
+    if cnt != n:
+        raise ValueError(f"{what}: expected {n} elements, got {cnt}")
+
+
 def _check(status, plan=None):
     if status != MM_OK:
         msg = lib().mm_last_error(plan).decode()
@@ -381,54 +403,64 @@ class Plan:
         return r
 
     def gather(self, x, precision=MM_FP64):
+        _expect(x, _DT.get(precision), self.n, "x")
         y = self._new(self.nt, precision)
         self._sync_in()
         mm_gather(self.handle, precision, x, y)
         return y
 
     def apply_ninv(self, y, precision=MM_FP64):
+        _expect(y, _DT.get(precision), self.nt, "y")
         z = self._new(self.nt, precision)
         self._sync_in()
         mm_apply_ninv(self.handle, precision, y, z)
         return z
 
     def scatter(self, z, precision=MM_FP64):
+        _expect(z, _DT.get(precision), self.nt, "z")
         w = self._new(self.n, precision)
         self._sync_in()
         mm_scatter(self.handle, precision, z, w)
         return w
 
     def apply_A(self, x, precision=MM_FP64, out=None):
+        _expect(x, _DT.get(precision), self.n, "x")
+        _expect(out, _DT.get(precision), self.n, "out")
         y = self._new(self.n, precision) if out is None else out
         self._sync_in()
         mm_apply_A(self.handle, precision, x, y)
         return y
 
     def rhs(self, d):
+        _expect(d, "float64", self.nt, "d")
         b = self._new(self.n, MM_FP64)
         self._sync_in()
         mm_rhs(self.handle, d, b)
         return b
 
     def precond(self, r, kind=MM_PREC_BD, precision=MM_FP64):
+        _expect(r, _DT.get(precision), self.n, "r")
         z = self._new(self.n, precision)
         self._sync_in()
         mm_precond(self.handle, kind, precision, r, z)
         return z
 
     def build_coarse(self, k, precision=MM_FP64, bprime=None, tol=1e-6, maxit=1000):
+        _expect(bprime, "float64", self.n, "bprime")
         self._sync_in()
         mm_build_coarse(self.handle, k, precision, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
 
     def build_coarse_eps(self, eps_tol, kmax=64, precision=MM_FP64, bprime=None, tol=1e-6, maxit=1000):
         """A posteriori coarse space from the Ritz pairs below eps_tol (at most kmax)."""
+        _expect(bprime, "float64", self.n, "bprime")
         self._sync_in()
         mm_build_coarse_eps(self.handle, kmax, eps_tol, precision, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
 
     def build_coarse_arnoldi(self, eps_tol, kmax=64, bprime=None, tol=1e-6, maxit=1000):
         """A posteriori coarse space from Arnoldi on M_BD A (Algorithm 1); returns (k, values)."""
+        _expect(bprime, "float64", self.n, "bprime")
         self._sync_in()
         mm_build_coarse_arnoldi(self.handle, kmax, eps_tol, bprime, tol, maxit)
         return mm_coarse_info(self.handle)
@@ -455,6 +487,8 @@ class Plan:
     def solve(self, d, tol=1e-6, maxit=1000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, out=None,
               raise_on_error=True, **extra):
         """extra: max_outer, inner_tol_min, first_inner_tol (mm_solve_opts)."""
+        _expect(d, "float64", self.nt, "d")
+        _expect(out, "float64", self.n, "out")
         m = self._new(self.n, MM_FP64) if out is None else out
         if extra:
             o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver,
@@ -471,6 +505,9 @@ class Plan:
     def grad(self, d, m, g, tol=1e-10, maxit=10000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, want_d=True,
              want_psd=True):
         """(dL/dd [nt] tensor or None, dL/dtheta [npsd, 3] numpy or None, stats) for g = dL/dm."""
+        _expect(d, "float64", self.nt, "d")
+        _expect(m, "float64", self.n, "m")
+        _expect(g, "float64", self.n, "g")
         o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver)
         dd = self._new(self.nt, MM_FP64) if want_d else None
         dp = np.zeros((self.npsd, 3), dtype=np.float64) if want_psd else None
@@ -491,6 +528,8 @@ class Plan:
     def apply_A_batch(self, X, out=None):
         """Y[r] = A X[r] in FP32 for a float32 cuda tensor X [R, n] (R <= 64)."""
         R = X.shape[0]
+        _expect(X, "float32", R * self.n, "X")
+        _expect(out, "float32", R * self.n, "out")
         Y = self._torch.empty((R, self.n), dtype=self._torch.float32, device="cuda") if out is None else out
         self._sync_in()
         mm_apply_A_batch(self.handle, R, X, Y)
@@ -499,6 +538,8 @@ class Plan:
     def solve_batch(self, D, tol=1e-6, maxit=5000, out=None, raise_on_error=True, **extra):
         """Maps for D [R, nt] float64 (mixed precision, block-Jacobi); returns (M, stats, status)."""
         R = D.shape[0]
+        _expect(D, "float64", R * self.nt, "D")
+        _expect(out, "float64", R * self.n, "out")
         M = self._torch.empty((R, self.n), dtype=self._torch.float64, device="cuda") if out is None else out
         o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=MM_PREC_BD, solver=MM_SOLVE_MIXED,
                           max_outer=int(extra.get("max_outer", 0)),

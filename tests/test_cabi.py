@@ -3,6 +3,9 @@ import ctypes
 import os
 import re
 
+import numpy as np
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -46,7 +49,6 @@ def test_null_arguments_are_rejected_without_a_gpu():
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     # no CPU fallback: without libmm.so every entry point raises instead of computing
     from paper_1408_3048_gb300 import mm
-    import pytest
     monkeypatch.setattr(mm, "LIBPATH", str(tmp_path / "absent" / "libmm.so"))
     monkeypatch.setattr(mm, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
@@ -78,3 +80,36 @@ def test_invalid_plans_are_rejected_on_the_host():
     assert plan(ncomp=2) == mm.MM_ERR_ARG
     assert plan(lam=50) == mm.MM_ERR_ARG
     assert plan(off_=np.array([0, 60, 50, 100], dtype=np.int64)) == mm.MM_ERR_ARG
+
+
+def test_binding_rejects_mistyped_or_missized_arrays_before_any_call():
+    # plain pointers carry no type or size: the binding checks both against the plan before
+    # the C call (a float32 buffer passed for doubles would be read past its end).  A Plan
+    # shell without a library handle shows that nothing reaches the library or the GPU.
+    torch = pytest.importorskip("torch")
+    from paper_1408_3048_gb300 import mm
+    p = mm.Plan.__new__(mm.Plan)
+    p._torch, p.handle, p.n, p.nt, p.npsd = torch, None, 12, 40, 1
+    f64, f32 = torch.float64, torch.float32
+    cases = [
+        (lambda: p.solve(torch.zeros(40, dtype=f32)), TypeError),
+        (lambda: p.solve(torch.zeros(39, dtype=f64)), ValueError),
+        (lambda: p.solve(torch.zeros(40, dtype=f64), out=torch.zeros(12, dtype=f32)), TypeError),
+        (lambda: p.rhs(np.zeros(40, dtype=np.float32)), TypeError),
+        (lambda: p.apply_A(torch.zeros(12, dtype=f64), mm.MM_FP32), TypeError),
+        (lambda: p.apply_A(torch.zeros(13, dtype=f64)), ValueError),
+        (lambda: p.gather(torch.zeros(40, dtype=f64)), ValueError),
+        (lambda: p.apply_ninv(torch.zeros(40, dtype=f32)), TypeError),
+        (lambda: p.scatter(torch.zeros(12, dtype=f64)), ValueError),
+        (lambda: p.precond(torch.zeros(12, dtype=f32), mm.MM_PREC_BD, mm.MM_FP64), TypeError),
+        (lambda: p.build_coarse(4, bprime=torch.zeros(12, dtype=f32)), TypeError),
+        (lambda: p.grad(torch.zeros(40, dtype=f64), torch.zeros(12, dtype=f64), torch.zeros(11, dtype=f64)),
+         ValueError),
+        (lambda: p.apply_A_batch(torch.zeros(2, 12, dtype=f64)), TypeError),
+        (lambda: p.apply_A_batch(torch.zeros(12, dtype=f32)), ValueError),      # 1-D: not [R, n]
+        (lambda: p.solve_batch(torch.zeros(3, 41, dtype=f64)), ValueError),
+        (lambda: p.solve(object()), TypeError),
+    ]
+    for call, exc in cases:
+        with pytest.raises(exc, match="expected|unsupported array type"):
+            call()
