@@ -259,7 +259,8 @@ mm_status mm_build_coarse_arnoldi(mm_plan_t plan, int kmax, double eps_tol, cons
  * Install a given coarse basis Z (host or device double[k * n], column j at Z[j*n ..]):
  * AZ = A Z, E = Z^T A Z, E^-1 as for mm_build_coarse -- to reuse a basis saved from an
  * earlier plan of the same pointing (mm_coarse_vectors) without its construction solve.
- * The columns must be linearly independent (MM_ERR_NOT_SPD otherwise).  1 <= k <= 64.
+ * The columns must be linearly independent (MM_ERR_NOT_SPD otherwise) and finite
+ * (MM_ERR_NUMERIC otherwise); the previous coarse space then stays.  1 <= k <= 64.
  * The paper has no counterpart beyond reusing a coarse space across solves.
  */
 mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k);

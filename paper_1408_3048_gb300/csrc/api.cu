@@ -758,6 +758,8 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
         cd.AZ64 = dalloc<double>((size_t)k * P.n);
         for (int j = 0; j < k; ++j) apply_A<double>(P, cd.Z64 + (size_t)j * P.n, cd.AZ64 + (size_t)j * P.n, nullptr);
         std::vector<double> E = gram_host(P, cd.Z64, k, cd.AZ64, k);
+        for (double v : E)
+            if (!std::isfinite(v)) throw Error{MM_ERR_NUMERIC, "coarse vectors hold NaN or Inf"};
         for (int i = 0; i < k; ++i)
             for (int j = 0; j < i; ++j) {
                 const double v = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
