@@ -1,5 +1,4 @@
 """Small seeded problems shared by the tests (inputs only; no method arithmetic)."""
-import numpy as np
 
 from paper_1408_3048_gb300 import synth
 

@@ -11,7 +11,6 @@ torch = pytest.importorskip("torch")
 
 from oracle import adjoint as oadj
 from oracle import precond as oprec
-from oracle.pcg import dense_solve, pcg
 from paper_1408_3048_gb300 import mm, synth
 from problems import oracle_problem, tiny_scan
 

@@ -1,6 +1,5 @@
 """Pins of the oracle's noise model (Eq. 19, App. D / Eq. 28) -- CPU only."""
 import numpy as np
-import pytest
 
 from oracle import noise
 

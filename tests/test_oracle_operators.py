@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle import noise, pointing, toeplitz
+from oracle import pointing, toeplitz
 from oracle.pcg import pcg, dense_solve
 from oracle.precond import BlockJacobi
 from paper_1408_3048_gb300 import synth
