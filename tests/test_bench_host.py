@@ -1,0 +1,71 @@
+"""Host logic of bench.py on the CPU: the DRAM traffic of a kernel is taken from a recorded
+ncu capture only while the kernel's sources hash to the recorded value, and the roofline's
+algorithmic bytes per launch follow the per-sample figures stated for each kernel
+(pixel index, weights, time-domain value per sample; the map once)."""
+import hashlib
+import os
+import shutil
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1408_3048_gb300", "csrc")
+
+
+def _tree(tmp_path, kernel):
+    csrc = tmp_path / "paper_1408_3048_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    h = hashlib.sha256()
+    for f in bench.KERNEL_SOURCES[kernel]:
+        shutil.copy(os.path.join(CSRC, f), csrc / f)
+        h.update((csrc / f).read_bytes())
+    (tmp_path / "profiles").mkdir()
+    return csrc, h.hexdigest()
+
+
+def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc, digest = _tree(tmp_path, "toeplitz_f32")
+    prof = tmp_path / "profiles" / "toeplitz_f32_case.md"
+    assert bench.recorded_traffic("toeplitz_f32") == (None, "no ncu capture recorded")
+    prof.write_text("notes\ntraffic: toeplitz_f32 dram_bytes_per_launch=12345 source_sha256=%s\n" % digest)
+    assert bench.recorded_traffic("toeplitz_f32") == (12345, os.path.join("profiles", "toeplitz_f32_case.md"))
+    # a changed kernel source makes the record stale: no traffic figure is reported
+    with open(csrc / "toeplitz_f32.cu", "a") as f:
+        f.write("\n// changed\n")
+    val, why = bench.recorded_traffic("toeplitz_f32")
+    assert val is None and "predates" in why
+    assert bench.recorded_traffic("no_such_kernel") == (None, "no source map")
+
+
+def _plan(ncomp):
+    return SimpleNamespace(nt=1 << 20, n=3 * 4096 if ncomp == 3 else 4096, ncomp=ncomp,
+                           fft_block_f32=1 << 15, fft_block_f64=1 << 14)
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+@pytest.mark.parametrize("kernel", ["toeplitz_f32", "toeplitz_f64", "scatter_f32", "scatter_f64"])
+def test_roofline_algorithmic_bytes(kernel, ncomp):
+    plan = _plan(ncomp)
+    scan = SimpleNamespace(lam=4096, offsets=np.array([0, 1 << 19, 1 << 20]))
+    s = 4 if kernel.endswith("f32") else 8
+    per_sample = 4 + (2 * s if ncomp == 3 else 0) + s     # index, weights, one value
+    expect = plan.nt * per_sample + plan.n * s
+    ms = 0.25
+    r = bench.roofline(kernel, ms, plan, scan, 6769.0, "measured")
+    hbm = r if r["bound"] == "hbm" else r["hbm"]
+    assert hbm["bytes_per_launch"] == expect
+    assert hbm["achieved"] == pytest.approx(expect / (ms * 1e-3) / 1e9, abs=0.05)
+    assert hbm["frac"] == pytest.approx(hbm["achieved"] / 6769.0, abs=1e-4)
+    if kernel.startswith("toeplitz"):
+        # the bound is whichever fraction is larger
+        alu = r["alu"] if r["bound"] == "hbm" else r
+        assert r["frac"] == max(hbm["frac"], alu["frac"])
+        B = plan.fft_block_f32 if s == 4 else plan.fft_block_f64
+        assert bench.fft_tiles(scan, B) == 2 * -(-(1 << 19) // (B - 2 * 4096))
+    else:
+        assert r["bound"] == "hbm" and "alu" not in r
