@@ -179,7 +179,10 @@ mm_status mm_apply_ninv(mm_plan_t plan, int precision, const void* y, void* z);
  */
 mm_status mm_scatter(mm_plan_t plan, int precision, const void* z, void* w);
 
-/* y = A x = P^T [N^-1 [P x]] (Eq. 5, 8).  x, y device [n] in `precision`. */
+/* y = A x = P^T [N^-1 [P x]] (Eq. 5, 8).  x, y device [n] in `precision`.
+ * Errors of mm_gather, mm_apply_ninv, mm_scatter and mm_apply_A: MM_ERR_ARG for a null
+ * vector, an unknown precision, or a precision with no overlap-save block for this
+ * lambda (FP64 blocks reach lambda <= 32767, FP32 ones lambda <= 65535). */
 mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y);
 
 /*
@@ -216,14 +219,17 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
  * at most `maxit` steps), the Lanczos tridiagonal of that solve
  * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), its k
  * smallest Ritz pairs, Ritz vectors Z = sum_j (-1)^j z_j / sqrt(r_j^T z_j) s_j,
- * Euclidean orthonormalisation (columns with R_jj < 1e-10 max R_jj dropped), then
+ * Euclidean orthonormalisation (a column is dropped when its part orthogonal to the
+ * kept ones is below 1e-10 of the largest kept one or at most 1e-6 of its own norm), then
  * AZ = A Z (FP64) and E = Z^T A Z, Cholesky-factored in FP64 (App. C, "Constructing"),
- * kept as E^-1 = L^-T L^-1 for the PCG kernels.  A failed build leaves the previous
- * coarse space (or none) in place.
+ * kept as E^-1 = L^-T L^-1 for the PCG kernels (when rounding leaves E numerically
+ * indefinite, E^-1 comes from LU with partial pivoting, symmetrised).  A failed build
+ * leaves the previous coarse space (or none) in place.
  *   k       requested coarse dimension, 1 <= k <= 64.
  *   bprime  device double[n] right-hand side of the first solve, or NULL for b' = the
  *           b of the last mm_solve (MM_ERR_STATE if there was none).
- * Errors: MM_ERR_NOT_SPD when E is not positive definite.
+ * Errors: MM_ERR_NOT_SPD when E is singular, MM_ERR_NUMERIC when it holds NaN or Inf,
+ * MM_ERR_ARG for k outside 1..64 or maxit < 1.
  */
 mm_status mm_build_coarse(mm_plan_t plan, int k, int precision, const double* bprime,
                           double tol, int maxit);
