@@ -188,3 +188,63 @@ def test_psd_gradient_matches_central_differences(arg):
             # the difference quotient's own rounding floor: kappa eps L / h
             floor = 10 * kappa * np.finfo(float).eps * L0 / h
             assert fd == pytest.approx(G[p, c], rel=1e-4, abs=1e-6 * np.abs(G).max() + floor), (p, c)
+
+
+@SETTINGS
+@given(problems(), st.integers(1, 6))
+def test_apriori_rows_sum_to_one(arg, r):
+    """Z_S of Eq. 16-17: each observed pixel's T row is its hit fractions over the
+    intervals, so it sums to 1; Q/U rows are zero; merging intervals keeps both."""
+    pr, _ = arg
+    from oracle.precond import deflation_apriori, deflation_apriori_merged
+    Z = deflation_apriori(pr)
+    K = pr.offsets.size - 1
+    nc = pr.ncomp
+    np.testing.assert_allclose(Z[0::nc].sum(axis=1), 1.0, rtol=0, atol=1e-14)
+    if nc == 3:
+        assert np.all(Z[1::3] == 0.0) and np.all(Z[2::3] == 0.0)
+    Zm = deflation_apriori_merged(pr, min(r, K))
+    np.testing.assert_allclose(Zm[0::nc].sum(axis=1), 1.0, rtol=0, atol=1e-14)
+    # brute force: the fraction of pixel q's hits inside interval j
+    j = 0
+    a, b = int(pr.offsets[j]), int(pr.offsets[j + 1])
+    for q in range(min(pr.npix_obs, 5)):
+        frac = np.sum(pr.pix_c[a:b] == q) / pr.hits[q]
+        assert Z[q * nc, j] == pytest.approx(frac, abs=1e-15)
+
+
+@SETTINGS
+@given(problems())
+def test_lanczos_ritz_values_lie_in_the_spectrum(arg):
+    """Ritz values of the CG-Lanczos tridiagonal (Sec. 3.3.2) are Rayleigh quotients of
+    M_BD A, so they lie in its spectrum's hull [lambda_min, lambda_max]."""
+    pr, rng = arg
+    bd = precond.BlockJacobi(pr)
+    A = pr.dense_A()
+    ev = np.sort(np.linalg.eigvals(bd.dense() @ A).real)
+    res = pcg(pr.A, bd.apply, rng.standard_normal(pr.n), 1e-10, pr.n)
+    assume(len(res.alphas) >= 1)
+    T = precond.lanczos_tridiagonal(res.alphas, res.betas[: len(res.alphas) - 1])
+    th = np.linalg.eigvalsh(T)
+    slack = 1e-8 * ev[-1]
+    assert th.min() >= ev[0] - slack and th.max() <= ev[-1] + slack
+
+
+@SETTINGS
+@given(problems(), st.integers(1, 12))
+def test_arnoldi_relation(arg, m):
+    """Algorithm 1 gives B W_j = W_{j+1} Hbar_j (Eq. A.3), B = M_BD A, with W_j orthonormal;
+    w_{j+1} is a unit vector orthogonal to W_j unless h_{j+1,j} is at rounding level (the
+    Krylov space is exhausted: then it is noise, and the relation holds through the
+    negligible h_{j+1,j})."""
+    pr, rng = arg
+    bd = precond.BlockJacobi(pr)
+    B = lambda x: bd.apply(pr.A(x))
+    W, H, beta, _ = precond.arnoldi(B, bd.apply(rng.standard_normal(pr.n)), min(m, pr.n))
+    j = H.shape[1]
+    assume(j >= 1)
+    BW = np.stack([B(W[:, i]) for i in range(j)], axis=1)
+    np.testing.assert_allclose(BW, W @ H, rtol=0, atol=1e-10 * np.abs(BW).max())
+    np.testing.assert_allclose(W[:, :j].T @ W[:, :j], np.eye(j), atol=1e-10)
+    if H[j, j - 1] > 1e-8 * np.abs(H).max():
+        np.testing.assert_allclose(W.T @ W, np.eye(j + 1), atol=1e-10)
