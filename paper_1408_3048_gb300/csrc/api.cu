@@ -1,8 +1,10 @@
 // C-ABI entry points of libmm (declared in include/mm.h) and the host drivers behind
 // them: plan construction (Sec. 2 observed pixels, Eq. 4 / App. D Toeplitz rows,
-// overlap-save tiling, Eq. 10 M_BD), operator applications (Eq. 5-8), the PCG driver
-// (Sec. 3.1) with FP64 or mixed arithmetic plus iterative refinement, and the
-// a posteriori coarse space (Sec. 3.3.2, App. A, App. C).
+// overlap-save tiling and its block choice, Eq. 10 M_BD), operator applications
+// (Eq. 5-8), the PCG driver (Sec. 3.1) with FP64 or mixed arithmetic plus iterative
+// refinement and its residual history (Sec. 5.1), the coarse spaces (a posteriori from
+// CG-Lanczos or Arnoldi, Sec. 3.3.2 and App. A; a priori, Sec. 3.3.1; imported), the
+// A-DEF2 start (App. B), the adjoint and PSD gradients, and the batched solver.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
