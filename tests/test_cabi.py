@@ -113,3 +113,52 @@ def test_binding_rejects_mistyped_or_missized_arrays_before_any_call():
     for call, exc in cases:
         with pytest.raises(exc, match="expected|unsupported array type"):
             call()
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "mm.h"
+
+/* a plain C99 caller: every declared entry point is referenced (so the link resolves all
+ * of them) and the calls that need no GPU are made */
+typedef void (*any_fn)(void);
+int main(void) {
+    any_fn fns[] = {
+%s
+    };
+    size_t i;
+    mm_plan_t plan = NULL;
+    mm_opts opts;
+    for (i = 0; i < sizeof fns / sizeof fns[0]; ++i)
+        if (fns[i] == NULL) return 3;
+    memset(&opts, 0, sizeof opts);
+    if (mm_plan(&plan, NULL, 0, 0, NULL, NULL, 0, NULL, NULL, 0, &opts) != MM_ERR_ARG || plan != NULL) return 4;
+    if (mm_apply_A(NULL, MM_FP64, NULL, NULL) != MM_ERR_ARG) return 5;
+    if (strstr(mm_version(), "sm_103a") == NULL) return 6;
+    if (mm_launch_count() < 0) return 7;
+    mm_destroy(NULL);
+    printf("%%s\n", mm_version());
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(tmp_path):
+    """include/mm.h is plain C (C99, pedantic) and a C program links every symbol it
+    declares from libmm.so."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1408_3048_gb300 import build
+    path = build.build()
+    refs = "\n".join(f"        (any_fn){name}," for name in _declared())
+    (tmp_path / "consumer.c").write_text(C_CONSUMER % refs)
+    exe = tmp_path / "consumer"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-Wno-cast-function-type",
+                    "-I", os.path.join(ROOT, "include"), str(tmp_path / "consumer.c"), path,
+                    "-Wl,-rpath," + os.path.dirname(path), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "sm_103a" in r.stdout
