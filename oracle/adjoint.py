@@ -26,7 +26,8 @@ from .pcg import dense_solve, pcg
 
 
 def inverse_psd_derivative_grids(sigma, fknee, alpha, L, fsamp):
-    """d(1/S_j)/d(sigma, fknee, alpha) for j = 0..L/2 (requires fknee > 0)."""
+    """d(1/S_j)/d(sigma, fknee, alpha) for j = 0..L/2 (requires fknee > 0): the analytic
+    derivatives of the inverse of the Eq. 19 PSD on the grid of reading R1 (R14)."""
     if not fknee > 0.0:
         raise ValueError("the PSD gradient needs fknee > 0")
     j = np.arange(L // 2 + 1, dtype=np.float64)
@@ -49,7 +50,8 @@ def row_derivatives(sigma, fknee, alpha, L, fsamp, lam, kind=noise.WINDOW_GAUSS,
 
 
 def lagged_products(u, v, offsets, interval_psd, npsd, lam):
-    """R[p, k], k = 0..lam: interval-restricted lagged products of u and v per PSD id."""
+    """R[p, k], k = 0..lam: interval-restricted lagged products of u and v per PSD id
+    (the blocks of Eq. 4 act within their interval only; reading R14)."""
     R = np.zeros((npsd, lam + 1), dtype=np.float64)
     for i in range(len(offsets) - 1):
         a, b = int(offsets[i]), int(offsets[i + 1])
@@ -62,7 +64,7 @@ def lagged_products(u, v, offsets, interval_psd, npsd, lam):
 
 
 def psd_gradient(prob, u, v, kind=noise.WINDOW_GAUSS):
-    """dL/dtheta[p, (sigma, fknee, alpha)] = sum_k dt_k/dtheta R[p, k]."""
+    """dL/dtheta[p, (sigma, fknee, alpha)] = sum_k dt_k/dtheta R[p, k] (reading R14)."""
     R = lagged_products(u, v, prob.offsets, prob.interval_psd, len(prob.psds), prob.lam)
     G = np.zeros((len(prob.psds), 3), dtype=np.float64)
     for p, (s, fk, al) in enumerate(prob.psds):
@@ -72,7 +74,8 @@ def psd_gradient(prob, u, v, kind=noise.WINDOW_GAUSS):
 
 
 def gradients(prob, d, m, g, apply_M=None, tol=1e-12, maxit=10000, dense=False):
-    """(dL/dd, dL/dtheta) for the loss gradient g = dL/dm at the solution m of d."""
+    """(dL/dd, dL/dtheta) for the loss gradient g = dL/dm at the solution m of d: the
+    derivative of Eq. 3 through one solve with the symmetric A of Eq. 5 (reading R14)."""
     if dense:
         mu = dense_solve(prob.dense_A(), g)
     else:
@@ -85,7 +88,8 @@ def gradients(prob, d, m, g, apply_M=None, tol=1e-12, maxit=10000, dense=False):
 
 
 def dense_psd_gradient(prob, u, v, kind=noise.WINDOW_GAUSS):
-    """The same quantity through dense derivative blocks (tiny problems): u^T dN^-1 v."""
+    """The same quantity through dense derivative blocks (tiny problems): u^T dN^-1 v,
+    dN^-1 block-diagonal Toeplitz as in Eq. 4 (reading R14)."""
     G = np.zeros((len(prob.psds), 3), dtype=np.float64)
     for p, (s, fk, al) in enumerate(prob.psds):
         D = row_derivatives(s, fk, al, prob.L, prob.fsamp, prob.lam, kind)

@@ -81,7 +81,8 @@ def window(lam, kind=WINDOW_GAUSS):
 
 
 def toeplitz_row(sigma, fknee, alpha, L, fsamp, lam, kind=WINDOW_GAUSS, route="fft"):
-    """t_k = w_k r_k, k = 0..lam: the first row of one banded Toeplitz block of N^-1."""
+    """t_k = w_k r_k, k = 0..lam: the first row of one banded Toeplitz block of N^-1
+    (App. D and Eq. 28 by readings R1-R3)."""
     inv = inverse_psd_grid(sigma, fknee, alpha, L, fsamp)
     r = row_fft(inv, L, lam) if route == "fft" else row_direct(inv, L, lam)
     return window(lam, kind) * r
@@ -97,7 +98,8 @@ def symbol_grid_size(lam):
 
 
 def symbol(t, M):
-    """sigma(w_m) = t_0 + 2 sum_{k>=1} t_k cos(w_m k), w_m = 2 pi m / M, m = 0..M-1."""
+    """sigma(w_m) = t_0 + 2 sum_{k>=1} t_k cos(w_m k), w_m = 2 pi m / M, m = 0..M-1: the
+    symbol of the banded block, whose minimum decides positive definiteness (reading R4)."""
     lam = len(t) - 1
     m = np.arange(M, dtype=np.int64)
     s = np.full(M, t[0], dtype=np.float64)
@@ -107,7 +109,8 @@ def symbol(t, M):
 
 
 def symbol_fft(t, M):
-    """The same M symbol values by one real FFT of the even row laid out circularly."""
+    """The same M symbol values by one real FFT of the even row laid out circularly
+    (reading R4)."""
     lam = len(t) - 1
     h = np.zeros(M, dtype=np.float64)
     h[0] = t[0]

@@ -17,6 +17,10 @@ import scipy.linalg
 
 
 class PCGResult:
+    """What one PCG run (Sec. 3.1, reading R7) leaves: the iterate, its step count, the
+    relative residual history that Sec. 5.1 plots, and the step scalars and
+    preconditioned residuals the Ritz construction of Sec. 3.3.2 reads."""
+
     def __init__(self, x, iters, converged, rel_hist, alphas, betas, zs, rzs):
         self.x = x
         self.iters = iters
@@ -29,6 +33,9 @@ class PCGResult:
 
 
 def pcg(apply_A, apply_M, b, tol, maxit, record=False, x0=None):
+    """Preconditioned CG for A x = b (Sec. 3.1; reading R7: Hestenes-Stiefel PCG, stop on
+    ||r_j|| / ||b|| <= tol, Sec. 5.1).  record=True keeps z_j and r_j^T z_j for the
+    Lanczos tridiagonal of Sec. 3.3.2; x0 is the A-DEF2 start of App. B."""
     b = np.asarray(b, dtype=np.float64)
     if x0 is None:
         x = np.zeros_like(b)

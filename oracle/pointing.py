@@ -24,7 +24,9 @@ import numpy as np
 
 
 def unit_weight_blocks(pix, weights, npix_sky):
-    """B_p for every sky pixel, shape (npix_sky, 3, 3), accumulated in float64."""
+    """B_p = sum_{t in p} w_t w_t^T, w_t = (1, cos 2phi_t, sin 2phi_t) of Eq. 2, for every
+    sky pixel, shape (npix_sky, 3, 3), accumulated in float64 (the block whose
+    conditioning decides which pixels are observed, reading R6)."""
     c = weights[:, 0]
     s = weights[:, 1]
     one = np.ones_like(c)
@@ -40,7 +42,8 @@ def unit_weight_blocks(pix, weights, npix_sky):
 
 def rcond2(B):
     """Reciprocal 2-norm condition number lambda_min / lambda_max of stacked symmetric
-    3x3 blocks (eigenvalues by LAPACK's symmetric solver; 0 when lambda_max <= 0)."""
+    3x3 blocks (eigenvalues by LAPACK's symmetric solver; 0 when lambda_max <= 0):
+    the pixel acceptance test of reading R6."""
     ev = np.linalg.eigvalsh(B)
     lo, hi = ev[:, 0], ev[:, -1]
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -83,8 +86,9 @@ def depoint(x, pix_c, ncomp, weights=None):
 
 
 def point(y, pix_c, npix_obs, ncomp, weights=None):
-    """w = P^T y: per observed pixel, sum over its samples of y_t (I) and, for
-    polarisation, cos 2phi_t y_t (Q) and sin 2phi_t y_t (U).  Flat (npix_obs*ncomp,)."""
+    """w = P^T y (the transpose of Eq. 2, Sec. 2): per observed pixel, sum over its samples
+    of y_t (I) and, for polarisation, cos 2phi_t y_t (Q) and sin 2phi_t y_t (U).  Flat
+    (npix_obs*ncomp,)."""
     y = np.asarray(y, dtype=np.float64)
     kept = pix_c >= 0
     p = pix_c[kept]
@@ -98,7 +102,7 @@ def point(y, pix_c, npix_obs, ncomp, weights=None):
 
 
 def dense_pointing(pix_c, npix_obs, ncomp, weights=None):
-    """P as a dense (nt, npix_obs*ncomp) matrix (tiny problems only)."""
+    """P of Eq. 1-2 as a dense (nt, npix_obs*ncomp) matrix (tiny problems only)."""
     nt = pix_c.size
     P = np.zeros((nt, npix_obs * ncomp), dtype=np.float64)
     for t in range(nt):

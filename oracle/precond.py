@@ -62,10 +62,12 @@ class BlockJacobi:
         self.inv = np.linalg.inv(B)
 
     def apply(self, r):
+        """z = M_BD r: each pixel's block inverse applied to its components (Eq. 10)."""
         R = np.asarray(r, dtype=np.float64).reshape(self.npix, self.ncomp)
         return np.einsum("pab,pb->pa", self.inv, R).reshape(-1)
 
     def dense(self):
+        """M_BD (Eq. 10) as a dense block-diagonal matrix."""
         return scipy.linalg.block_diag(*list(self.inv))
 
 
@@ -80,10 +82,12 @@ class TwoLevel:
         self.lu = scipy.linalg.lu_factor(self.E)
 
     def coarse(self, r):
-        """v = E^-1 Z^T r."""
+        """v = E^-1 Z^T r (the coarse solve of Eq. 12, LU of E as in App. C)."""
         return scipy.linalg.lu_solve(self.lu, self.Z.T @ r)
 
     def apply(self, r):
+        """z = M_2lvl r = M_BD (r - A Z v) + Z v, v = E^-1 Z^T r (Eq. 12 in the order of
+        App. C)."""
         r = np.asarray(r, dtype=np.float64)
         v = self.coarse(r)
         return self.bd.apply(r - self.AZ @ v) + self.Z @ v
@@ -106,7 +110,8 @@ class TwoLevel:
 
 
 def lanczos_tridiagonal(alphas, betas):
-    """T_m from m CG steps (alphas[0..m-1], betas[0..m-2])."""
+    """T_m from m CG steps (alphas[0..m-1], betas[0..m-2]): the Lanczos tridiagonal of the
+    first solve (Sec. 3.3.2, reading R8)."""
     m = len(alphas)
     T = np.zeros((m, m), dtype=np.float64)
     for j in range(m):
@@ -168,8 +173,9 @@ def arnoldi(apply_B, r0, m, tol=0.0):
 
 
 def arnoldi_coarse_space(W, H, k, eps_tol, drop_rtol=1e-10):
-    """Ritz selection from an Arnoldi run (see the module note).  Returns (Z with
-    orthonormal columns, the selected Ritz values)."""
+    """Ritz selection from an Arnoldi run (App. A, Eq. A.4; selection |Re lambda| < eps_tol
+    of Sec. 5; reading R17).  Returns (Z with orthonormal columns, the selected Ritz
+    values)."""
     j = H.shape[1]
     lam, V = np.linalg.eig(H[:j, :j])
     order = np.argsort(lam.real, kind="stable")

@@ -66,12 +66,15 @@ class Problem:
 
     # ---- operators (Eq. 8) -------------------------------------------------------
     def P(self, x):
+        """y = P x (Eq. 2)."""
         return pointing.depoint(x, self.pix_c, self.ncomp, self.weights)
 
     def PT(self, y):
+        """w = P^T y (Sec. 2)."""
         return pointing.point(y, self.pix_c, self.npix_obs, self.ncomp, self.weights)
 
     def Ninv(self, y, route="direct"):
+        """z = N^-1 y (Eq. 4)."""
         return toeplitz.apply_ninv(y, self.offsets, self.interval_psd, self.rows, route)
 
     def A(self, x, route="direct"):
@@ -83,15 +86,19 @@ class Problem:
         return self.PT(self.Ninv(d, route))
 
     def ninv_diag(self):
+        """diag(N^-1), the weights of M_BD (Eq. 10)."""
         return toeplitz.diagonal(self.nt, self.offsets, self.interval_psd, self.rows)
 
     # ---- dense forms (tiny problems only) ----------------------------------------
     def dense_P(self):
+        """P (Eq. 1-2) as a dense matrix."""
         return pointing.dense_pointing(self.pix_c, self.npix_obs, self.ncomp, self.weights)
 
     def dense_Ninv(self):
+        """N^-1 (Eq. 4) as a dense matrix."""
         return toeplitz.dense_ninv(self.offsets, self.interval_psd, self.rows)
 
     def dense_A(self):
+        """A = P^T N^-1 P (Eq. 5) as a dense matrix."""
         P = self.dense_P()
         return P.T @ self.dense_Ninv() @ P

@@ -20,21 +20,24 @@ def _full_kernel(t):
 
 
 def apply_block_direct(y, t):
-    """z = T y for one block by direct convolution (np.convolve is the plain sum)."""
+    """z = T y for one block of Eq. 4 by direct convolution (np.convolve is the plain sum;
+    band |k| <= lambda of Sec. 4.1.4, truncated at the block edges: readings R3, R5)."""
     lam = len(t) - 1
     full = np.convolve(np.asarray(y, dtype=np.float64), _full_kernel(t), mode="full")
     return full[lam : lam + len(y)]
 
 
 def apply_block_fft(y, t):
-    """The same product through scipy.signal.fftconvolve (library FFT as a step)."""
+    """The same product (one block of Eq. 4) through scipy.signal.fftconvolve (library FFT
+    as a step)."""
     lam = len(t) - 1
     full = scipy.signal.fftconvolve(np.asarray(y, dtype=np.float64), _full_kernel(t), mode="full")
     return full[lam : lam + len(y)]
 
 
 def dense_block(t, n):
-    """T as a dense n x n symmetric Toeplitz matrix (band truncated at the block edge)."""
+    """T as a dense n x n symmetric Toeplitz matrix (one block of Eq. 4, band truncated at
+    the block edge)."""
     c = np.zeros(n, dtype=np.float64)
     m = min(n, len(t))
     c[:m] = t[:m]
@@ -42,7 +45,8 @@ def dense_block(t, n):
 
 
 def apply_ninv(y, offsets, interval_psd, rows, route="direct"):
-    """z = N^-1 y over all intervals.  offsets[K+1], interval_psd[K], rows[psd] = t_k."""
+    """z = N^-1 y over all intervals (Eq. 4: block-diagonal, one block per stationary
+    interval).  offsets[K+1], interval_psd[K], rows[psd] = t_k."""
     y = np.asarray(y, dtype=np.float64)
     z = np.zeros_like(y)
     fn = apply_block_direct if route == "direct" else apply_block_fft
@@ -53,7 +57,7 @@ def apply_ninv(y, offsets, interval_psd, rows, route="direct"):
 
 
 def dense_ninv(offsets, interval_psd, rows):
-    """N^-1 as a dense block-diagonal matrix (tiny problems only)."""
+    """N^-1 of Eq. 4 as a dense block-diagonal matrix (tiny problems only)."""
     blocks = [
         dense_block(rows[int(interval_psd[i])], int(offsets[i + 1] - offsets[i]))
         for i in range(len(offsets) - 1)
