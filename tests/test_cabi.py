@@ -162,3 +162,33 @@ def test_header_compiles_as_c_and_links(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert "sm_103a" in r.stdout
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes (mm_psd, mm_opts, mm_stats, mm_solve_opts) has the
+    size and field offsets of include/mm.h as a C compiler lays it out."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1408_3048_gb300 import mm
+    structs = {"mm_psd": mm.mm_psd, "mm_opts": mm.mm_opts, "mm_stats": mm.mm_stats,
+               "mm_solve_opts": mm.mm_solve_opts}
+    lines = []
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            cfield = "lambda" if fname == "lambda_" else fname
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {cfield}));')
+    src = "#include <stddef.h>\n#include <stdio.h>\n#include \"mm.h\"\nint main(void) {\n" + "\n".join(lines) + \
+          "\n    return 0;\n}\n"
+    (tmp_path / "layout.c").write_text(src)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(tmp_path / "layout.c"), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert c[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert c[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
