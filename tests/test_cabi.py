@@ -192,3 +192,46 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert c[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert c[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def _header_prototypes():
+    """name -> (return type, [argument types]) for every function declared in mm.h."""
+    with open(os.path.join(ROOT, "include", "mm.h")) as f:
+        txt = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"^\s*((?:const\s+)?[a-z_0-9]+\s*\**)\s*(mm_[A-Za-z_0-9]+)\s*\(([^)]*)\)\s*;", txt,
+                         re.M | re.S):
+        ret, name, args = m.group(1), m.group(2), m.group(3)
+        args = [" ".join(a.split()) for a in args.split(",")]
+        protos[name] = (" ".join(ret.split()), [] if args == ["void"] else args)
+    return protos
+
+
+def _kind(c_decl):
+    """Type class of a C parameter or return type: pointer, int32, int64, double, void."""
+    if "*" in c_decl or c_decl.startswith("mm_plan_t"):
+        return "ptr"
+    t = c_decl.replace("const ", "").split()[0]
+    return {"int32_t": "i32", "int": "i32", "mm_status": "i32", "int64_t": "i64", "double": "f64",
+            "void": "void"}[t]
+
+
+def _ctypes_kind(t):
+    import ctypes as C
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return "ptr"
+    return {C.c_int32: "i32", C.c_int: "i32", C.c_int64: "i64", C.c_double: "f64"}[t]
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    from paper_1408_3048_gb300 import mm
+    protos = _header_prototypes()
+    assert sorted(protos) == _declared()
+    for name, (ret, args) in protos.items():
+        res, argt = mm._SIGS[name]
+        assert _ctypes_kind(res) == _kind(ret), (name, "return")
+        assert len(argt) == len(args), (name, len(argt), len(args))
+        for i, (a, t) in enumerate(zip(args, argt)):
+            assert _ctypes_kind(t) == _kind(a), (name, i, a)
