@@ -346,7 +346,8 @@ mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
  *   rel_resid  host double[max], may be NULL.
  *   count      host, may be NULL: number of entries, stats.iters + 1 (0 before any
  *              solve; fewer when a solve ran past 2^20 products, which are not kept).
- * Errors: MM_ERR_ARG for max < 0.  The batched solver keeps no history.
+ * Errors: MM_ERR_ARG for max < 0.  The batched solver keeps no history: after it the
+ * entries are still those of the last single-right-hand-side solve.
  */
 mm_status mm_solve_history(mm_plan_t plan, int32_t max, double* rel_resid, int32_t* count);
 
