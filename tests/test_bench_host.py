@@ -69,3 +69,27 @@ def test_roofline_algorithmic_bytes(kernel, ncomp):
         assert bench.fft_tiles(scan, B) == 2 * -(-(1 << 19) // (B - 2 * 4096))
     else:
         assert r["bound"] == "hbm" and "alu" not in r
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
+    """Under torchrun the oracle arm runs and prints on rank 0 only; other ranks return at
+    once (the oracle is never started there)."""
+    monkeypatch.setattr(bench, "oracle_time_to_solution",
+                        lambda *a, **k: (_ for _ in ()).throw(AssertionError("oracle started")))
+    args = SimpleNamespace(gpus=2, steps=2, warmup=1)
+    assert bench.run_reference(args, 1, 2) is None
+    assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    """The oracle arm's JSON line: the GPU arm's metric, time-like, per-step values after
+    the warm-up steps averaged, its own cpu_baseline and e2e."""
+    import json
+    monkeypatch.setattr(bench, "oracle_time_to_solution", lambda steps, iters: ([9.0] + [2.0] * (steps - 1), {}))
+    bench.run_reference(SimpleNamespace(gpus=1, steps=3, warmup=1), 0, 1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "s"
+    assert line["value"] == 2.0 and line["higher_is_better"] is False
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["value"] == 2.0 and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["workload"] == bench.WORKLOAD
