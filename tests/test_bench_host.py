@@ -93,3 +93,31 @@ def test_reference_arm_line(capsys, monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["value"] == 2.0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["config"]["workload"] == bench.WORKLOAD
+
+
+def test_clock_record_parsing(tmp_path):
+    """The clocks key: median SM clock over the loaded samples, the maximum clock, and every
+    throttle reason seen Active (samples from nvidia-smi --format=csv,noheader,nounits)."""
+    path = tmp_path / "clocks.csv"
+    rows = ["0, 345, 2070, 120.5, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",   # idle
+            "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "garbled line"]
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(path)
+    cs.proc = SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: None, kill=lambda: None)
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 4
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert not path.exists()
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_peak_bandwidth_source(tmp_path, monkeypatch):
+    import json
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6769.4}))
+    assert bench.peaks() == (6769.4, "measured")
