@@ -1107,6 +1107,11 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
             if (!cholesky_drop(G, kcur, pass == 0 ? 1e-10 : 0.0, W, kept))
                 throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
             const int knew = (int)kept.size();
+            if (pass == 0 && knew < kcur) {   // the reported Ritz values follow the kept columns
+                std::vector<double> th2;
+                for (int c : kept) th2.push_back(theta[(size_t)c]);
+                theta.swap(th2);
+            }
             C = dalloc<double>(W.size());
             h2d(C, W.data(), W.size() * 8, s);
             Y2 = dalloc<double>((size_t)knew * P.n);
