@@ -123,7 +123,8 @@ def lanczos_tridiagonal(alphas, betas):
 
 def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
     """Reading R8.  zs[j] = z_j, rzs[j] = r_j^T z_j for j = 0..m-1.
-    Returns (Z with orthonormal columns, the k smallest Ritz values).  With eps_tol the
+    Returns (Z with orthonormal columns, the Ritz values of the kept columns, ascending:
+    the k smallest unless a dependent column was dropped).  With eps_tol the
     Ritz pairs kept are those with value below eps_tol (Sec. 5: |Re lambda_i| < eps_tol,
     the paper uses 0.2), at most k of them, smallest first."""
     m = len(alphas)
@@ -139,7 +140,7 @@ def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
     Q, R = np.linalg.qr(Y)
     d = np.abs(np.diag(R))
     keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
-    return Q[:, keep], theta[:kk]
+    return Q[:, keep], theta[:kk][keep]      # the values of the kept vectors
 
 
 def arnoldi(apply_B, r0, m, tol=0.0):
@@ -200,7 +201,7 @@ def arnoldi_coarse_space(W, H, k, eps_tol, drop_rtol=1e-10):
     Q, R = np.linalg.qr(Y)
     d = np.abs(np.diag(R))
     keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
-    return Q[:, keep], np.asarray(vals)
+    return Q[:, keep], np.asarray(vals)[keep]      # the values of the kept vectors
 
 
 def deflation_apriori(prob):

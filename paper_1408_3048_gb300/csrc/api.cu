@@ -802,7 +802,7 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
 // Orthonormalises the kc columns of Y (FP64 [kc][n], device) twice by Cholesky of the
 // Gram matrix (CholQR2), dropping in the first pass columns whose pivot is below 1e-10
 // of the largest kept one; Y is replaced, kc updated.
-static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc) {
+static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc, std::vector<int>* kept_out = nullptr) {
     cudaStream_t s = P.stream;
     for (int pass = 0; pass < 2; ++pass) {
         const std::vector<double> G = gram_host(P, Y, kc, Y, kc);
@@ -810,6 +810,7 @@ static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc) {
         std::vector<int> kept;
         if (!cholesky_drop(G, kc, pass == 0 ? 1e-10 : 0.0, W, kept) || kept.empty())
             throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
+        if (pass == 0 && kept_out != nullptr) *kept_out = kept;   // the input columns kept
         const int knew = (int)kept.size();
         double* C = dalloc<double>(W.size());
         double* Y2 = nullptr;
@@ -990,11 +991,13 @@ static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const 
         dfree(hv);
         hv = nullptr;
         int kc = kk;
-        orthonormalise_drop(P, Y, kc);
+        std::vector<int> kept;
+        orthonormalise_drop(P, Y, kc, &kept);
         double* Zk = Y;
         Y = nullptr;
-        vals.resize((size_t)kc);
-        install_coarse(P, Zk, kc, vals);
+        std::vector<double> kept_vals;   // the values of the kept columns
+        for (int c : kept) kept_vals.push_back(vals[(size_t)c]);
+        install_coarse(P, Zk, kc, kept_vals);
     } catch (...) {
         dfree(W);
         dfree(hv);
