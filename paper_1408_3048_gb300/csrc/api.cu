@@ -340,13 +340,16 @@ static void autotune_toeplitz(PlanHolder& P, ToeplitzDev& tz, T* tod, const T* z
     float best_ms = 0.f;
     for (size_t i = 0; i < c.size() && i < 3; ++i) {
         ToeplitzDev cand;
-        if (c[i].second == tz.logn) {
-            cand = tz;
-        } else {
-            build_toeplitz<T>(P, cand, c[i].second + 1);
+        const bool fresh = c[i].second != tz.logn;
+        float ms = 0.f;
+        try {
+            if (fresh) build_toeplitz<T>(P, cand, c[i].second + 1);
+            else cand = tz;
+            ms = time_launches(P, [&] { launch_toeplitz<T>(P, cand, nullptr, zmap, tod, nullptr, P.stream); }, 3);
+        } catch (...) {
+            if (fresh) free_tz(cand);   // a candidate built here and not kept
+            throw;
         }
-        const float ms =
-            time_launches(P, [&] { launch_toeplitz<T>(P, cand, nullptr, zmap, tod, nullptr, P.stream); }, 3);
         tuned_ms[c[i].second - 8] = ms;
         if (cand.logn == tz.logn) {
             if (best_ms == 0.f || ms < best_ms) best_ms = ms;
