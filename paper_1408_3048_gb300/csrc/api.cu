@@ -878,8 +878,13 @@ static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const 
             if (j + 2 > wcap) {
                 const int ncap = std::min(2 * wcap, mcap + 1);
                 double* W2 = dalloc<double>((size_t)ncap * n);
-                check_cuda(cudaMemcpyAsync(W2, W, (size_t)wcap * n * 8, cudaMemcpyDeviceToDevice, s), "grow W");
-                sync(s);
+                try {
+                    check_cuda(cudaMemcpyAsync(W2, W, (size_t)wcap * n * 8, cudaMemcpyDeviceToDevice, s), "grow W");
+                    sync(s);
+                } catch (...) {
+                    dfree(W2);
+                    throw;
+                }
                 dfree(W);
                 W = W2;
                 wcap = ncap;
@@ -978,8 +983,8 @@ static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const 
         std::vector<double> C((size_t)j * kk);
         for (int q = 0; q < j; ++q)
             for (int c = 0; c < kk; ++c) C[(size_t)q * kk + c] = cols[(size_t)c][(size_t)q];
+        Y = dalloc<double>((size_t)kk * n);   // freed by the handler below on failure
         double* Cd = dalloc<double>(C.size());
-        Y = dalloc<double>((size_t)kk * n);
         try {
             h2d(Cd, C.data(), C.size() * 8, s);
             launch_lincomb<double>(W, j, n, Cd, kk, Y, s);
