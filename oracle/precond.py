@@ -14,10 +14,14 @@ tridiagonal T_m built from the CG step scalars,
     T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},   T_{j,j+1} = sqrt(beta_j)/alpha_j,
 give Ritz vectors V_m s with Lanczos vectors v_j = (-1)^j z_j / sqrt(r_j^T z_j)
 (z_j = M_BD r_j, the preconditioned CG residuals).  The selected vectors are
-orthonormalised (Euclidean QR) and columns with |R_jj| < 1e-10 max |R_jj|, or with
-|R_jj| <= 1e-6 of the column's own norm, dropped (reading R16: the paper says nothing on
-dependent coarse columns; a part orthogonal to the kept ones below 1e-6 of the column is
-taken as dependence, the resolution of a Gram-matrix orthonormalisation).
+orthonormalised (Euclidean QR) after dropping dependent columns.
+Reading R16 (the paper says nothing on dependent coarse columns; E = Z^T A Z of Eq. 12
+must be invertible): the columns are taken in order and column j is dependent when its
+part orthogonal to the columns kept before it (Gram-Schmidt, projected twice) has norm
+below 1e-10 times the largest column norm of the matrix -- the R_jj < 1e-10 max R_jj
+rule of a QR factorisation, with the scale taken from the columns themselves.  Double
+projection in FP64 resolves that part to a few eps of the column norm, so an exact
+duplicate (part ~1e-16) is dropped and a near-duplicate 1e-9 away is kept.
 Reading R9: E is factored by LU with partial pivoting (as App. C does).
 
 Arnoldi route (App. A, Algorithm 1; the paper's own Z_D source): the basic Arnoldi
@@ -33,7 +37,7 @@ orthonormalisation and dropping as above.
 import numpy as np
 import scipy.linalg
 
-OWN_NORM_RTOL = 1e-6   # reading R16: dependence threshold relative to a column's own norm
+DROP_RTOL = 1e-10   # reading R16: dependence threshold relative to the largest column norm
 
 
 class BlockJacobi:
@@ -137,10 +141,8 @@ def ritz_coarse_space(alphas, betas, zs, rzs, k, drop_rtol=1e-10, eps_tol=None):
             raise ValueError("no Ritz value below eps_tol")
     V = np.stack([((-1.0) ** j) * zs[j] / np.sqrt(rzs[j]) for j in range(m)], axis=1)
     Y = V @ S[:, :kk]
-    Q, R = np.linalg.qr(Y)
-    d = np.abs(np.diag(R))
-    keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
-    return Q[:, keep], theta[:kk][keep]      # the values of the kept vectors
+    Q, kept = orthonormal_basis(Y, drop_rtol)
+    return Q, theta[:kk][kept]      # the values of the kept vectors
 
 
 def arnoldi(apply_B, r0, m, tol=0.0):
@@ -198,10 +200,8 @@ def arnoldi_coarse_space(W, H, k, eps_tol, drop_rtol=1e-10):
     if not cols:
         raise ValueError("no Ritz value below eps_tol")
     Y = np.stack(cols, axis=1)
-    Q, R = np.linalg.qr(Y)
-    d = np.abs(np.diag(R))
-    keep = (d >= drop_rtol * d.max()) & (d > OWN_NORM_RTOL * np.linalg.norm(Y, axis=0))
-    return Q[:, keep], np.asarray(vals)[keep]      # the values of the kept vectors
+    Q, kept = orthonormal_basis(Y, drop_rtol)
+    return Q, np.asarray(vals)[kept]      # the values of the kept vectors
 
 
 def deflation_apriori(prob):
@@ -233,28 +233,38 @@ def deflation_apriori_merged(prob, r):
     return Z @ G
 
 
-def independent_columns(Z, drop_rtol=1e-10):
-    """Columns of Z in order, skipping each column whose component orthogonal to the
-    kept ones has norm < drop_rtol times the largest such norm kept so far, or at most
-    OWN_NORM_RTOL times the column's own norm: Z_S has dependent columns whenever
-    intervals see the same hit fractions, and E = Z^T A Z must be invertible (Eq. 12).
-    Gram-Schmidt, projected twice."""
+def independent_columns(Z, drop_rtol=DROP_RTOL):
+    """Reading R16.  Columns of Z in order, skipping each column whose component
+    orthogonal to the kept ones (Gram-Schmidt, projected twice) has norm below drop_rtol
+    times the largest column norm of Z (or is zero): Z_S has dependent columns whenever
+    intervals see the same hit fractions, Ritz vectors can repeat, and E = Z^T A Z must
+    be invertible (Eq. 12).  Returns (the kept columns, their indices)."""
     Z = np.asarray(Z, dtype=np.float64)
+    scale = np.linalg.norm(Z, axis=0).max() if Z.shape[1] else 0.0
     Q = np.zeros((Z.shape[0], 0))
-    kept, maxpiv = [], 0.0
+    kept = []
     for j in range(Z.shape[1]):
         v = Z[:, j].copy()
         for _ in range(2):
             v -= Q @ (Q.T @ v)
         piv = np.linalg.norm(v)
-        if piv < drop_rtol * maxpiv or piv <= OWN_NORM_RTOL * np.linalg.norm(Z[:, j]):
+        if not piv > 0.0 or piv < drop_rtol * scale:
             continue
         kept.append(j)
         Q = np.column_stack([Q, v / piv])
-        maxpiv = max(maxpiv, piv)
     return Z[:, kept], kept
+
+
+def orthonormal_basis(Y, drop_rtol=DROP_RTOL):
+    """Orthonormal basis of the columns of Y kept by independent_columns (reading R16),
+    by Householder QR of the kept columns (np.linalg.qr).  Returns (Q, kept indices)."""
+    Yk, kept = independent_columns(Y, drop_rtol)
+    if not kept:
+        raise ValueError("every column is dependent")
+    Q, _ = np.linalg.qr(Yk)
+    return Q, kept
 
 
 __all__ = ["BlockJacobi", "TwoLevel", "lanczos_tridiagonal", "ritz_coarse_space",
            "arnoldi", "arnoldi_coarse_space", "deflation_apriori", "deflation_apriori_merged",
-           "independent_columns"]
+           "independent_columns", "orthonormal_basis"]

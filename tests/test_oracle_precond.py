@@ -290,3 +290,49 @@ def test_two_level_needs_fewer_iterations():
     it_bd = pcg(pr.A, bd.apply, b2, 1e-6, 2000).iters
     it_2l = pcg(pr.A, tl.apply, b2, 1e-6, 2000).iters
     assert it_2l < it_bd
+
+
+def test_dependence_rule_pins():
+    # reading R16: a column is dependent when its part orthogonal to the earlier kept
+    # columns is below 1e-10 of the largest column norm.  Exact duplicates, scaled copies,
+    # combinations and zero columns go; a near-duplicate 1e-9 away stays, one 1e-11 away
+    # goes (both relative to the column norm of ~8)
+    rng = np.random.default_rng(4)
+    Y = rng.standard_normal((64, 9))
+    Y[:, 2] = Y[:, 0]
+    Y[:, 3] = -3.0 * Y[:, 1]
+    Y[:, 4] = Y[:, 0] - 2.0 * Y[:, 1]
+    Y[:, 5] = 0.0
+    u = rng.standard_normal(64)
+    u /= np.linalg.norm(u)
+    Y[:, 6] = Y[:, 1] + 1e-9 * np.linalg.norm(Y[:, 1]) * u
+    Y[:, 7] = Y[:, 0] + 1e-11 * np.linalg.norm(Y[:, 0]) * u
+    _, kept = precond.independent_columns(Y)
+    assert kept == [0, 1, 6, 8]
+    Q, kept2 = precond.orthonormal_basis(Y)
+    assert kept2 == kept
+    np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-12)
+    Yk = Y[:, kept]
+    assert np.linalg.norm(Yk - Q @ (Q.T @ Yk)) <= 1e-12 * np.linalg.norm(Yk)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dependence_rule_matches_the_numerical_rank(seed):
+    # independent of the Gram-Schmidt route: for a matrix of exact rank r with the other
+    # columns random combinations of earlier ones, the kept count equals the number of
+    # singular values above 1e-10 of the largest column norm, the first r columns are kept
+    # and their span contains every column
+    rng = np.random.default_rng(seed)
+    n, r, k = 80, 5, 12
+    B = rng.standard_normal((n, r))
+    C = np.zeros((r, k))
+    C[:, :r] = np.eye(r)
+    C[:, r:] = rng.standard_normal((r, k - r))
+    Y = B @ C
+    Y[:, r:] += 1e-14 * rng.standard_normal((n, k - r))
+    _, kept = precond.independent_columns(Y)
+    s = np.linalg.svd(Y, compute_uv=False)
+    assert len(kept) == int(np.sum(s > 1e-10 * np.linalg.norm(Y, axis=0).max())) == r
+    assert kept == list(range(r))
+    Q, _ = precond.orthonormal_basis(Y)
+    assert np.linalg.norm(Y - Q @ (Q.T @ Y)) <= 1e-12 * np.linalg.norm(Y)
