@@ -194,10 +194,12 @@ mm_status mm_apply_A(mm_plan_t plan, int precision, const void* x, void* y);
  * into the library (held on every device that loads it, until the process exits)
  * instead of in the plan's buffer; so nt * (8 for MM_FP64, 4 for MM_FP32) must not
  * exceed 32 MiB (nt <= 4194304 in FP64, 8388608 in FP32), else MM_ERR_ARG.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * All calls share the array: every call rewrites what it reads, but calls that overlap
- * on the GPU (other streams, other host threads) race.  x, y device [n] in `precision`.
+ * mm_plan looks up the array's device address (cudaGetSymbolAddress, with the plan's
+ * device current), which also creates the array on that device; the call itself does
+ * no set-up.  The call launches on the plan's stream and synchronises it before it
+ * returns.  All calls share the array: every call rewrites what it reads, but calls
+ * that overlap on the GPU (other streams, other host threads) race.  x, y device [n]
+ * in `precision`.  Errors: those of mm_apply_A, and MM_ERR_ARG for a null plan.
  */
 mm_status mm_apply_A_static(mm_plan_t plan, int precision, const void* x, void* y);
 
@@ -219,8 +221,10 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
  * at most `maxit` steps), the Lanczos tridiagonal of that solve
  * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), its k
  * smallest Ritz pairs, Ritz vectors Z = sum_j (-1)^j z_j / sqrt(r_j^T z_j) s_j,
- * Euclidean orthonormalisation (a column is dropped when its part orthogonal to the
- * kept ones is below 1e-10 of the largest kept one or at most 1e-6 of its own norm), then
+ * Euclidean orthonormalisation in FP64 (classical Gram-Schmidt projected twice, in
+ * order; a column is dropped when its part orthogonal to the kept ones is below 1e-10
+ * of the largest column norm -- an exact duplicate goes, a near-duplicate 1e-9 away
+ * stays), then
  * AZ = A Z (FP64) and E = Z^T A Z, Cholesky-factored in FP64 (App. C, "Constructing"),
  * kept as E^-1 = L^-T L^-1 for the PCG kernels (when rounding leaves E numerically
  * indefinite, E^-1 comes from LU with partial pivoting, symmetrised).  A failed build
@@ -263,10 +267,13 @@ mm_status mm_build_coarse_arnoldi(mm_plan_t plan, int kmax, double eps_tol, cons
 
 /*
  * Install a given coarse basis Z (host or device double[k * n], column j at Z[j*n ..]):
- * AZ = A Z, E = Z^T A Z, E^-1 as for mm_build_coarse -- to reuse a basis saved from an
- * earlier plan of the same pointing (mm_coarse_vectors) without its construction solve.
- * The columns must be linearly independent (MM_ERR_NOT_SPD otherwise) and finite
- * (MM_ERR_NUMERIC otherwise); the previous coarse space then stays.  1 <= k <= 64.
+ * its columns are orthonormalised in order with dependent ones dropped (the rule of
+ * mm_build_coarse; a basis saved by mm_coarse_vectors is already orthonormal and comes
+ * back unchanged up to rounding), then AZ = A Z, E = Z^T A Z, E^-1 as for
+ * mm_build_coarse -- to reuse a basis saved from an earlier plan of the same pointing
+ * without its construction solve.  mm_coarse_info reports the kept dimension.  The
+ * columns must be finite (MM_ERR_NUMERIC otherwise, also when every column is zero);
+ * the previous coarse space then stays.  1 <= k <= 64.
  * The paper has no counterpart beyond reusing a coarse space across solves.
  */
 mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k);
@@ -278,9 +285,9 @@ mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k);
  * 1.  Its K columns are merged into r groups of consecutive intervals (interval i joins
  * group floor(i r / K); merged column = sum of its members, rows still sum to 1), as the
  * paper allows to reduce the coarse dimension.  The merged columns are replaced by an
- * orthonormal basis of their range (Cholesky QR twice; columns whose pivot is below
- * 1e-10 times the largest kept one are dropped -- intervals that see the same hit
- * fractions give equal columns).  M_2lvl depends on Z only through its range, and the
+ * orthonormal basis of their range (the orthonormalisation and dropping rule of
+ * mm_build_coarse -- intervals that see the same hit fractions give equal columns,
+ * which are dropped).  M_2lvl depends on Z only through its range, and the
  * orthonormal basis keeps E = Z^T A Z as well conditioned as A on that range (raw
  * hit-fraction columns of an evenly covered patch are nearly parallel).  Then AZ, E and
  * E^-1 as for mm_build_coarse.  No solve is needed.
@@ -350,6 +357,23 @@ mm_status mm_profile_read(mm_plan_t plan, double* ms, int64_t* launches);
  * entries are still those of the last single-right-hand-side solve.
  */
 mm_status mm_solve_history(mm_plan_t plan, int32_t max, double* rel_resid, int32_t* count);
+
+/*
+ * Diagnostic of the bounded waits inside the persistent PCG kernels (the paper has no
+ * counterpart).  Every grid-barrier wait of the cooperative PCG kernels is limited in
+ * time (2 s in every solve) and a wait that runs out ends the kernel with
+ * MM_ERR_TIMEOUT instead of hanging the GPU.  This call exercises that path without a
+ * fault: it runs the FP64 block-Jacobi PCG start kernel on a zero right-hand side
+ * through the solver's own driver, with the barrier counting `absent_blocks` blocks
+ * that are never launched and each wait limited to `wait_s` seconds, and returns the
+ * status the solver reports: MM_OK for absent_blocks = 0, MM_ERR_TIMEOUT (message in
+ * mm_last_error) for absent_blocks > 0 after about wait_s.  The plan's barrier settings
+ * go back to the defaults afterwards and the plan stays usable (every run starts from a
+ * zeroed barrier counter).  The PCG vectors' contents are overwritten.
+ *   absent_blocks  0 .. 1024;  wait_s  in (0, 10].
+ * Errors: MM_ERR_ARG for arguments out of range.
+ */
+mm_status mm_pcg_barrier_check(mm_plan_t plan, int32_t absent_blocks, double wait_s);
 
 /* Options of mm_solve_ex.  Zero-initialise and set what you need; 0 selects the default. */
 typedef struct {

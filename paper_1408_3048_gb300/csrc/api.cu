@@ -11,6 +11,9 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "coarse.cuh"
 #include "coarse_host.h"
@@ -29,6 +32,17 @@ void check_cuda(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
         throw Error{MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
     }
+}
+
+void ensure_smem_attr(const void* kern, int bytes, const char* what) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;   // (kernel, device)
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kern, dev})) return;
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), what);
+    done.insert({kern, dev});
 }
 
 void* dmalloc(size_t bytes) {
@@ -136,6 +150,10 @@ struct BatchState {
 
 struct PlanHolder : Plan {
     BatchState batch;
+    // grid-barrier settings of the PCG kernels: every solve waits for the launched blocks
+    // with a 2 s limit per wait; mm_pcg_barrier_check changes them for one run
+    unsigned bar_absent = 0;
+    unsigned long long bar_wait_ns = BARRIER_WAIT_NS;
     std::vector<mm_psd> h_psd;
     double* grad_H = nullptr;   // [3][npsd][N+1] derivative spectra (FP64 block)
     double* grad_u = nullptr;   // [nt] P mu
@@ -407,7 +425,10 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     }
     int dev = 0;
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    P.device = dev;
     check_cuda(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    // the no-allocation A x (mm_apply_A_static) finds its scratch address set up here
+    static_scratch_setup(dev);
 
     // --- host copies of the pointing
     std::vector<int32_t> hpix((size_t)nt);
@@ -635,6 +656,8 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
     a.scal = g.scal;
     a.flags = g.flags;
     a.bar = g.barrier;
+    a.bar_absent = P.bar_absent;
+    a.wait_ns = P.bar_wait_ns;
     a.hist_alpha = g.hist_alpha;
     a.hist_beta = g.hist_beta;
     a.hist_rz = g.hist_rz;
@@ -667,6 +690,8 @@ static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstor
     P.h_scal[0] = tol * tol;
     h2d(P.pcg.scal + SC_TOL2, P.h_scal, 8, s);
     const int nb = P.pcg.nblocks;
+    // a barrier that timed out keeps partial arrivals: start every run from zero
+    check_cuda(cudaMemsetAsync(P.pcg.barrier, 0, sizeof(unsigned), s), "memset barrier");
     launch_pcg<T>(0, P.ncomp, cm, a, nb, s);
     int launched = 0;
     int chunk = 4;
@@ -802,35 +827,64 @@ static void install_coarse(PlanHolder& P, double* Z, int k, std::vector<double> 
     P.coarse = cd;
 }
 
-// Orthonormalises the kc columns of Y (FP64 [kc][n], device) twice by Cholesky of the
-// Gram matrix (CholQR2), dropping in the first pass columns whose pivot is below 1e-10
-// of the largest kept one; Y is replaced, kc updated.
+// Orthonormalises the kc columns of Y (FP64 [kc][n], device) in order by classical
+// Gram-Schmidt with a second projection (CGS2) in FP64 on the device.  Reading R16 (the
+// paper is silent on dependent coarse columns, and E = Z^T A Z of Eq. 12 must be
+// invertible): column j is dropped when its part orthogonal to the columns kept before
+// it has norm below COARSE_DROP_RTOL times the largest column norm of Y.  Two
+// projections resolve that part to a few eps of the column's norm, so an exact
+// duplicate (~1e-16) is dropped and a near-duplicate 1e-9 away is kept.  Y is replaced
+// by the orthonormal columns (kept order), kc updated, *kept_out = the input columns
+// kept.  Non-finite columns: MM_ERR_NUMERIC.  Uses P.r64 and P.x64 as scratch.
+static constexpr double COARSE_DROP_RTOL = 1e-10;
 static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc, std::vector<int>* kept_out = nullptr) {
     cudaStream_t s = P.stream;
-    for (int pass = 0; pass < 2; ++pass) {
-        const std::vector<double> G = gram_host(P, Y, kc, Y, kc);
-        std::vector<double> W;
+    const int64_t n = P.n;
+    double scale = 0.0;
+    for (int j = 0; j < kc; ++j) {
+        const double nj = std::sqrt(dot64(P, Y + (size_t)j * n, Y + (size_t)j * n));
+        if (!std::isfinite(nj)) throw Error{MM_ERR_NUMERIC, "coarse vectors hold NaN or Inf"};
+        scale = std::max(scale, nj);
+    }
+    if (!(scale > 0.0)) throw Error{MM_ERR_NUMERIC, "coarse vectors are all zero"};
+    double* Q = nullptr;
+    double* hv = nullptr;
+    try {
+        Q = dalloc<double>((size_t)kc * n);
+        hv = dalloc<double>((size_t)kc);
+        double* v = P.r64;
+        double* t = P.x64;
         std::vector<int> kept;
-        if (!cholesky_drop(G, kc, pass == 0 ? 1e-10 : 0.0, W, kept) || kept.empty())
-            throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
-        if (pass == 0 && kept_out != nullptr) *kept_out = kept;   // the input columns kept
-        const int knew = (int)kept.size();
-        double* C = dalloc<double>(W.size());
-        double* Y2 = nullptr;
-        try {
-            h2d(C, W.data(), W.size() * 8, s);
-            Y2 = dalloc<double>((size_t)knew * P.n);
-            launch_lincomb<double>(Y, kc, P.n, C, knew, Y2, s);
-            sync(s);
-        } catch (...) {
-            dfree(C);
-            dfree(Y2);
-            throw;
+        for (int j = 0; j < kc; ++j) {
+            check_cuda(cudaMemcpyAsync(v, Y + (size_t)j * n, (size_t)n * 8, cudaMemcpyDeviceToDevice, s), "copy column");
+            const int q = (int)kept.size();
+            for (int pass = 0; q > 0 && pass < 2; ++pass) {
+                const std::vector<double> h = gram_host(P, Q, q, v, 1);
+                h2d(hv, h.data(), h.size() * 8, s);
+                launch_lincomb<double>(Q, q, n, hv, 1, t, s);
+                launch_sub(v, t, v, n, s);
+            }
+            const double piv = std::sqrt(dot64(P, v, v));
+            if (!std::isfinite(piv)) throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation produced NaN or Inf"};
+            if (!(piv > 0.0) || piv < COARSE_DROP_RTOL * scale) continue;
+            const double inv = 1.0 / piv;
+            h2d(hv, &inv, 8, s);
+            launch_lincomb<double>(v, 1, n, hv, 1, Q + (size_t)q * n, s);
+            sync(s);   // hv is rewritten by the next column
+            kept.push_back(j);
         }
-        dfree(C);
+        sync(s);
+        dfree(hv);
+        hv = nullptr;
+        if (kept.empty()) throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation kept no column"};
         dfree(Y);
-        Y = Y2;
-        kc = knew;
+        Y = Q;
+        kc = (int)kept.size();
+        if (kept_out != nullptr) *kept_out = kept;
+    } catch (...) {
+        dfree(Q);
+        dfree(hv);
+        throw;
     }
 }
 
@@ -840,8 +894,8 @@ static void orthonormalise_drop(PlanHolder& P, double*& Y, int& kc, std::vector<
 // re-orthogonalisation pass), until the GMRES residual min ||beta e_1 - Hbar y|| (Givens
 // updates on the host) is <= tol beta, maxit steps, or breakdown.  The Ritz pairs of H_m
 // (Eq. A.4) with |Re lambda| < eps_tol (Sec. 5), at most kmax, smallest Re first, give
-// y = W_m v (a complex pair: the real and imaginary parts of one member), then CholQR2
-// with dropping and the coarse operators.
+// y = W_m v (a complex pair: the real and imaginary parts of one member), then the
+// orthonormalisation with dropping (orthonormalise_drop) and the coarse operators.
 static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const double* bprime, double tol,
                                  int maxit) {
     cudaStream_t s = P.stream;
@@ -1017,9 +1071,9 @@ static void build_coarse_arnoldi(PlanHolder& P, int kmax, double eps_tol, const 
 // The a priori coarse space Z_S of Sec. 3.3.1 (Eq. 16-17) with its K interval columns
 // merged into r groups of consecutive intervals (interval i -> group floor(i r / K); a
 // merged column is the sum of its members, so observed temperature rows still sum to 1,
-// Q/U rows are 0), then replaced by an orthonormal basis of its range (CholQR2, columns
-// whose Gram-Cholesky pivot is below 1e-10 of the largest kept one dropped: intervals
-// that see the same hit fractions give equal columns).  M_2lvl depends on Z only through
+// Q/U rows are 0), then replaced by an orthonormal basis of its range (orthonormalise_drop:
+// intervals that see the same hit fractions give equal columns, which are dropped).
+// M_2lvl depends on Z only through
 // its range, and raw hit-fraction columns of a scan that covers the patch evenly are
 // nearly parallel, which leaves E = Z^T A Z numerically singular; the orthonormal basis
 // keeps E as well conditioned as A is on that range.
@@ -1059,7 +1113,6 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
     P.hist_runs.clear();
     T* zstore = static_cast<T*>(dmalloc((size_t)(maxit + 1) * P.n * sizeof(T)));
     double* Y = nullptr;
-    double* Y2 = nullptr;
     double* C = nullptr;
     try {
         const PcgOutcome o = run_pcg<T>(P, 0, tol, maxit, zstore, maxit + 1);
@@ -1109,31 +1162,14 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
         zstore = nullptr;
         dfree(C);
         C = nullptr;
-        // Euclidean orthonormalisation, twice (CholQR2); drop dependent columns first pass
+        // Euclidean orthonormalisation with dependent columns dropped (reading R16)
         int kcur = kk;
-        for (int pass = 0; pass < 2; ++pass) {
-            const std::vector<double> G = gram_host(P, Y, kcur, Y, kcur);
-            std::vector<double> W;
-            std::vector<int> kept;
-            if (!cholesky_drop(G, kcur, pass == 0 ? 1e-10 : 0.0, W, kept))
-                throw Error{MM_ERR_NUMERIC, "coarse orthonormalisation failed"};
-            const int knew = (int)kept.size();
-            if (pass == 0 && knew < kcur) {   // the reported Ritz values follow the kept columns
-                std::vector<double> th2;
-                for (int c : kept) th2.push_back(theta[(size_t)c]);
-                theta.swap(th2);
-            }
-            C = dalloc<double>(W.size());
-            h2d(C, W.data(), W.size() * 8, s);
-            Y2 = dalloc<double>((size_t)knew * P.n);
-            launch_lincomb<double>(Y, kcur, P.n, C, knew, Y2, s);
-            sync(s);
-            dfree(C);
-            C = nullptr;
-            dfree(Y);
-            Y = Y2;
-            Y2 = nullptr;
-            kcur = knew;
+        std::vector<int> kept;
+        orthonormalise_drop(P, Y, kcur, &kept);
+        if (kcur < kk) {   // the reported Ritz values follow the kept columns
+            std::vector<double> th2;
+            for (int c : kept) th2.push_back(theta[(size_t)c]);
+            theta.swap(th2);
         }
         double* Zk = Y;
         Y = nullptr;
@@ -1141,7 +1177,6 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
     } catch (...) {
         dfree(zstore);
         dfree(Y);
-        dfree(Y2);
         dfree(C);
         throw;
     }
@@ -1582,6 +1617,8 @@ static BatchPcgArgs batch_pcg_args(PlanHolder& P, int R, int maxit) {
     a.state = bt.state;
     a.flags = bt.flags;
     a.bar = bt.bar;
+    a.bar_absent = P.bar_absent;
+    a.wait_ns = P.bar_wait_ns;
     return a;
 }
 
@@ -1593,6 +1630,7 @@ static void run_batch_pcg(PlanHolder& P, int R, int maxit) {
     const BatchPcgArgs a = batch_pcg_args(P, R, maxit);
     check_cuda(cudaMemsetAsync(bt.flags, 0, 32, s), "memset flags");
     check_cuda(cudaMemsetAsync(bt.state, 0, BATCH_RMAX, s), "memset state");
+    check_cuda(cudaMemsetAsync(bt.bar, 0, sizeof(unsigned), s), "memset barrier");
     launch_batch_pcg(0, P.ncomp, a, bt.nblocks, s);
     constexpr int kChunk = 4;
     auto body = [&]() {
@@ -1787,6 +1825,13 @@ mm_status guarded(mm_plan_t plan, F&& f) {
     }
 }
 
+}  // namespace
+
+mm_status mm::run_guarded(Plan* P, void (*f)(void*), void* ctx) {
+    return guarded(reinterpret_cast<mm_plan_t>(static_cast<PlanHolder*>(P)), [&] { f(ctx); });
+}
+
+namespace {
 PlanHolder* get(mm_plan_t p) {
     if (p == nullptr) throw Error{MM_ERR_ARG, "null plan"};
     return reinterpret_cast<PlanHolder*>(p);
@@ -1952,6 +1997,7 @@ mm_status mm_precond(mm_plan_t plan, int kind, int precision, const void* r, voi
         const int cm = coarse_mode(kind);
         const bool two = cm != 0;
         if (two && P->coarse.k == 0) throw Error{MM_ERR_STATE, "two-level preconditioner needs mm_build_coarse"};
+        check_cuda(cudaMemsetAsync(P->pcg.barrier, 0, sizeof(unsigned), P->stream), "memset barrier");
         if (prec_ok(precision) == MM_FP64) {
             PcgArgs<double> a = pcg_args<double>(*P, two, 0);
             a.r = const_cast<double*>(static_cast<const double*>(r));
@@ -1994,13 +2040,15 @@ mm_status mm_coarse_import(mm_plan_t plan, const double* Z, int k) {
         PlanHolder* P = get(plan);
         if (Z == nullptr || k < 1 || k > KMAX) throw Error{MM_ERR_ARG, "need non-null Z and 1 <= k <= 64"};
         double* Zd = dalloc<double>((size_t)k * P->n);
+        int kc = k;
         try {
             check_cuda(cudaMemcpyAsync(Zd, Z, (size_t)k * P->n * 8, cudaMemcpyDefault, P->stream), "copy Z");
+            orthonormalise_drop(*P, Zd, kc);
         } catch (...) {
             dfree(Zd);
             throw;
         }
-        install_coarse(*P, Zd, k, {});
+        install_coarse(*P, Zd, kc, {});
     });
 }
 
@@ -2030,6 +2078,26 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z) {
         if (P->coarse.k == 0) throw Error{MM_ERR_STATE, "no coarse space"};
         if (Z == nullptr) throw Error{MM_ERR_ARG, "null output"};
         check_cuda(cudaMemcpy(Z, P->coarse.Z64, (size_t)P->coarse.k * P->n * 8, cudaMemcpyDefault), "copy Z");
+    });
+}
+
+mm_status mm_pcg_barrier_check(mm_plan_t plan, int32_t absent_blocks, double wait_s) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (absent_blocks < 0 || absent_blocks > 1024 || !(wait_s > 0.0) || !(wait_s <= 10.0))
+            throw Error{MM_ERR_ARG, "need 0 <= absent_blocks <= 1024 and 0 < wait_s <= 10"};
+        P->bar_absent = (unsigned)absent_blocks;
+        P->bar_wait_ns = (unsigned long long)(wait_s * 1e9);
+        try {
+            check_cuda(cudaMemsetAsync(P->pcg.r, 0, (size_t)P->n * 8, P->stream), "memset r");
+            (void)run_pcg<double>(*P, 0, 0.0, 1, nullptr, 0, 0);
+        } catch (...) {
+            P->bar_absent = 0;
+            P->bar_wait_ns = BARRIER_WAIT_NS;
+            throw;
+        }
+        P->bar_absent = 0;
+        P->bar_wait_ns = BARRIER_WAIT_NS;
     });
 }
 

@@ -203,12 +203,7 @@ static void launch_bt(const BatchTzArgs& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<float, LOGB>();
     const size_t smem = batch_toeplitz_smem(LOGB);
     auto kern = batch_toeplitz_kernel<LOGB, NT, NC>;
-    static bool attr = false;
-    if (!attr) {
-        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "cudaFuncSetAttribute(batch toeplitz)");
-        attr = true;
-    }
+    ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(batch toeplitz)");
     const int64_t grid = (int64_t)ntiles * ((A.R + 1) / 2);
     kern<<<(unsigned)grid, NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "batch toeplitz launch");
@@ -220,12 +215,7 @@ static void launch_bt_cl(const BatchTzArgs& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<float, LOGM>();
     const size_t smem = batch_toeplitz_smem(LOGM);
     auto kern = batch_toeplitz_cl_kernel<LOGM, NT, NC, CL>;
-    static bool attr = false;
-    if (!attr) {
-        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "cudaFuncSetAttribute(batch toeplitz cluster)");
-        attr = true;
-    }
+    ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(batch toeplitz cluster)");
     const int64_t grid = (int64_t)CL * ntiles * ((A.R + 1) / 2);
     kern<<<(unsigned)grid, NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "batch toeplitz cluster launch");
@@ -439,7 +429,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
         }
         batch_dots(a.r, a.r, a.n, e0, e1, R, prow, act);
         batch_dots(a.r, a.z, a.n, e0, e1, R, prow + BATCH_RMAX, act);
-        if (!grid_sync(a.bar, a.flags)) return;
+        if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
         batch_totals(a.partial, BATCH_PSTRIDE, 0, R, sh);
         batch_totals(a.partial, BATCH_PSTRIDE, BATCH_RMAX, R, sh2);
         if (blockIdx.x == 0) {
@@ -456,7 +446,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     }
     // phase A: alpha_r = rho_r / p_r^T q_r
     batch_dots(a.p, a.q, a.n, e0, e1, R, prow, act);
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     batch_totals(a.partial, BATCH_PSTRIDE, 0, R, sh);
     // phase B: x += alpha p, r -= alpha q (active RHS only; (RHS, element) pairs spread
     // over the threads); r^T r
@@ -475,7 +465,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     }
     __syncthreads();
     batch_dots(a.r, a.r, a.n, e0, e1, R, prow + BATCH_RMAX, act);
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     batch_totals(a.partial, BATCH_PSTRIDE, BATCH_RMAX, R, sh2);
     const int it = a.flags[F_ITER] + 1;
     // convergence per RHS (every block decides the same)
@@ -500,7 +490,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     batch_bd_all<NC>(a, p0, p1, R, act);
     __syncthreads();
     batch_dots(a.r, a.z, a.n, e0, e1, R, prow + 2 * BATCH_RMAX, act);
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     batch_totals(a.partial, BATCH_PSTRIDE, 2 * BATCH_RMAX, R, sh);
     bool any = false;
     for (int r = 0; r < R; ++r) any = any || act[r];
@@ -517,7 +507,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_pcg_kernel(BatchPcgArgs a
     }
     // every block has read rho and F_ITER above; block 0 publishes the new values after a
     // final barrier so no block can see them early
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     if (blockIdx.x == 0) {
         for (int r = threadIdx.x; r < R; r += blockDim.x) {
             if (act[r]) {

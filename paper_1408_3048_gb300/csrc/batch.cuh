@@ -47,6 +47,8 @@ struct BatchPcgArgs {
     unsigned char* state;      // [R] 0 running, 1 converged, 2 maxit, 3 breakdown
     int* flags;
     unsigned* bar;
+    unsigned bar_absent;           // 0 (see grid_sync)
+    unsigned long long wait_ns;    // limit of each barrier wait
 };
 
 size_t batch_toeplitz_smem(int logb);

@@ -2,8 +2,7 @@
 //   * the k smallest eigenpairs of the symmetric tridiagonal Lanczos matrix T_m, by
 //     Sturm-sequence bisection (eigenvalues) and inverse iteration with
 //     re-orthogonalisation inside clusters (eigenvectors);
-//   * Cholesky factorisation with column dropping (orthonormalisation of the Ritz
-//     vectors and the factor of the coarse operator E = Z^T A Z, App. C).
+//   * the Cholesky factor and inverses of the coarse operator E = Z^T A Z (App. C).
 #include <algorithm>
 #include <cmath>
 
@@ -122,58 +121,6 @@ void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e
         }
         for (int i = 0; i < m; ++i) S[(size_t)i * k + j] = x[i];
     }
-}
-
-// Cholesky G = R^T R (G k x k row-major, symmetric).  Column j is dropped (keep[j] =
-// false) when its pivot sqrt(g_jj - ...) is < drop_rtol * max kept pivot so far or
-// <= GRAM_RESOLUTION * sqrt(g_jj) (drop_rtol = 0: never drop; a non-positive pivot then
-// fails).  Returns the inverse factor Rinv restricted to kept columns as a k x kk matrix
-// W with Y_kept = Y W.
-static constexpr double GRAM_RESOLUTION = 1e-6;
-bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
-                   std::vector<int>& kept) {
-    std::vector<double> R((size_t)k * k, 0.0);   // upper, only kept rows/cols filled
-    kept.clear();
-    double maxpiv = 0.0;
-    for (int j = 0; j < k; ++j) {
-        // r_ij for kept i
-        std::vector<double> col(kept.size());
-        double s = G[(size_t)j * k + j];
-        for (size_t a = 0; a < kept.size(); ++a) {
-            const int i = kept[a];
-            double v = G[(size_t)i * k + j];
-            for (size_t b = 0; b < a; ++b) v -= R[(size_t)kept[b] * k + i] * col[b];
-            v /= R[(size_t)i * k + i];
-            col[a] = v;
-            s -= v * v;
-        }
-        const double piv = s > 0.0 ? std::sqrt(s) : 0.0;
-        // s = G_jj - sum v^2 carries a rounding error of a few k eps G_jj, so the Gram
-        // matrix resolves the orthogonal part of column j only down to ~sqrt(k eps) of the
-        // column's norm: below GRAM_RESOLUTION of its own norm it counts as dependent
-        // (an exact duplicate would otherwise survive on the sign of that rounding).
-        const double own = std::sqrt(std::max(G[(size_t)j * k + j], 0.0));
-        if (drop_rtol > 0.0 && (piv < drop_rtol * maxpiv || piv <= GRAM_RESOLUTION * own)) continue;
-        if (!(piv > 0.0)) return false;
-        for (size_t a = 0; a < kept.size(); ++a) R[(size_t)kept[a] * k + j] = col[a];
-        R[(size_t)j * k + j] = piv;
-        kept.push_back(j);
-        maxpiv = std::max(maxpiv, piv);
-    }
-    // W = R_kept^-1 (upper triangular inverse), as k x kk: W[i][c] for kept col c
-    const int kk = (int)kept.size();
-    W.assign((size_t)k * kk, 0.0);
-    for (int c = 0; c < kk; ++c) {
-        // solve R_kept w = e_c (upper triangular in kept indices)
-        std::vector<double> w(kk, 0.0);
-        for (int a = kk - 1; a >= 0; --a) {
-            double v = (a == c) ? 1.0 : 0.0;
-            for (int b = a + 1; b < kk; ++b) v -= R[(size_t)kept[a] * k + kept[b]] * w[b];
-            w[a] = v / R[(size_t)kept[a] * k + kept[a]];
-        }
-        for (int a = 0; a < kk; ++a) W[(size_t)kept[a] * kk + c] = w[a];
-    }
-    return true;
 }
 
 // Plain Cholesky E = L L^T (row-major lower); false when E is not positive definite.

@@ -13,12 +13,6 @@ namespace mm {
 void tridiag_smallest(const std::vector<double>& d, const std::vector<double>& e, int k,
                       std::vector<double>& theta, std::vector<double>& S);
 
-// Cholesky of a Gram matrix with column dropping (pivot < drop_rtol * largest kept pivot,
-// or <= 1e-6 of the column's own norm, the Gram matrix's resolution); W (k x kept) maps Y
-// to orthonormal Y W.
-bool cholesky_drop(const std::vector<double>& G, int k, double drop_rtol, std::vector<double>& W,
-                   std::vector<int>& kept);
-
 // E = L L^T, row-major lower L; false if E is not positive definite.
 bool cholesky_lower(const std::vector<double>& E, int k, std::vector<double>& L);
 // E^-1 (row-major, symmetric) from the lower Cholesky factor L of E: L^-T L^-1.

@@ -91,6 +91,7 @@ struct Plan {
     double fsamp = 100.0;
     double rcond_min = 1e-6;
     cudaStream_t stream = 0;
+    int device = 0;                // device current when the plan was made
     int num_sms = 0;
     int64_t L_grid = 0;
 
@@ -147,6 +148,18 @@ struct Error {
 };
 
 void check_cuda(cudaError_t e, const char* what);   // throws Error{MM_ERR_CUDA}
+// cudaFuncSetAttribute(kern, MaxDynamicSharedMemorySize, bytes) once per kernel and
+// device (thread-safe; the attribute is per device, so a second GPU gets its own call)
+void ensure_smem_attr(const void* kern, int bytes, const char* what);
+// Runs f and turns what it throws into a status: sets P->err (P may be null) and the
+// calling thread's last-error message (mm_last_error(NULL)).  Nothing leaves it.
+mm_status run_guarded(Plan* P, void (*f)(void*), void* ctx);
+// No-allocation scratch of mm_apply_A_static (apply_static.cu): looks up the device
+// address of the library's static array on the current device (called by mm_plan with
+// the plan's device current) and returns it / its size.
+void static_scratch_setup(int device);
+void* static_scratch_ptr(int device);
+size_t static_scratch_bytes();
 void note_launch(int kernels = 1);                   // process-wide kernel launch counter
 void* dmalloc(size_t bytes);                         // throws Error{MM_ERR_OOM}
 void dfree(void* p);

@@ -12,7 +12,8 @@
 // partials and summed by every block in block order after a grid barrier, so every block
 // sees the same scalars and the result is bit-reproducible.  The grid barrier is a
 // counter whose top bit flips once all blocks arrived; each wait is bounded in time
-// (2 s on the global timer), after which the kernel records MM_ERR_TIMEOUT and returns.
+// (a kernel argument, 2 s on the global timer in every solve), after which the kernel
+// records MM_ERR_TIMEOUT and returns.
 // The iteration count, stopping decision and scalar history live in device memory; the
 // host only polls a done flag every few iterations.
 #include "pcg.cuh"
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     const double bb = block_total(bacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RR] = bb;
     if constexpr (CM != 0) coarse_partials<T, 1>(a, a.r, e0, e1);
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     const double bbt = grid_total(a.partial, S_RR, sh);
     if constexpr (CM != 0) coarse_solve(a, v_sh);
     if constexpr (CM == 2) {
@@ -295,9 +296,9 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
         __syncthreads();   // bd_into_z reads whole pixels of r written element-wise above
         bd_into_z<T, NC>(a, p0, p1);
         // every block has read the first coarse partials before they are overwritten
-        if (!grid_sync(a.bar, a.flags)) return;
+        if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
         coarse_partials<T, 2>(a, a.r, e0, e1);
-        if (!grid_sync(a.bar, a.flags)) return;
+        if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
         coarse_solve(a, v_sh);
     }
     const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     }
     const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     const double rho = grid_total(a.partial, S_RZ, sh);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.scal[SC_RHO] = rho;
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
         __syncthreads();
         coarse_partials<T, 2>(a, a.r, e0, e1);
     }
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     const double rrt = grid_total(a.partial, S_RR, sh);
     const int it = a.flags[F_ITER] + 1;     // every block reads the same value here
     bool stop = false;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     }
     if (stop) {
         // every block has read F_ITER above; wait for all before block 0 updates it
-        if (!grid_sync(a.bar, a.flags)) return;
+        if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.flags[F_ITER] = it;
             a.scal[SC_RR] = rrt;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
     const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
-    if (!grid_sync(a.bar, a.flags)) return;
+    if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
     const double rzt = grid_total(a.partial, S_RZ, sh);
     const double beta = rzt / rho;
     const T be = (T)beta;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(PCG_THREADS) precond_kernel(PcgArgs<T> a) {
     }
     if constexpr (CM != 0) {
         coarse_partials<T, CM>(a, a.r, e0, e1);
-        if (!grid_sync(a.bar, a.flags)) return;
+        if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
         coarse_solve(a, v_sh);
     }
     (void)apply_precond<T, NC, CM>(a, v_sh, p0, p1);

@@ -37,6 +37,8 @@ struct PcgArgs {
     double* scal;
     int* flags;
     unsigned* bar;
+    unsigned bar_absent;           // 0 (diagnostic launches: blocks the barrier waits for in vain)
+    unsigned long long wait_ns;    // limit of each barrier wait
     double* hist_alpha;  // optional, [maxhist]
     double* hist_beta;
     double* hist_rz;
@@ -47,9 +49,12 @@ struct PcgArgs {
 };
 
 // Grid-wide barrier of a cooperative launch: a counter whose top bit flips once every
-// block arrived (block 0 adds 2^31 - (blocks - 1), the others 1).  Each wait is bounded
-// (2 s on the global timer); on timeout the block records MM_ERR_TIMEOUT, raises the done
-// flag and the caller returns.
+// block arrived (block 0 adds 2^31 - (blocks + absent - 1), the others 1; `absent` is 0
+// in every solve, a diagnostic launch sets it to make the barrier wait for blocks that
+// were never launched).  Each wait is bounded by wait_ns on the global timer (2 s in
+// every solve); on timeout the block records MM_ERR_TIMEOUT, raises the done flag and the
+// caller returns.  A timed-out barrier keeps partial arrivals in its counter: the host
+// zeroes the counter before every launch sequence.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -63,18 +68,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Returns false when this block gave up waiting (timeout recorded in flags).
-__device__ __forceinline__ bool grid_sync(unsigned* bar, int* flags) {
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* flags, unsigned absent, unsigned long long wait_ns) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        const unsigned nb = gridDim.x;
+        const unsigned nb = gridDim.x + absent;
         const unsigned inc = blockIdx.x == 0 ? (0x80000000u - (nb - 1u)) : 1u;
         __threadfence();
         const unsigned old = atomicAdd(bar, inc);
         const unsigned long long t0 = global_ns();
         while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0u) {
-            if (global_ns() - t0 > 2000000000ull) {
+            if (global_ns() - t0 > wait_ns) {
                 atomicExch(&flags[F_STATUS], (int)MM_ERR_TIMEOUT);
                 atomicExch(&flags[F_DONE], 1);
                 ok = 0;
@@ -87,6 +92,8 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* flags) {
     __syncthreads();
     return ok != 0;
 }
+
+constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;   // per wait, every solve
 
 // Dot-product accumulator of one thread.  FP64 vectors: plain FP64 FMAs.  FP32 vectors:
 // each product a b is formed exactly as p + e (p = fl(a b), e = fma(a, b, -p)) and

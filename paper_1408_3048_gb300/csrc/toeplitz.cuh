@@ -570,12 +570,7 @@ void launch_cl(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<T, LOGM>();
     const size_t smem = toeplitz2_smem_bytes_impl<T>(LOGM);
     auto kern = toeplitz_oscl_kernel<T, LOGM, NT, MODE, CL>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "cudaFuncSetAttribute(toeplitz cluster)");
-        attr_set = true;
-    }
+    ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(toeplitz cluster)");
     kern<<<(unsigned)((int64_t)CL * ntiles * A.R), NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz cluster kernel launch");
     note_launch();
@@ -609,12 +604,7 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<T, LOGN>();
     const size_t smem = toeplitz_smem_bytes_impl<T>(LOGN);
     auto kern = toeplitz_os_kernel<T, LOGN, NT, MODE>;
-    static bool attr_set = false;   // per instantiation; set once per process
-    if (!attr_set) {
-        check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "cudaFuncSetAttribute(toeplitz)");
-        attr_set = true;
-    }
+    ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(toeplitz)");
     kern<<<(unsigned)((int64_t)ntiles * A.R), NT, smem, s>>>(A);
     check_cuda(cudaGetLastError(), "toeplitz kernel launch");
     note_launch();

@@ -31,7 +31,8 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_coarse_vectors", "mm_solve", "mm_profile", "mm_profile_read", "mm_last_error", "mm_destroy",
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
            "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
-           "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi", "mm_solve_history"]
+           "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi", "mm_solve_history",
+           "mm_pcg_barrier_check"]
 
 
 class mm_psd(ctypes.Structure):
@@ -102,6 +103,7 @@ _SIGS = {
     "mm_profile": (I32, [P, ctypes.c_int]),
     "mm_profile_read": (I32, [P, P, P]),
     "mm_solve_history": (I32, [P, I32, P, P]),
+    "mm_pcg_barrier_check": (I32, [P, I32, ctypes.c_double]),
     "mm_last_error": (ctypes.c_char_p, [P]),
     "mm_destroy": (None, [P]),
     "mm_version": (ctypes.c_char_p, []),
@@ -314,6 +316,12 @@ def mm_solve_history(plan):
     return h[: cnt.value]
 
 
+def mm_pcg_barrier_check(plan, absent_blocks, wait_s):
+    """Status of a PCG start whose grid barrier waits for `absent_blocks` blocks that are
+    never launched, each wait limited to wait_s seconds (MM_ERR_TIMEOUT when > 0)."""
+    return int(lib().mm_pcg_barrier_check(plan, int(absent_blocks), float(wait_s)))
+
+
 def mm_solve_ex(plan, d, opts, m, raise_on_error=True):
     st = mm_stats()
     status = lib().mm_solve_ex(plan, _ptr(d), ctypes.byref(opts), _ptr(m), ctypes.byref(st))
@@ -383,6 +391,7 @@ class Plan:
         self.ncomp = ncomp
         self.lam = int(lam)
         self.npsd = len(ps)
+        self.psds = ps.copy()     # (sigma, fknee, alpha) per PSD id, as the plan was built
 
     # helpers
     def _dtype(self, precision):
@@ -562,6 +571,11 @@ class Plan:
         """Relative recursive residual after each A p of the last solve (Sec. 5.1)."""
         return mm_solve_history(self.handle)
 
+    def barrier_check(self, absent_blocks, wait_s):
+        """Status (int) of the bounded-wait diagnostic mm_pcg_barrier_check."""
+        self._sync_in()
+        return mm_pcg_barrier_check(self.handle, absent_blocks, wait_s)
+
     def profile_read(self):
         """{stage: (total ms, launches)} per kernel and precision."""
         ms, n = mm_profile_read(self.handle)
@@ -587,11 +601,18 @@ def map_solve(plan, d, theta, tol=1e-10, maxit=10000, kind=MM_PREC_BD, solver=MM
 
     d      cuda float64 tensor [nt] (time-ordered data)
     theta  float64 tensor [npsd, 3] = (sigma, fknee, alpha) per PSD id; it must equal the
-           plan's PSDs (the plan was built from them) and only carries their gradient.
+           plan's PSDs (plan.psds, the values the plan was built from: ValueError
+           otherwise) and only carries their gradient.
     The backward pass runs one adjoint PCG solve (A is symmetric) and the PSD gradient
     products of mm_grad; no Krylov vectors are kept from the forward solve.
     """
     import torch
+
+    th = theta.detach().cpu().numpy().astype(np.float64).reshape(-1, 3)
+    ps = np.asarray(plan.psds, dtype=np.float64).reshape(-1, 3)
+    if th.shape != ps.shape or not np.array_equal(th, ps):
+        raise ValueError("theta must equal the PSD parameters the plan was built from (plan.psds); "
+                         "build a new plan for other noise parameters")
 
     class _MapSolve(torch.autograd.Function):
         @staticmethod

@@ -18,6 +18,7 @@ class OraclePlan:
 
     def __init__(self, pr):
         self.pr = pr
+        self.psds = np.array(pr.psds, dtype=np.float64)
         self.calls = []
 
     def solve(self, d, tol=1e-6, maxit=1000, kind=mm.MM_PREC_BD, solver=mm.MM_SOLVE_FP64, **kw):
@@ -62,3 +63,13 @@ def test_map_solve_skips_unneeded_gradients():
     # d/dd of sum(m) = N^-1 P A^-1 1: the adjoint with g = ones
     ref = pr.Ninv(pr.P(dense_solve(pr.dense_A(), np.ones(pr.n))))
     np.testing.assert_allclose(gd.numpy(), ref, rtol=1e-10, atol=1e-12)
+
+
+def test_map_solve_rejects_theta_other_than_the_plans():
+    scan = tiny_scan(ncomp=1, psds=((1.0, 1.0, 1.3),), lam=6)
+    plan = OraclePlan(oracle_problem(scan))
+    d = torch.zeros(plan.pr.nt, dtype=torch.float64)
+    for bad in ([[1.0, 1.0, 1.4]], [[1.0, 1.0, 1.3], [1.0, 1.0, 1.3]]):
+        with pytest.raises(ValueError):
+            mm.map_solve(plan, d, torch.tensor(bad, dtype=torch.float64))
+    assert plan.calls == []

@@ -273,6 +273,44 @@ def test_coarse_threshold_and_import(case):
     other.close()
 
 
+def test_coarse_import_drops_dependent_columns():
+    # reading R16 in the library against the oracle's rule: an imported basis is
+    # orthonormalised in order and a column whose part orthogonal to the kept ones is
+    # below 1e-10 of the largest column norm is dropped.  Exact duplicates, scaled copies,
+    # combinations and zero columns go; a near-duplicate 1e-9 away stays, one 1e-11 away
+    # goes; the kept basis spans the oracle's kept columns.
+    scan = tiny_scan(ncomp=3)
+    pr = oracle_problem(scan)
+    plan = _plan(scan)
+    rng = np.random.default_rng(4)
+    Y = rng.standard_normal((pr.n, 9))
+    Y[:, 2] = Y[:, 0]
+    Y[:, 3] = -3.0 * Y[:, 1]
+    Y[:, 4] = Y[:, 0] - 2.0 * Y[:, 1]
+    Y[:, 5] = 0.0
+    u = rng.standard_normal(pr.n)
+    u /= np.linalg.norm(u)
+    Y[:, 6] = Y[:, 1] + 1e-9 * np.linalg.norm(Y[:, 1]) * u
+    Y[:, 7] = Y[:, 0] + 1e-11 * np.linalg.norm(Y[:, 0]) * u
+    Yo, kept = oprec.independent_columns(Y)
+    assert kept == [0, 1, 6, 8]
+    assert plan.coarse_import(Y) == len(kept)
+    Zl = plan.coarse_vectors()
+    np.testing.assert_allclose(Zl.T @ Zl, np.eye(len(kept)), atol=1e-12)
+    assert np.linalg.norm(Yo - Zl @ (Zl.T @ Yo)) <= 1e-12 * np.linalg.norm(Yo)
+    # the space acts as the oracle's M_2lvl on the same range
+    tl = oprec.TwoLevel(pr, oprec.BlockJacobi(pr), oprec.orthonormal_basis(Y)[0])
+    r = rng.standard_normal(pr.n)
+    assert _rel(plan.precond(_cuda(r), mm.MM_PREC_TWOLEVEL, mm.MM_FP64).cpu().numpy(), tl.apply(r)) <= 1e-9
+    # non-finite columns are reported and the previous space stays
+    Y[3, 4] = np.nan
+    with pytest.raises(mm.MMError) as e:
+        plan.coarse_import(Y)
+    assert e.value.status == mm.MM_ERR_NUMERIC
+    assert plan.coarse_vectors().shape[1] == len(kept)
+    plan.close()
+
+
 def test_coarse_arnoldi(case):
     # the paper's Ritz source (Algorithm 1 on M_BD A) with eps_tol selection
     name, scan, pr, plan = case

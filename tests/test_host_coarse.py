@@ -1,9 +1,9 @@
 """Host dense algebra of the coarse space (csrc/coarse_host.cpp, plain C++, no GPU) on the
 CPU: the k smallest eigenpairs of a symmetric tridiagonal (the Lanczos T_m of Sec. 3.3.2)
-against LAPACK, the Gram-matrix orthonormalisation with column dropping against the
-oracle's Gram-Schmidt rule (reading R16), and the Cholesky factor, the SPD inverse and
-the pivoted Gauss-Jordan inverse of the coarse operator E = Z^T A Z (Eq. 12, App. C)
-against numpy.  Compiled here with g++."""
+against LAPACK, and the Cholesky factor, the SPD inverse and the pivoted Gauss-Jordan
+inverse of the coarse operator E = Z^T A Z (Eq. 12, App. C) against numpy.  Compiled
+here with g++.  (The orthonormalisation with column dropping runs on the device; its
+GPU test is in test_gpu_parity.py.)"""
 import os
 import shutil
 import subprocess
@@ -32,16 +32,7 @@ int main() {
     char cmd[16];
     int k;
     if (std::scanf("%15s %d", cmd, &k) != 2) return 2;
-    if (!std::strcmp(cmd, "drop")) {
-        double rtol;
-        if (std::scanf("%lf", &rtol) != 1) return 2;
-        std::vector<double> W;
-        std::vector<int> kept;
-        const bool ok = mm::cholesky_drop(read_vec((size_t)k * k), k, rtol, W, kept);
-        std::printf("%d\n%zu\n", ok ? 1 : 0, kept.size());
-        for (int i : kept) std::printf("%d\n", i);
-        put(W);
-    } else if (!std::strcmp(cmd, "tri")) {
+    if (!std::strcmp(cmd, "tri")) {
         int m;
         if (std::scanf("%d", &m) != 1) return 2;
         const std::vector<double> d = read_vec((size_t)m), e = read_vec((size_t)(m - 1));
@@ -84,53 +75,6 @@ def host(tmp_path_factory):
         out = subprocess.run([str(exe)], input=txt, capture_output=True, text=True, check=True).stdout
         return np.array(out.split(), dtype=np.float64)
     return call
-
-
-def _drop(host, Y, rtol=1e-10):
-    k = Y.shape[1]
-    out = host(f"drop {k} {rtol}", Y.T @ Y)
-    ok, kk = int(out[0]), int(out[1])
-    kept = [int(v) for v in out[2:2 + kk]]
-    W = out[2 + kk:].reshape(k, kk) if ok else None   # no factor after a failure
-    return ok, kept, W
-
-
-@pytest.mark.parametrize("seed", range(6))
-def test_dropping_matches_the_oracle_on_dependent_columns(host, seed):
-    """Exact duplicates and combinations are dropped (both by the library's Gram route and
-    the oracle's Gram-Schmidt), whatever the sign of the rounding in the Gram pivot;
-    columns with a clear orthogonal part are kept; Y W is orthonormal."""
-    rng = np.random.default_rng(seed)
-    Y = rng.standard_normal((60, 8))
-    Y[:, 3] = Y[:, 1]
-    Y[:, 5] = 2.0 * Y[:, 0] - Y[:, 2]
-    Y[:, 6] = 3.0 * Y[:, 4] + 1e-9 * rng.standard_normal(60)   # below resolution: dependent
-    Y[:, 7] = Y[:, 2] + 1e-3 * rng.standard_normal(60)          # clearly independent
-    ok, kept, W = _drop(host, Y)
-    _, kept_or = precond.independent_columns(Y)
-    assert ok == 1 and kept == kept_or == [0, 1, 2, 4, 7]
-    Q = Y @ W
-    # one Gram-route pass leaves ~kappa^2 eps; the library runs a second pass (CholQR2)
-    assert np.abs(Q.T @ Q - np.eye(len(kept))).max() <= 1e-4
-    ok2, kept2, W2 = _drop(host, Q, 0.0)
-    Q2 = Q @ W2
-    assert ok2 == 1 and kept2 == list(range(len(kept)))
-    np.testing.assert_allclose(Q2.T @ Q2, np.eye(len(kept)), atol=1e-12)
-    # the basis spans the kept columns
-    Yk = Y[:, kept]
-    assert np.linalg.norm(Yk - Q2 @ (Q2.T @ Yk)) <= 1e-10 * np.linalg.norm(Yk)
-
-
-def test_dropping_zero_and_scaled_columns(host):
-    rng = np.random.default_rng(9)
-    Y = rng.standard_normal((20, 4))
-    Y[:, 1] = 0.0
-    Y[:, 3] = 1e-12 * rng.standard_normal(20)    # tiny but independent: below 1e-10 of the largest
-    ok, kept, _ = _drop(host, Y)
-    assert ok == 1 and kept == precond.independent_columns(Y)[1] == [0, 2]
-    # without dropping a zero column is a failure, not a silent NaN
-    ok, _, _ = _drop(host, Y, 0.0)
-    assert ok == 0
 
 
 @pytest.mark.parametrize("m,k", [(1, 1), (5, 3), (40, 8), (120, 32)])

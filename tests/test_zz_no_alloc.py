@@ -2,8 +2,15 @@
 (their GPU memory is reserved by a pool they do not own, or the call sits on a path
 where a cudaMalloc could fail or stall).  It keeps the time-domain intermediate in a
 fixed 32 MiB array inside the library.  Checked through the C-ABI against mm_apply_A
-on two calls in a row (the array keeps the previous call's contents), in FP64 and FP32,
-plus the size limit.  Needs a GPU; this file is collected last on purpose.
+on two calls in a row (the array keeps the previous call's contents), in FP64 and FP32;
+after a call by a plan with more samples, a plan with fewer samples gets its own result
+(it never reads entries the larger one left); the device's free memory is the same
+before and after a call; sizes beyond the array are rejected.  Needs a GPU.
+
+The file name makes pytest collect it last, so that a run which stops at its first
+failure (pytest -x) has run every other test before this one.  The tests themselves do
+not depend on that order: each makes its own plans, and they pass alone in a fresh
+process too.
 """
 import numpy as np
 import pytest
@@ -20,22 +27,50 @@ def _plan(scan):
                    scan.lam, scan.fsamp)
 
 
+def _scan(ncomp, nper=24000, seed=5):
+    return synth.raster_scan(24, 24, 4, nper, ncomp, 4, 500, [(1.0, 1.0, 1.0), (0.8, 1.5, 1.5)],
+                             det_psd=[0, 1, 0, 1], uneven=(3000, 9000), seed=seed)
+
+
+def _check(plan, prec, rng):
+    """mm_apply_A_static against mm_apply_A on one random x; returns the relative error
+    and the change of the device's free memory across the static call."""
+    dt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+    x = torch.as_tensor(rng.standard_normal(plan.n), dtype=dt).cuda()
+    ref = torch.empty(plan.n, dtype=dt, device="cuda")
+    out = torch.full((plan.n,), float("nan"), dtype=dt, device="cuda")
+    mm.mm_apply_A(plan.handle, prec, x, ref)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    mm.mm_apply_A_static(plan.handle, prec, x, out)
+    free1 = torch.cuda.mem_get_info()[0]
+    err = float(torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double()))
+    return err, free0 - free1
+
+
 @pytest.mark.parametrize("ncomp", [1, 3])
 def test_static_matches_apply_A_twice(ncomp):
-    scan = synth.raster_scan(24, 24, 4, 24000, ncomp, 4, 500, [(1.0, 1.0, 1.0), (0.8, 1.5, 1.5)],
-                             det_psd=[0, 1, 0, 1], uneven=(3000, 9000), seed=5)
-    plan = _plan(scan)
+    plan = _plan(_scan(ncomp))
     rng = np.random.default_rng(11)
-    for prec, dt, tol in ((mm.MM_FP64, torch.float64, 1e-12), (mm.MM_FP32, torch.float32, 3e-5)):
-        for call in range(2):   # second call runs on the array the first one left behind
-            x = torch.as_tensor(rng.standard_normal(plan.n), dtype=dt).cuda()
-            ref = torch.empty(plan.n, dtype=dt, device="cuda")
-            out = torch.full((plan.n,), float("nan"), dtype=dt, device="cuda")
-            mm.mm_apply_A(plan.handle, prec, x, ref)
-            mm.mm_apply_A_static(plan.handle, prec, x, out)
-            err = float(torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double()))
+    for prec, tol in ((mm.MM_FP64, 1e-12), (mm.MM_FP32, 3e-5)):
+        for call in range(2):   # the second call runs on the array the first one left behind
+            err, dfree = _check(plan, prec, rng)
             assert err <= tol, (prec, call, err)
+            assert dfree == 0, (prec, call, dfree)
     plan.close()
+
+
+def test_static_smaller_plan_after_larger_one():
+    big = _plan(_scan(3, nper=60000, seed=8))
+    small = _plan(_scan(3, nper=9000, seed=9))
+    assert big.nt > 4 * small.nt
+    rng = np.random.default_rng(12)
+    for prec, tol in ((mm.MM_FP64, 1e-12), (mm.MM_FP32, 3e-5)):
+        for plan in (big, small, big, small):
+            err, dfree = _check(plan, prec, rng)
+            assert err <= tol and dfree == 0, (prec, plan.nt, err, dfree)
+    big.close()
+    small.close()
 
 
 def test_static_rejects_sizes_beyond_the_array():
@@ -48,10 +83,10 @@ def test_static_rejects_sizes_beyond_the_array():
         mm.mm_apply_A_static(plan.handle, mm.MM_FP64, x, y)
     assert e.value.status == mm.MM_ERR_ARG and "static" in str(e.value)
     # FP32 needs half the bytes and fits
-    x32 = torch.ones(plan.n, dtype=torch.float32, device="cuda")
-    ref = torch.empty_like(x32)
-    out = torch.empty_like(x32)
-    mm.mm_apply_A(plan.handle, mm.MM_FP32, x32, ref)
-    mm.mm_apply_A_static(plan.handle, mm.MM_FP32, x32, out)
-    assert float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref)) <= 3e-5
+    err, dfree = _check(plan, mm.MM_FP32, np.random.default_rng(13))
+    assert err <= 3e-5 and dfree == 0
     plan.close()
+
+
+def test_static_null_plan_is_an_argument_error():
+    assert mm.lib().mm_apply_A_static(None, mm.MM_FP64, None, None) == mm.MM_ERR_ARG
