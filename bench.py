@@ -39,6 +39,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
 WORKLOAD = ("polarised I/Q/U raster, 256x256 patch, 16 detectors x 2^20 = 2^24 samples, 256 uneven "
             "intervals, 1/f noise fknee U[0.1,2] Hz alpha U[1,2], lambda=4096, tol 1e-6, two-level k=32")
 METRIC = "time-to-solution @1e-6 resid (2-level mixed vs FP64 BJ, 1 GPU); A·x HBM GB/s"
+ARITHMETIC = ("mixed solve: FP32 gather, Toeplitz N^-1, scatter and PCG vectors; CG dot products as "
+              "double-float FP32 pairs (~48-bit significand, not FP64); FP64 step scalars, FP64 E^-1 and "
+              "FP64 iterative-refinement residual P^T N^-1 (d - P m)")
+# bandwidth and knee-frequency cases of the secondary sweep (the paper's Sec. 5 studies)
+SWEEP_CASES = [(1024, 1.0), (4096, 1.0), (16384, 1.0), (4096, 0.25), (4096, 4.0)]
+BATCH_R = 64
 L2_NOTE = "inputs larger than L2 (d 134 MB, pointing 335 MB)"
 
 
@@ -49,6 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements after the timed region (coarse-space variants, "
+                         "bandwidth / knee sweep, batched right-hand sides)")
     ap.add_argument("--sweep", action="store_true",
                     help="iteration counts of block-Jacobi and two-level PCG over Toeplitz bandwidths "
                          "and knee frequencies on the 2^24-sample workload (one JSON line per case; no "
@@ -178,17 +187,25 @@ def recorded_traffic(kernel):
     return None, "no ncu capture recorded"
 
 
+def ax_bytes(plan, s):
+    """Algorithmic bytes of one A x (Eq. 8) at s bytes per value: pointing (4 B index) and
+    weights (2 s, I/Q/U) per sample, x read and y written (n s each).  Time-domain
+    intermediates are excluded: a fully fused A x never writes them."""
+    return plan.nt * (4 + (2 * s if plan.ncomp == 3 else 0)) + 2 * plan.n * s
+
+
 def roofline(kernel, ms, plan, scan, hbm, peak_src):
     """Algorithmic bytes and flops of one launch of `kernel` over its measured duration;
-    the bound is whichever of HBM or ALU the launch uses the larger fraction of."""
+    the bound is whichever of HBM or ALU the launch uses the larger fraction of.  The
+    Toeplitz and scatter kernels are the two launches of one A x: each is charged the
+    algorithmic bytes of the whole A x (the stage it belongs to), so their fractions are
+    the fraction of the A x roofline they would reach if they were the whole A x."""
     nt, n = plan.nt, plan.n
     key = "f32" if kernel.endswith("f32") else "f64"
     s = 4 if key == "f32" else 8
-    w = 2 * s if plan.ncomp == 3 else 0
     flops = None
     if kernel.startswith("toeplitz"):
-        # pointing (4 B) + weights read, time-domain output written per sample; map read
-        byts = nt * (4 + w + s) + n * s
+        byts = ax_bytes(plan, s)
         B = plan.fft_block_f32 if key == "f32" else plan.fft_block_f64
         N = B // 2
         tiles = fft_tiles(scan, B)
@@ -196,7 +213,7 @@ def roofline(kernel, ms, plan, scan, hbm, peak_src):
         # product (20 N), I/Q/U de-pointing (2 FMA per sample)
         flops = tiles * (2 * 5 * N * np.log2(N) + 20 * N) + (4 * nt if plan.ncomp == 3 else 0)
     elif kernel.startswith("scatter"):
-        byts = nt * (4 + w + s) + n * s
+        byts = ax_bytes(plan, s)
     else:
         byts = 8 * n * s
     t = ms * 1e-3
@@ -249,7 +266,7 @@ A = lambda x: pr.A(x, route="fft")
 def m2(r):
     v = scipy.linalg.lu_solve(lu, Z.T @ r)
     return bd.apply(r - AZ @ v) + Z @ v
-out = []
+out, samples = [], []
 for s in range(steps):
     t0 = time.perf_counter()
     b = pr.rhs(d, route="fft")
@@ -258,20 +275,25 @@ for s in range(steps):
     t2 = time.perf_counter()
     per_it = (t2 - t1) / {sample_iters}
     out.append((t1 - t0) + iters * per_it)
-print(json.dumps({{"values": out, "t_plan": t_plan, "per_iter": per_it, "rhs": t1 - t0}}))
+    samples.append(t2 - t0)
+print(json.dumps({{"values": out, "samples": samples, "t_plan": t_plan, "per_iter": per_it, "rhs": t1 - t0}}))
 """
 
 
 def oracle_time_to_solution(steps, iters, sample_iters=2):
-    """Run the oracle in a fresh single-threaded process; return (values, info)."""
+    """Run the oracle, as it stands, in a fresh process on the host cores; each step times
+    b = P^T N^-1 d and `sample_iters` two-level PCG iterations of the full workload and
+    extrapolates to `iters` iterations.  Returns (extrapolated values, info)."""
     code = ORACLE_SNIPPET.format(root=ROOT, steps=steps, iters=iters, cfg=CONFIG, sky_seed=1000 + CONFIG,
                                  noise_seed=2000 + 100 * CONFIG + 1, k=K_COARSE, sample_iters=sample_iters)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     j = json.loads(r.stdout.strip().splitlines()[-1])
+    j["threads"] = os.cpu_count() or 1
+    j["sample_iters"] = sample_iters
+    j["sample_s"] = float(np.mean(j["samples"]))
     return j["values"], j
 
 
@@ -284,8 +306,25 @@ def oracle_iterations():
     return None, None, None
 
 
+GOLDEN_MAPS = os.path.join(ROOT, "tests", "golden", "c2_maps.npz")
+
+
+def oracle_map():
+    """The oracle's converged map m* (block-Jacobi PCG to 1e-10) of the bench's data, as
+    written by tests/golden/make_c2_oracle.py (same scan, sky seed 1002, noise seed 2201),
+    or None."""
+    if not os.path.exists(GOLDEN_MAPS):
+        return None
+    with np.load(GOLDEN_MAPS) as z:
+        return z["m_star"]
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 oracle on the host cores.  Each of the W + K steps is a
+    bounded sample of the workload (b plus two two-level PCG iterations); ms_per_step is
+    the measured time of one such sample, `value` the time-to-solution it extrapolates to
+    (the oracle's own two-level iteration count)."""
     if rank != 0:
         return
     iters, src, g = oracle_iterations()
@@ -294,16 +333,21 @@ def run_reference(a, rank, world):
         return
     vals, info = oracle_time_to_solution(a.warmup + a.steps, iters)
     v = float(np.mean(vals[a.warmup:]))
+    sample_ms = float(np.mean(info["samples"][a.warmup:])) * 1e3
     line = {
         "impl": "reference", "metric": METRIC,
         "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": sample_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
+        "value_is": (f"time-to-solution extrapolated from each step's measured sample (b = P^T N^-1 d plus "
+                     f"{info['sample_iters']} two-level PCG iterations, {sample_ms / 1e3:.2f} s) to {iters} "
+                     f"iterations ({src}); ms_per_step is the sample's measured time"),
         "config": {"workload": WORKLOAD, "nt": 1 << 24, "n": int(g["n"]), "npix_obs": int(g["npix_obs"]),
                    "k_kept": int(g["k_kept"]), "l2": L2_NOTE, "parallelism": "one host process (FP64 oracle)"},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: b = P^T N^-1 d plus 2 two-level PCG iterations of the full "
-                                   f"workload, extrapolated to {iters} iterations ({src})"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": info["threads"], "kind": "oracle",
+                         "sample": f"per step: b = P^T N^-1 d plus {info['sample_iters']} two-level PCG "
+                                   f"iterations of the full workload (FP64 NumPy/SciPy; FFTs on one thread, BLAS "
+                                   f"on {info['threads']}), extrapolated to {iters} iterations ({src})"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -325,6 +369,50 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+class PlanInfo:
+    """The plan figures the roofline needs, kept after the plan is closed."""
+
+    def __init__(self, nt, n, ncomp, fft_block_f32, fft_block_f64):
+        self.nt, self.n, self.ncomp = nt, n, ncomp
+        self.fft_block_f32, self.fft_block_f64 = fft_block_f32, fft_block_f64
+
+
+def coarse_variants(plan, b0, dc1, m):
+    """The paper's other coarse spaces on the bench data (each replaces the previous one):
+    the a priori Z_S merged into 32 interval groups (Sec. 3.3.1), the Arnoldi (Algorithm 1)
+    and CG-Lanczos a posteriori spaces keeping the Ritz values below eps_tol = 0.2 (Sec. 5),
+    and the A-DEF2 form (App. B) on the last one."""
+    import torch
+    from paper_1408_3048_gb300 import mm
+    out = {}
+    for name, build in (("apriori_r32", lambda: plan.build_coarse_apriori(K_COARSE)),
+                        ("arnoldi_eps0.2", lambda: plan.build_coarse_arnoldi(
+                            0.2, 64, bprime=b0, tol=TOL, maxit=400)[0]),
+                        ("aposteriori_eps0.2", lambda: plan.build_coarse_eps(
+                            0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)[0])):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        try:
+            kc = build()
+        except mm.MMError as e:
+            out[name] = {"error": str(e)}
+            continue
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t
+        _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
+        _, smx, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, out=m)
+        out[name] = {"k": kc, "build_s": round(tb, 4), "fp64_s": s64["ms_total"] / 1e3,
+                     "fp64_iters": s64["iters"], "mixed_s": smx["ms_total"] / 1e3,
+                     "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
+    if "error" not in out.get("aposteriori_eps0.2", {"error": 1}):
+        _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_FP64, out=m)
+        _, smx, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_MIXED, out=m)
+        out["aposteriori_eps0.2_adef2"] = {
+            "k": out["aposteriori_eps0.2"]["k"], "fp64_s": s64["ms_total"] / 1e3, "fp64_iters": s64["iters"],
+            "mixed_s": smx["ms_total"] / 1e3, "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
+    return out
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     from paper_1408_3048_gb300 import mm
@@ -334,6 +422,7 @@ def run_ours(a, rank, world, local_rank):
     scan, (d0, d1) = make_inputs(replica_realisations(rank))
     plan = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, scan.psds,
                    scan.lam, scan.fsamp, stream=stream)
+    pinfo = PlanInfo(plan.nt, plan.n, plan.ncomp, plan.fft_block_f32, plan.fft_block_f64)
     dc0 = torch.from_numpy(d0).to(dev)
     dc1 = torch.from_numpy(d1).to(dev)
     m = torch.empty(plan.n, dtype=torch.float64, device=dev)
@@ -367,10 +456,33 @@ def run_ours(a, rank, world, local_rank):
         plan.close()
         return
 
-    # FP64 block-Jacobi and FP64 two-level references (one solve each)
-    _, st_bj, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_BD, mm.MM_SOLVE_FP64, out=m)
-    _, st_2f, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
-    m_ref64 = m.clone()
+    # maps compared: the oracle's converged map of this data (rank 0's realisation) and a
+    # converged FP64 GPU map (two-level, 1e-10)
+    mstar = oracle_map() if rank == 0 else None
+    mstar_t = torch.from_numpy(mstar).to(dev) if mstar is not None and mstar.size == plan.n else None
+    _, st_ref, _ = plan.solve(dc1, 1e-10, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
+    m_conv = m.clone()
+
+    def errs(x):
+        e = {"vs_fp64_gpu_1e-10": float(torch.linalg.norm(x - m_conv) / torch.linalg.norm(m_conv))}
+        if mstar_t is not None:
+            e["vs_oracle_1e-10"] = float(torch.linalg.norm(x - mstar_t) / torch.linalg.norm(mstar_t))
+        return e
+
+    def solve_rec(tol, kind, solver):
+        _, st_, _ = plan.solve(dc1, tol, 20000, kind, solver, out=m)
+        rec = {"s": st_["ms_total"] / 1e3, "iters": st_["iters"], "rel_resid": st_["rel_resid"],
+               "map_rel_err": errs(m)}
+        if solver == mm.MM_SOLVE_MIXED:
+            rec["outer"] = st_["outer"]
+        return rec
+
+    # FP64 block-Jacobi (the baseline of the metric), FP64 two-level, mixed block-Jacobi
+    # (what the FP32 arithmetic alone gives), mixed two-level at the second tolerance
+    fp64_bj = solve_rec(TOL, mm.MM_PREC_BD, mm.MM_SOLVE_FP64)
+    fp64_2l = solve_rec(TOL, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64)
+    mixed_bj = solve_rec(TOL, mm.MM_PREC_BD, mm.MM_SOLVE_MIXED)
+    mixed_2l_1e8 = solve_rec(1e-8, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED)
 
     for _ in range(a.warmup):
         step()
@@ -392,7 +504,7 @@ def run_ours(a, rank, world, local_rank):
     clk = clocks.stop()
     ms_step = max_over_ranks(ms_total, world, dev) / a.steps
     st = stats[-1]
-    err_vs_fp64 = float(torch.linalg.norm(m - m_ref64) / torch.linalg.norm(m_ref64))
+    solve_errs = errs(m)
 
     # per-kernel profile of one more step (events around every launch)
     plan.profile(True)
@@ -429,111 +541,108 @@ def run_ours(a, rank, world, local_rank):
     barrier()
     e2e_s = (time.perf_counter() - t) / a.steps
 
-    # the paper's other coarse spaces, after the timed region (each replaces the one
-    # above): the a priori Z_S merged into 32 interval groups (Sec. 3.3.1), the Arnoldi
-    # (Algorithm 1) and CG-Lanczos a posteriori spaces keeping the Ritz values below
-    # eps_tol = 0.2 (Sec. 5)
-    coarse_variants = {}
-    for name, build in (("apriori_r32", lambda: plan.build_coarse_apriori(K_COARSE)),
-                        ("arnoldi_eps0.2", lambda: plan.build_coarse_arnoldi(
-                            0.2, 64, bprime=b0, tol=TOL, maxit=400)[0]),
-                        ("aposteriori_eps0.2", lambda: plan.build_coarse_eps(
-                            0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)[0])):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        try:
-            kc = build()
-        except mm.MMError as e:
-            coarse_variants[name] = {"error": str(e)}
-            continue
-        torch.cuda.synchronize()
-        tb = time.perf_counter() - t
-        _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64, out=m)
-        _, smx, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, out=m)
-        coarse_variants[name] = {"k": kc, "build_s": round(tb, 4), "fp64_s": s64["ms_total"] / 1e3,
-                                 "fp64_iters": s64["iters"], "mixed_s": smx["ms_total"] / 1e3,
-                                 "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
-    # the A-DEF2 form (App. B) on the last coarse space
-    plan.build_coarse_eps(0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=3000)
-    _, s64, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_FP64, out=m)
-    _, smx, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_ADEF2, mm.MM_SOLVE_MIXED, out=m)
-    coarse_variants["aposteriori_eps0.2_adef2"] = {
-        "k": coarse_variants.get("aposteriori_eps0.2", {}).get("k"), "fp64_s": s64["ms_total"] / 1e3, "fp64_iters": s64["iters"],
-        "mixed_s": smx["ms_total"] / 1e3, "mixed_iters": smx["iters"], "mixed_rel_resid": smx["rel_resid"]}
+    extras = {}
+    if not a.no_extras:
+        extras["coarse_variants"] = coarse_variants(plan, b0, dc1, m)
+        plan.close()
+        plan = None
+        del dc0, x32, x64, y32, y64
+        torch.cuda.empty_cache()
+        extras["sweep"] = run_sweep(cases=SWEEP_CASES, d_base=(d0, d1))
+        extras["batched"] = run_batched(scan, dev)
+    if plan is not None:
+        plan.close()
 
     if rank != 0:
         return
     # roofline of the dominant kernel of the step
     hbm, peak_src = peaks()
-    nt, n = plan.nt, plan.n
+    nt = pinfo.nt
     stages = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(stages, key=lambda k: stages[k][0])
-    roof = roofline(dom, stages[dom][0] / stages[dom][1], plan, scan, hbm, peak_src)
-    # A x HBM GB/s (algorithmic bytes per A x: pointing + weights + x and y; TOD excluded)
-    axgbs = {}
+    roof = roofline(dom, stages[dom][0] / stages[dom][1], pinfo, scan, hbm, peak_src)
+    # A x against the HBM roofline (algorithmic bytes of Eq. 8 over the two launches)
+    ax_roof = {}
     for key, sz in (("f32", 4), ("f64", 8)):
         t_ax = (ax[key]["toeplitz_ms"] + ax[key]["scatter_ms"]) * 1e-3
-        axgbs[key] = (nt * (4 + 2 * sz) + 2 * n * sz) / t_ax / 1e9
+        byts = ax_bytes(pinfo, sz)
+        ax_roof[key] = {"achieved": round(byts / t_ax / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(byts / t_ax / 1e9 / hbm, 4), "bytes": int(byts),
+                        "ms": round(t_ax * 1e3, 4)}
     line = {
         "metric": METRIC,
         "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nt": nt, "n": n, "npix_obs": plan.npix_obs, "k_kept": kk,
-                   "fft_block_f64": plan.fft_block_f64, "fft_block_f32": plan.fft_block_f32,
-                   "l2": L2_NOTE,
+        "config": {"workload": WORKLOAD, "nt": nt, "n": pinfo.n, "npix_obs": pinfo.n // scan.ncomp,
+                   "k_kept": kk, "fft_block_f64": pinfo.fft_block_f64, "fft_block_f32": pinfo.fft_block_f32,
+                   "arithmetic": ARITHMETIC, "l2": L2_NOTE,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
         "solve": {"iters": st["iters"], "outer": st["outer"], "fp64_products": st["fp64_products"],
-                  "rel_resid": st["rel_resid"], "map_rel_err_vs_fp64_2lvl": err_vs_fp64},
-        "fp64_bj": {"s": st_bj["ms_total"] / 1e3, "iters": st_bj["iters"], "rel_resid": st_bj["rel_resid"]},
-        "fp64_2lvl": {"s": st_2f["ms_total"] / 1e3, "iters": st_2f["iters"]},
-        "speedup_vs_fp64_bj": (st_bj["ms_total"] / 1e3) / (ms_step / 1e3),
+                  "rel_resid": st["rel_resid"], "map_rel_err": solve_errs},
+        "fp64_bj": fp64_bj,
+        "fp64_2lvl": fp64_2l,
+        "mixed_bj": mixed_bj,
+        "mixed_2lvl_tol1e-8": mixed_2l_1e8,
+        "fp64_2lvl_tol1e-10": {"s": st_ref["ms_total"] / 1e3, "iters": st_ref["iters"],
+                               "map_rel_err_vs_oracle_1e-10": errs(m_conv).get("vs_oracle_1e-10")},
+        "speedup_vs_fp64_bj": fp64_bj["s"] / (ms_step / 1e3),
+        "speedup_split": {"fp32_arithmetic": fp64_bj["s"] / mixed_bj["s"],
+                          "two_level_given_fp32": mixed_bj["s"] / (ms_step / 1e3)},
         "coarse_build_s": t_coarse,
-        "coarse_variants": coarse_variants,
-        "ax_gbs": {k: round(v, 1) for k, v in axgbs.items()},
+        "ax_roofline": ax_roof,
         "ax_ms": ax,
         "profile_ms": {k: [round(v[0], 4), v[1]] for k, v in stages.items()},
         "roofline": roof,
         "clocks": clk,
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(nt * 8), "d2h_bytes_per_step": int(n * 8)},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(nt * 8), "d2h_bytes_per_step": int(pinfo.n * 8)},
     }
+    line.update(extras)
     if world == 1 and not a.no_cpu_baseline:
         iters, src, _ = oracle_iterations()
         if iters is None:
-            iters, src = st_2f["iters"], "FP64 two-level PCG iteration count of this run"
+            iters, src = fp64_2l["iters"], "FP64 two-level PCG iteration count of this run"
         try:
             vals, info = oracle_time_to_solution(1, iters)
-            line["cpu_baseline"] = {"value": vals[0], "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": f"b = P^T N^-1 d plus 2 two-level PCG iterations of the full workload "
-                                              f"(FP64 NumPy/SciPy, 1 thread), extrapolated to {iters} iterations "
-                                              f"({src}); plan time {info['t_plan']:.1f} s excluded"}
+            line["cpu_baseline"] = {"value": vals[0], "unit": "s", "cores": info["threads"], "kind": "oracle",
+                                    "sample": f"b = P^T N^-1 d plus {info['sample_iters']} two-level PCG iterations "
+                                              f"of the full workload (FP64 NumPy/SciPy; FFTs on one thread, BLAS on "
+                                              f"{info['threads']}), measured {info['sample_s']:.1f} s, extrapolated "
+                                              f"to {iters} iterations ({src}); plan time {info['t_plan']:.1f} s "
+                                              f"excluded"}
         except Exception as ex:  # the GPU number stands; say why the baseline is missing
             line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {str(ex)[:200]}"}
     print(json.dumps(line))
-    plan.close()
 
 
-def run_sweep():
+def run_sweep(cases=None, d_base=None, emit=False):
     """Bandwidth and knee-frequency sweeps (the paper's Sec. 5 studies of lambda_T and
     f_knee, on the synthetic 2^24-sample polarised scan): iterations and times to 1e-6 of
-    FP64 block-Jacobi, two-level a priori (Z_S, 32 interval groups) and two-level a
-    posteriori (Ritz values below eps_tol = 0.2) PCG, and of the mixed-precision two-level
-    solve."""
+    FP64 block-Jacobi, mixed block-Jacobi, two-level a priori (Z_S, 32 interval groups)
+    and two-level a posteriori (Ritz values below eps_tol = 0.2) PCG.  Cases at the
+    workload's own knee frequencies reuse the bench's two realisations (d_base); scaled
+    knees draw new ones (seeds 2200, 2201).  Returns the records (emit: also one JSON
+    line each)."""
     import torch
     from paper_1408_3048_gb300 import mm, synth
     base = synth.config(CONFIG)
     sky = synth.sky_map(base.npix_sky, base.ncomp, 1000 + CONFIG)
-    cases = [(lam, 1.0) for lam in (1024, 2048, 4096, 8192, 16384)] + [(4096, f) for f in (0.25, 4.0)]
+    if cases is None:
+        cases = [(lam, 1.0) for lam in (1024, 2048, 4096, 8192, 16384)] + [(4096, f) for f in (0.25, 4.0)]
+    recs = []
     for lam, fk in cases:
         psds = np.array(base.psds, dtype=np.float64).reshape(-1, 3).copy()
         psds[:, 1] *= fk
         scan = synth.config(CONFIG)
         scan.lam = lam
         scan.psds = psds
-        d0 = synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, psds, scan.fsamp, 2200))
-        d1 = synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, psds, scan.fsamp, 2201))
+        if fk == 1.0 and d_base is not None:
+            d0, d1 = d_base
+        else:
+            d0, d1 = (synth.tod(scan, sky, synth.noise_realisation(scan.offsets, scan.interval_psd, psds, scan.fsamp,
+                                                                   2200 + r)) for r in (0, 1))
         plan = mm.Plan(scan.pix, scan.npix_sky, scan.weights, scan.offsets, scan.interval_psd, psds, lam, scan.fsamp)
         dc0, dc1 = torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()
         m = torch.empty(plan.n, dtype=torch.float64, device="cuda")
@@ -541,7 +650,9 @@ def run_sweep():
         if plan.fft_block_f64:
             _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_BD, mm.MM_SOLVE_FP64, out=m)
             out["bd_fp64"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3}
-        b0 = plan.rhs(dc0) if plan.fft_block_f64 else None
+        _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_BD, mm.MM_SOLVE_MIXED, out=m)
+        out["bd_mixed"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3}
+        b0 = plan.rhs(dc0)
         for name, build in (("apriori_r32", lambda: plan.build_coarse_apriori(K_COARSE)),
                             ("aposteriori_eps0.2", lambda: plan.build_coarse_eps(
                                 0.2, 64, mm.MM_FP32, bprime=b0, tol=TOL, maxit=5000)[0])):
@@ -557,16 +668,72 @@ def run_sweep():
             _, st, _ = plan.solve(dc1, TOL, 20000, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_MIXED, out=m)
             rec["mixed"] = {"iters": st["iters"], "s": st["ms_total"] / 1e3, "rel_resid": st["rel_resid"]}
             out[name] = rec
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
+        recs.append(out)
         plan.close()
         del dc0, dc1, m
         torch.cuda.empty_cache()
+    return recs
+
+
+def run_batched(scan, dev, lams=(1024, 4096, 16384), R=BATCH_R, nbase=4):
+    """Many right-hand sides through one plan (the batched Monte-Carlo workload): R noise
+    realisations of the bench scan solved together to 1e-6 (mixed precision, block-Jacobi,
+    per-column refinement) at each bandwidth.  The R noise vectors are unit-norm random
+    combinations (seed 2400) of `nbase` seeded realisations (seeds 2400..): a unit-norm
+    combination of independent realisations of one Gaussian noise is again a realisation
+    of it, and drawing R full realisations on the host would take minutes.  Reports the
+    time per map, the batched operator's form, and one A X per column."""
+    import torch
+    from paper_1408_3048_gb300 import mm, synth
+    sky = synth.sky_map(scan.npix_sky, scan.ncomp, 1000 + CONFIG)
+    signal = torch.from_numpy(synth.tod(scan, sky, np.zeros(scan.nt))).to(dev)
+    base = torch.stack([torch.from_numpy(synth.noise_realisation(scan.offsets, scan.interval_psd, scan.psds,
+                                                                 scan.fsamp, 2400 + j)).to(dev)
+                        for j in range(nbase)])
+    C = np.random.default_rng(2400).standard_normal((R, nbase))
+    C /= np.linalg.norm(C, axis=1, keepdims=True)
+    D = signal[None, :] + torch.from_numpy(C).to(dev) @ base
+    del base
+    out = {"R": R, "tol": TOL, "noise": f"unit-norm combinations of {nbase} realisations (seeds 2400..)"}
+    for lam in lams:
+        sc = synth.config(CONFIG)
+        sc.lam = lam
+        plan = mm.Plan(sc.pix, sc.npix_sky, sc.weights, sc.offsets, sc.interval_psd, sc.psds, lam, sc.fsamp)
+        kind, logb, tm = plan.batch_config(R)
+        M = torch.empty((R, plan.n), dtype=torch.float64, device=dev)
+        plan.solve_batch(D, tol=TOL, maxit=5000, out=M)     # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st, status = plan.solve_batch(D, tol=TOL, maxit=5000, out=M)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t
+        X = torch.randn((R, plan.n), dtype=torch.float32, device=dev)
+        Y = torch.empty_like(X)
+        plan.apply_A_batch(X, out=Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            plan.apply_A_batch(X, out=Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ax_ms = e0.elapsed_time(e1) / 3
+        out[f"lambda_{lam}"] = {"s_per_map": ts / R, "s_total": ts, "status": int(status),
+                                "converged": int(sum(x["converged"] for x in st)),
+                                "iters_max": int(max(x["iters"] for x in st)),
+                                "form": "pair" if kind == 0 else "real", "log2_block": int(logb),
+                                "ax_batch_ms_per_column": ax_ms / R}
+        plan.close()
+        del M, X, Y
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
     a = parse()
     if a.sweep:
-        run_sweep()
+        run_sweep(emit=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

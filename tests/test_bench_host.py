@@ -1,7 +1,7 @@
 """Host logic of bench.py on the CPU: the DRAM traffic of a kernel is taken from a recorded
 ncu capture only while the kernel's sources hash to the recorded value, and the roofline's
-algorithmic bytes per launch follow the per-sample figures stated for each kernel
-(pixel index, weights, time-domain value per sample; the map once)."""
+algorithmic bytes per launch are those of one A x (pixel index and weights per sample, x
+read and y written; time-domain intermediates excluded)."""
 import hashlib
 import os
 import shutil
@@ -53,8 +53,8 @@ def test_roofline_algorithmic_bytes(kernel, ncomp):
     plan = _plan(ncomp)
     scan = SimpleNamespace(lam=4096, offsets=np.array([0, 1 << 19, 1 << 20]))
     s = 4 if kernel.endswith("f32") else 8
-    per_sample = 4 + (2 * s if ncomp == 3 else 0) + s     # index, weights, one value
-    expect = plan.nt * per_sample + plan.n * s
+    per_sample = 4 + (2 * s if ncomp == 3 else 0)         # index and weights; no time-domain value
+    expect = plan.nt * per_sample + 2 * plan.n * s        # x read, y written
     ms = 0.25
     r = bench.roofline(kernel, ms, plan, scan, 6769.0, "measured")
     hbm = r if r["bound"] == "hbm" else r["hbm"]
@@ -82,15 +82,19 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
 
 
 def test_reference_arm_line(capsys, monkeypatch):
-    """The oracle arm's JSON line: the GPU arm's metric, time-like, per-step values after
-    the warm-up steps averaged, its own cpu_baseline and e2e."""
+    """The oracle arm's JSON line: the GPU arm's metric, time-like; `value` the extrapolated
+    time-to-solution and ms_per_step the measured sample, each averaged over the steps after
+    the warm-up; its own cpu_baseline (cores as used) and e2e."""
     import json
-    monkeypatch.setattr(bench, "oracle_time_to_solution", lambda steps, iters: ([9.0] + [2.0] * (steps - 1), {}))
+    info = {"samples": [5.0] + [0.5] * 3, "threads": 8, "sample_iters": 2}
+    monkeypatch.setattr(bench, "oracle_time_to_solution",
+                        lambda steps, iters: ([9.0] + [2.0] * (steps - 1), info))
     bench.run_reference(SimpleNamespace(gpus=1, steps=3, warmup=1), 0, 1)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "s"
     assert line["value"] == 2.0 and line["higher_is_better"] is False
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["ms_per_step"] == 500.0 and "extrapolated" in line["value_is"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 8
     assert line["e2e"]["value"] == 2.0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["config"]["workload"] == bench.WORKLOAD
 
