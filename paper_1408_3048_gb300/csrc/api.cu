@@ -129,7 +129,7 @@ struct BatchState {
     float tuned_ms[2] = {};       // timed forms (autotuning), 0 when not timed
     int logb = 0;                 // complex FFT length of the pair kernel
     int ntiles = 0;
-    Tile* tiles = nullptr;
+    SpanTile* tiles = nullptr;
     float* H = nullptr;           // [npsd][B/2 + 1] / B
     float* ptw = nullptr;         // per-pass FFT twiddles of the per-CTA transform
     float* twiddle = nullptr;     // cos(2 pi k / B), k = 0..B/4 (cluster blocks)
@@ -248,7 +248,73 @@ double block_weight<double>(int logn) { return logn >= 15 ? 2.0 : (logn == 14 ? 
 template <>
 double block_weight<float>(int logn) { return fp32_cluster_weight(logn >= 16 ? 4 : (logn == 15 ? 2 : 1)); }
 
+// Overlap-save tiles of blocks of B real positions (B - 2 lambda valid outputs each) for
+// the single-right-hand-side kernels.  Consecutive stationary intervals with the same PSD
+// form a run; a run is laid out as its intervals one after another with lambda zeros
+// between them (so no band product reaches across an interval edge, Eq. 4) and tiled as
+// one sequence, which saves the partly filled last tile of every interval but one.  A run
+// is packed only when that gives fewer tiles and no tile needs more than TILE_SEGS
+// segments; otherwise each interval is tiled on its own (one segment per tile).
+static std::vector<Tile> make_tiles(const Plan& P, int64_t B) {
+    const int64_t lam = P.lambda;
+    const int64_t Lv = B - 2 * lam;
+    std::vector<Tile> out;
+    auto tile_run = [&](int i0, int i1, std::vector<Tile>& dst) -> bool {
+        // virtual start of each interval of the run [i0, i1)
+        std::vector<int64_t> V((size_t)(i1 - i0));
+        int64_t vlen = 0;
+        for (int i = i0; i < i1; ++i) {
+            if (i > i0) vlen += lam;
+            V[(size_t)(i - i0)] = vlen;
+            vlen += P.h_ioff[i + 1] - P.h_ioff[i];
+        }
+        int first = 0;   // first interval that can still meet the current window
+        for (int64_t k = 0; k * Lv < vlen; ++k) {
+            const int64_t w0 = k * Lv - lam;   // virtual position of block position 0
+            Tile t;
+            for (int g = 0; g < TILE_SEGS; ++g) {
+                t.d[g] = 0;
+                t.pb[g] = t.pe[g] = TILE_NONE;
+            }
+            int ns = 0;
+            while (first < i1 - i0 && V[(size_t)first] + (P.h_ioff[i0 + first + 1] - P.h_ioff[i0 + first]) <= w0) ++first;
+            for (int j = first; j < i1 - i0; ++j) {
+                const int64_t L = P.h_ioff[i0 + j + 1] - P.h_ioff[i0 + j];
+                const int64_t a = std::max(V[(size_t)j], w0), b = std::min(V[(size_t)j] + L, w0 + B);
+                if (V[(size_t)j] >= w0 + B) break;
+                if (a >= b) continue;
+                if (ns == TILE_SEGS) return false;
+                t.pb[ns] = (int32_t)(a - w0);
+                t.pe[ns] = (int32_t)(b - w0);
+                t.d[ns] = P.h_ioff[i0 + j] + w0 - V[(size_t)j];   // time of block position p: p + d
+                ++ns;
+            }
+            t.nout = (int32_t)std::min<int64_t>(Lv, vlen - k * Lv);
+            t.psd = P.h_ipsd[i0];
+            dst.push_back(t);
+        }
+        return true;
+    };
+    for (int i0 = 0; i0 < P.K;) {
+        int i1 = i0 + 1;
+        while (i1 < P.K && P.h_ipsd[i1] == P.h_ipsd[i0]) ++i1;
+        std::vector<Tile> single, packed;
+        for (int i = i0; i < i1; ++i) tile_run(i, i + 1, single);
+        if (i1 - i0 > 1 && tile_run(i0, i1, packed) && packed.size() < single.size())
+            out.insert(out.end(), packed.begin(), packed.end());
+        else
+            out.insert(out.end(), single.begin(), single.end());
+        i0 = i1;
+    }
+    return out;
+}
+
 static int64_t overlap_tiles(const Plan& P, int64_t Lv) {
+    return (int64_t)make_tiles(P, Lv + 2 * (int64_t)P.lambda).size();
+}
+
+// Tiles of the batched kernels: every interval on its own.
+static int64_t interval_tiles(const Plan& P, int64_t Lv) {
     int64_t tiles = 0;
     for (int i = 0; i < P.K; ++i) tiles += (P.h_ioff[i + 1] - P.h_ioff[i] + Lv - 1) / Lv;
     return tiles;
@@ -295,20 +361,7 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     tz.logn = choose_logn<T>(P, forced_log2B, &tz.cluster);
     const int64_t N = int64_t(1) << tz.logn;
     const int64_t B = 2 * N;
-    const int64_t Lv = B - 2 * (int64_t)P.lambda;
-    std::vector<Tile> tiles;
-    for (int i = 0; i < P.K; ++i) {
-        const int64_t a = P.h_ioff[i], b = P.h_ioff[i + 1];
-        for (int64_t s = a; s < b; s += Lv) {
-            Tile t;
-            t.out0 = s;
-            t.ibeg = a;
-            t.iend = b;
-            t.nout = (int32_t)std::min<int64_t>(Lv, b - s);
-            t.psd = P.h_ipsd[i];
-            tiles.push_back(t);
-        }
-    }
+    const std::vector<Tile> tiles = make_tiles(P, B);
     tz.ntiles = (int)tiles.size();
     tz.tiles = dalloc<Tile>(tiles.size());
     h2d(tz.tiles, tiles.data(), tiles.size() * sizeof(Tile), P.stream);
@@ -1442,11 +1495,11 @@ static void build_batch_pair(PlanHolder& P, int logb) {
     bt.logb = logb;
     const int64_t B = int64_t(1) << logb;
     const int64_t Lv = B - 2 * (int64_t)P.lambda;
-    std::vector<Tile> tiles;
+    std::vector<SpanTile> tiles;
     for (int i = 0; i < P.K; ++i) {
         const int64_t a = P.h_ioff[i], b = P.h_ioff[i + 1];
         for (int64_t s0 = a; s0 < b; s0 += Lv) {
-            Tile t;
+            SpanTile t;
             t.out0 = s0;
             t.ibeg = a;
             t.iend = b;
@@ -1456,8 +1509,8 @@ static void build_batch_pair(PlanHolder& P, int logb) {
         }
     }
     bt.ntiles = (int)tiles.size();
-    bt.tiles = dalloc<Tile>(tiles.size());
-    h2d(bt.tiles, tiles.data(), tiles.size() * sizeof(Tile), P.stream);
+    bt.tiles = dalloc<SpanTile>(tiles.size());
+    h2d(bt.tiles, tiles.data(), tiles.size() * sizeof(SpanTile), P.stream);
     std::vector<float> H((size_t)P.npsd * (B / 2 + 1));
     for (int p = 0; p < P.npsd; ++p) {
         // overlap_save_spectrum(t, N) returns sigma_k / N for k <= N on a 2N grid
@@ -1500,7 +1553,7 @@ static void ensure_batch_tables(PlanHolder& P, int R, int want = -1) {
         const int64_t Lv = B - 2 * (int64_t)P.lambda;
         if (Lv < 1) continue;
         const int cl = logb > BATCH_MAX_LOGB_CTA ? 1 << (logb - BATCH_MAX_LOGB_CTA) : 1;
-        const double cost = 0.5 * (double)overlap_tiles(P, Lv) * ((double)B * logb + 2048.0) * fp32_cluster_weight(cl);
+        const double cost = 0.5 * (double)interval_tiles(P, Lv) * ((double)B * logb + 2048.0) * fp32_cluster_weight(cl);
         if (best < 0 || cost < best_cost) {
             best = logb;
             best_cost = cost;

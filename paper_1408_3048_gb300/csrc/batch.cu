@@ -25,7 +25,7 @@ namespace mm {
 // Gathers points [s0, s0 + count) of the packed complex block (column pair x0 + i x1)
 // into a[0 .. count).
 template <int NT, int NC>
-__device__ __forceinline__ void batch_load(const BatchTzArgs& A, const Tile& tile, int64_t ws, const float* x0,
+__device__ __forceinline__ void batch_load(const BatchTzArgs& A, const SpanTile& tile, int64_t ws, const float* x0,
                                            const float* x1, bool has1, float2* a, int s0, int count) {
     const int tid = threadIdx.x;
     const int PER = count / NT;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(NT) batch_toeplitz_kernel(BatchTzArgs A) {
     float2* a = reinterpret_cast<float2*>(smem_raw);
     const int npairs = (A.R + 1) / 2;
     const int pair = blockIdx.x % npairs;
-    const Tile tile = A.tiles[blockIdx.x / npairs];
+    const SpanTile tile = A.tiles[blockIdx.x / npairs];
     const int r0 = 2 * pair;
     const bool has1 = r0 + 1 < A.R;
     const float* x0 = A.X + (size_t)r0 * A.n;
@@ -125,7 +125,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) batch_toeplitz_
     const int npairs = (A.R + 1) / 2;
     const int cid = blockIdx.x / CL;
     const int pair = cid % npairs;
-    const Tile tile = A.tiles[cid / npairs];
+    const SpanTile tile = A.tiles[cid / npairs];
     const int r0 = 2 * pair;
     const bool has1 = r0 + 1 < A.R;
     const float* x0 = A.X + (size_t)r0 * A.n;

@@ -12,7 +12,7 @@ constexpr int BATCH_MAX_LOGB_CTA = 14;         // largest complex block in one C
 constexpr int BATCH_MAX_LOGB = 16;             // 2- and 4-CTA clusters above it
 
 struct BatchTzArgs {
-    const Tile* tiles;
+    const SpanTile* tiles;
     const float* H;            // [npsd][B/2 + 1], divided by B
     const float2* ptw;         // per-pass FFT twiddles of the per-CTA transform
     const float* twiddle;      // cos(2 pi k / B), k = 0..B/4 (cluster variants)

@@ -12,9 +12,28 @@
 namespace mm {
 
 // ---------------------------------------------------------------------------------
-// Overlap-save tile: block of B real samples [in0, in0 + B) producing the valid outputs
-// [out0, out0 + nout) (out0 = in0 + lambda); samples outside [ibeg, iend) read as 0.
+// Overlap-save tile of the single-right-hand-side Toeplitz kernels: a block of B real
+// positions holding up to TILE_SEGS segments of samples.  Segment g covers block positions
+// [pb[g], pe[g]) and position p in it holds the sample of time p + d[g]; every other
+// position is 0.  The segments of one tile come from consecutive stationary intervals of
+// one PSD, separated in the block by at least lambda zeros, so the band product of one
+// interval never reaches another (Eq. 4: no coupling between intervals).  The valid
+// outputs are block positions [lambda, lambda + nout); those inside a segment are stored
+// at their time.  Unused segments have pb = pe = TILE_NONE.
+constexpr int TILE_SEGS = 3;
+constexpr int32_t TILE_NONE = 0x7fffffff;
 struct Tile {
+    int64_t d[TILE_SEGS];
+    int32_t pb[TILE_SEGS];
+    int32_t pe[TILE_SEGS];
+    int32_t nout;
+    int32_t psd;
+};
+
+// Tile of the batched kernels: block of B real samples [in0, in0 + B) of one interval
+// producing the valid outputs [out0, out0 + nout) (out0 = in0 + lambda); samples outside
+// [ibeg, iend) read as 0.
+struct SpanTile {
     int64_t out0;
     int64_t ibeg;
     int64_t iend;

@@ -1,8 +1,9 @@
 // Banded block-Toeplitz N^-1 by overlap-save FFT in shared memory (Eq. 4; band of
 // Sec. 4.1.4; FFT product of Sec. 2.1).  Included by toeplitz_f64.cu / toeplitz_f32.cu.
 //
-// One CTA per overlap-save tile.  A tile reads B = 2N real samples
-// [out0 - lambda, out0 - lambda + B) of one stationary interval (zero outside it),
+// One CTA per overlap-save tile.  A tile holds B = 2N real positions filled from up to
+// three segments of consecutive stationary intervals of one PSD (zeros between and
+// around them, at least lambda between two intervals: see Tile),
 // packs them as N complex values u_m = y_2m + i y_2m+1, runs an N-point complex FFT,
 // turns that into the spectrum of the real block (real-FFT post-processing), multiplies
 // by the real spectrum H of the even kernel (t_|k| for |k| <= lambda, laid out
@@ -225,6 +226,47 @@ __host__ __device__ constexpr int ptw_offset(int logns) {
     return off;
 }
 
+// (c, s) pairs stand for c - i s = exp(-i theta); their product is another such pair.
+__device__ __forceinline__ float2 tw_mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// FP32 pass twiddles computed in registers instead of read from a table: v[r] *= W^(r k)
+// with W = exp(-2 pi i / (Ns R)) for r = 1..R-1, from sincospif at x = 2k / (Ns R) and
+// 4x (exact scalings of an exact float): W^r = W^(4a) W^b, r = 4a + b, with W^2, W^3,
+// W^8, W^12 formed by one or two products, so every twiddle is at most four roundings
+// from the correctly rounded value.  (A table in global memory put an L2 load after
+// every barrier of the FFT on the critical path.)
+template <int R>
+__device__ __forceinline__ void apply_twiddles_f32(float2* v, float x) {
+    float s1, c1;
+    sincospif(x, &s1, &c1);
+    float2 w[4];
+    w[0] = make_float2(1.f, 0.f);
+    w[1] = make_float2(c1, s1);
+    w[2] = tw_mul(w[1], w[1]);
+    w[3] = tw_mul(w[1], w[2]);
+#pragma unroll
+    for (int b = 1; b < (R < 4 ? R : 4); ++b) v[b] = cmul<float>(v[b], w[b].x, w[b].y);
+    if constexpr (R > 4) {
+        float s4, c4;
+        sincospif(4.f * x, &s4, &c4);
+        float2 W[4];
+        W[0] = make_float2(1.f, 0.f);
+        W[1] = make_float2(c4, s4);
+        W[2] = tw_mul(W[1], W[1]);
+        W[3] = tw_mul(W[1], W[2]);
+#pragma unroll
+        for (int a = 1; a < R / 4; ++a) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float2 t = b == 0 ? W[a] : tw_mul(W[a], w[b]);
+                v[4 * a + b] = cmul<float>(v[4 * a + b], t.x, t.y);
+            }
+        }
+    }
+}
+
 // One in-place Stockham pass of radix R on N = 2^LOGN points (Ns = 2^LOGNS).
 template <typename T, int LOGN, int NT, int LOGR, int LOGNS>
 __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename Cx<T>::type* ptw) {
@@ -249,11 +291,15 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename
         const int j = tid + b * NT;
         const int k = j & (Ns - 1);
         if constexpr (LOGNS > 0) {
-            const C2* tw = ptw + ptw_offset<LOGN>(LOGNS) + k;
+            if constexpr (sizeof(T) == 4) {
+                apply_twiddles_f32<R>(v[b], (float)(2 * k) * (1.f / (float)(Ns * R)));
+            } else {
+                const C2* tw = ptw + ptw_offset<LOGN>(LOGNS) + k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const C2 w = __ldg(tw + (r - 1) * Ns);
-                v[b][r] = cmul<T>(v[b][r], w.x, w.y);
+                for (int r = 1; r < R; ++r) {
+                    const C2 w = __ldg(tw + (r - 1) * Ns);
+                    v[b][r] = cmul<T>(v[b][r], w.x, w.y);
+                }
             }
         }
         dft<T, R>(v[b]);
@@ -275,16 +321,32 @@ __device__ __forceinline__ void fft_all(typename Cx<T>::type* a, const typename 
     }
 }
 
+// Segment of block position p in a tile (the segments ascend): g with pb[g] <= p, and
+// whether p lies inside it (else it is a zero between or around the segments).
+__device__ __forceinline__ int tile_seg(const Tile& tl, int p, bool& inside) {
+    // selects, not indexing: a dynamically indexed Tile would be placed in local memory
+    const int g = (p >= tl.pb[1]) + (p >= tl.pb[2]);
+    const int b = g == 0 ? tl.pb[0] : (g == 1 ? tl.pb[1] : tl.pb[2]);
+    const int e = g == 0 ? tl.pe[0] : (g == 1 ? tl.pe[1] : tl.pe[2]);
+    inside = p >= b && p < e;
+    return g;
+}
+
+__device__ __forceinline__ int64_t seg_d(const Tile& tl, int g) {
+    return g == 0 ? tl.d[0] : (g == 1 ? tl.d[1] : tl.d[2]);
+}
+
 // MODE 0: y from a time-domain array; 1: gather T map; 3: gather I/Q/U map;
 // 2: y from an FP64 time-domain array (rounded to T); 4 / 5: FP64 data minus the T /
 // I/Q/U gather, d - P x (the residual b - A x = P^T N^-1 (d - P x) of Eq. 5 and 7).
-// Load real samples [s0, s0 + count) of the block that starts at time ws into ar[0..count)
-// (one sample per lane, coalesced; ar is the packed complex array viewed as reals, so local
-// sample s lands in component s & 1 of complex slot s / 2).  Samples outside the tile's
-// interval read as 0.  MODE 0: from A.y; 1: T gather; 3: I/Q/U gather.
+// Load block positions [s0, s0 + count) into ar[0..count) (one position per lane,
+// coalesced within a segment; ar is the packed complex array viewed as reals, so local
+// position s lands in component s & 1 of complex slot s / 2).  A position outside the
+// tile's segments reads as 0.  The common tile of one segment covering the whole range
+// takes a branch-free path.
 template <typename T, int NT, int MODE>
-__device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile, int64_t ws, T* ar, int s0,
-                                           int count, int64_t roff) {
+__device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile, T* ar, int s0, int count,
+                                           int64_t roff) {
     const T* __restrict__ y = A.y + roff;
     const T* __restrict__ x = A.x + roff;
     const double* __restrict__ yd = A.yd + roff;
@@ -292,17 +354,31 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
     const int PER = count / NT;
     constexpr bool IQU = MODE == 3 || MODE == 5;
     constexpr int UMAX = IQU ? 4 : 8;
-    const bool interior = ws + s0 >= tile.ibeg && ws + s0 + count <= tile.iend;
+    const bool whole = tile.pb[0] <= s0 && s0 + count <= tile.pe[0];
+    const int64_t d0 = tile.d[0];
 #pragma unroll 1
     for (int base = 0; base < PER; base += UMAX) {
         T v[UMAX];
+        int64_t tt[UMAX];
+        bool okv[UMAX];
+#pragma unroll
+        for (int u = 0; u < UMAX; ++u) {
+            const int p = s0 + (base + u) * NT + tid;
+            if (whole) {
+                tt[u] = p + d0;
+                okv[u] = base + u < PER;
+            } else {
+                bool in;
+                const int g = tile_seg(tile, p, in);
+                tt[u] = p + seg_d(tile, g);
+                okv[u] = base + u < PER && in;
+            }
+        }
         if constexpr (MODE == 0 || MODE == 2) {
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-                const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
-                const bool ok = base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend));
-                if constexpr (MODE == 0) v[u] = ok ? y[t] : (T)0;
-                else v[u] = ok ? (T)yd[t] : (T)0;
+                if constexpr (MODE == 0) v[u] = okv[u] ? y[tt[u]] : (T)0;
+                else v[u] = okv[u] ? (T)yd[tt[u]] : (T)0;
             }
         } else {
             int q[UMAX];
@@ -310,13 +386,11 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
             T dv[UMAX];
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-                const int64_t t = ws + s0 + (int64_t)((base + u) * NT + tid);
-                const bool ok = base + u < PER && (interior || (t >= tile.ibeg && t < tile.iend));
-                q[u] = ok ? __ldg(A.pixc + t) : -1;
+                q[u] = okv[u] ? __ldg(A.pixc + tt[u]) : -1;
                 if constexpr (IQU) {
-                    if (ok) w[u] = A.w[t];
+                    if (okv[u]) w[u] = A.w[tt[u]];
                 }
-                if constexpr (MODE >= 4) dv[u] = ok ? (T)yd[t] : (T)0;
+                if constexpr (MODE >= 4) dv[u] = okv[u] ? (T)yd[tt[u]] : (T)0;
             }
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
@@ -341,6 +415,15 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
             }
         }
     }
+}
+
+// Store output n (block position lambda + n) at its time, unless it falls between segments.
+template <typename T>
+__device__ __forceinline__ void store_out(const Tile& tile, T* z, int lambda, int n, T v) {
+    bool in;
+    const int p = n + lambda;
+    const int g = tile_seg(tile, p, in);
+    if (in) z[p + seg_d(tile, g)] = v;
 }
 
 // Real-FFT split of the packed spectrum at the bin pair (k, N - k), product with the real
@@ -396,8 +479,7 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
     for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
-    const int64_t ws = tile.out0 - A.lambda;
-    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
+    load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // real-FFT post-processing, spectrum product, pre-processing for the inverse.
@@ -413,12 +495,12 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     }
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
-    // outputs: real samples lambda .. lambda + nout - 1 of the block
-    T* zo = A.z + tr.rhs * A.out_stride + tile.out0;
+    // outputs: real block positions lambda .. lambda + nout - 1, stored at their times
+    T* zo = A.z + tr.rhs * A.out_stride;
     for (int n = tid; n < tile.nout; n += NT) {
         const int i = n + A.lambda;
         const C2 v = a[pad<T>(i >> 1)];
-        zo[n] = (i & 1) ? -v.y : v.x;
+        store_out<T>(tile, zo, A.lambda, n, (i & 1) ? -v.y : v.x);
     }
 }
 
@@ -465,8 +547,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
     const TileRhs tr = tile_rhs(blockIdx.x / CL, A.R);
     const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
-    const int64_t ws = tile.out0 - A.lambda;
-    load_block<T, NT, MODE>(A, tile, ws, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M, tr.rhs * A.in_stride);
+    load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), rank * 2 * M, 2 * M, tr.rhs * A.in_stride);
     cl.sync();
     C2 y[PER];
 #pragma unroll
@@ -528,7 +609,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
     __syncthreads();
     fft_all<T, LOGM, NT, 0>(a, A.ptw);
     cl.sync();
-    T* zo = A.z + tr.rhs * A.out_stride + tile.out0;
+    T* zo = A.z + tr.rhs * A.out_stride;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int n1 = u * NT + tid;
@@ -543,8 +624,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
         }
         // packed index m = rank M + n1 -> real samples 2m (f.x) and 2m + 1 (-f.y)
         const int i0 = 2 * (rank * M + n1) - A.lambda;
-        if (i0 >= 0 && i0 < tile.nout) zo[i0] = f.x;
-        if (i0 + 1 >= 0 && i0 + 1 < tile.nout) zo[i0 + 1] = -f.y;
+        if (i0 >= 0 && i0 < tile.nout) store_out<T>(tile, zo, A.lambda, i0, f.x);
+        if (i0 + 1 >= 0 && i0 + 1 < tile.nout) store_out<T>(tile, zo, A.lambda, i0 + 1, -f.y);
     }
     cl.sync();   // the other CTAs may still read this CTA's shared memory
 }
