@@ -40,8 +40,9 @@ WORKLOAD = ("polarised I/Q/U raster, 256x256 patch, 16 detectors x 2^20 = 2^24 s
             "intervals, 1/f noise fknee U[0.1,2] Hz alpha U[1,2], lambda=4096, tol 1e-6, two-level k=32")
 METRIC = "time-to-solution @1e-6 resid (2-level mixed vs FP64 BJ, 1 GPU); A·x HBM GB/s"
 ARITHMETIC = ("mixed solve: FP32 gather, Toeplitz N^-1, scatter and PCG vectors; CG dot products as "
-              "double-float FP32 pairs (~48-bit significand, not FP64); FP64 step scalars, FP64 E^-1 and "
-              "FP64 iterative-refinement residual P^T N^-1 (d - P m)")
+              "double-float FP32 pairs (~48-bit significand, not FP64); FP64 step scalars and FP64 E^-1; "
+              "iterative-refinement residual P^T N^-1 (d - P m) on FP64 data with the band product in "
+              "double-float arithmetic (agrees with FP64 to 1e-12 of ||b||, tested)")
 # bandwidth and knee-frequency cases of the secondary sweep (the paper's Sec. 5 studies)
 SWEEP_CASES = [(1024, 1.0), (4096, 1.0), (16384, 1.0), (4096, 0.25), (4096, 4.0)]
 BATCH_R = 64
@@ -478,7 +479,11 @@ def run_ours(a, rank, world, local_rank):
         return rec
 
     # FP64 block-Jacobi (the baseline of the metric), FP64 two-level, mixed block-Jacobi
-    # (what the FP32 arithmetic alone gives), mixed two-level at the second tolerance
+    # (what the FP32 arithmetic alone gives), mixed two-level at the second tolerance;
+    # one untimed solve of each form first (first launches load the kernels' modules)
+    for kind in (mm.MM_PREC_BD, mm.MM_PREC_TWOLEVEL):
+        for solver in (mm.MM_SOLVE_FP64, mm.MM_SOLVE_MIXED):
+            plan.solve(dc1, TOL, 20000, kind, solver, out=m)
     fp64_bj = solve_rec(TOL, mm.MM_PREC_BD, mm.MM_SOLVE_FP64)
     fp64_2l = solve_rec(TOL, mm.MM_PREC_TWOLEVEL, mm.MM_SOLVE_FP64)
     mixed_bj = solve_rec(TOL, mm.MM_PREC_BD, mm.MM_SOLVE_MIXED)

@@ -386,7 +386,26 @@ typedef struct {
                                (FP32 PCG tracks the true residual down to ~2e-7 relative)    */
     double first_inner_tol; /* inner tolerance of the first step (MIXED); default: the same
                                rule as later steps, max(inner_tol_min, 0.5 tol ||b||/||r||) */
+    int32_t residual;       /* arithmetic of the refinement residuals (MIXED, and the batched
+                               solver): MM_RESID_DF32 (default) or MM_RESID_FP64, see
+                               mm_residual                                                  */
 } mm_solve_opts;
+
+/*
+ * The residual of a map x from the data d, r = P^T N^-1 (d - P x) = b - A x (Eq. 5, 7),
+ * in one pass: de-pointing and subtraction per sample in FP64, the band product N^-1 of
+ * the residual data, then P^T in FP64.  `arith` selects the arithmetic of the band
+ * product: MM_RESID_FP64 runs the overlap-save FFT in FP64; MM_RESID_DF32 runs the same
+ * FFT in double-float arithmetic (unevaluated pairs of FP32 numbers, ~48-bit
+ * significands, error-free two-sum and FMA two-product) on the FP32 pipe, which GB300
+ * runs at 64 times its FP64 rate; its result agrees with the FP64 one to ~1e-13 of ||b||
+ * and it is the default residual of the mixed-precision solver's iterative refinement.
+ * The paper does not discuss arithmetic; this is this library's choice for Sec. 5.1's
+ * stopping test at 1e-6 .. 1e-8.  d device double[nt], x, r device double[n].
+ * Errors: MM_ERR_ARG for null vectors, an unknown `arith`, or no FP64 block for lambda.
+ */
+enum { MM_RESID_DF32 = 0, MM_RESID_FP64 = 1 };
+mm_status mm_residual(mm_plan_t plan, int arith, const double* d, const double* x, double* r);
 
 /* mm_solve with explicit options (same semantics and errors). */
 mm_status mm_solve_ex(mm_plan_t plan, const double* d, const mm_solve_opts* opts, double* m, mm_stats* st);

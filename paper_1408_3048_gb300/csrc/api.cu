@@ -17,6 +17,7 @@
 
 #include "coarse.cuh"
 #include "coarse_host.h"
+#include "dfloat.cuh"
 #include "mm_internal.h"
 #include "pcg.cuh"
 #include "batch.cuh"
@@ -206,6 +207,7 @@ static void destroy_plan(PlanHolder* P) {
         dfree(p);
     free_tz(P->tz64);
     free_tz(P->tz32);
+    free_tz(P->tzdf);
     free_coarse(P->coarse);
     PcgDev& g = P->pcg;
     for (void* p : {(void*)g.partial, (void*)g.sc_part, (void*)g.sc_count, (void*)g.scal, (void*)g.flags,
@@ -386,6 +388,49 @@ static void build_toeplitz(Plan& P, ToeplitzDev& tz, int forced_log2B) {
     tz.H = dalloc<T>(H.size());
     h2d(tz.H, H.data(), H.size() * sizeof(T), P.stream);
     sync(P.stream);   // host vectors go out of scope
+}
+
+// Double-float tables on the blocks of the FP64 kernel (tz64, which must be final):
+// its tiles copied, the cosine and per-pass twiddles and the kernel spectra rounded to
+// double-float pairs (hi = FP32 rounding, lo = FP32 rounding of the rest).
+static void build_toeplitz_df(Plan& P) {
+    const ToeplitzDev& src = P.tz64;
+    ToeplitzDev& tz = P.tzdf;
+    free_tz(tz);
+    tz = ToeplitzDev{};
+    if (src.logn == 0) return;
+    tz.logn = src.logn;
+    tz.cluster = src.cluster;
+    tz.ntiles = src.ntiles;
+    const int64_t N = int64_t(1) << tz.logn;
+    const int64_t B = 2 * N;
+    try {
+        tz.tiles = dalloc<Tile>((size_t)tz.ntiles);
+        check_cuda(cudaMemcpyAsync(tz.tiles, src.tiles, (size_t)tz.ntiles * sizeof(Tile), cudaMemcpyDeviceToDevice,
+                                   P.stream), "copy tiles");
+        std::vector<dfl> tw((size_t)(B / 4 + 1));
+        for (int64_t k = 0; k <= B / 4; ++k) tw[(size_t)k] = dfl(std::cos(2.0 * 3.14159265358979323846 * (double)k / (double)B));
+        tz.twiddle = dalloc<dfl>(tw.size());
+        h2d(tz.twiddle, tw.data(), tw.size() * sizeof(dfl), P.stream);
+        const int lc = tz.cluster == 4 ? 2 : (tz.cluster == 2 ? 1 : 0);
+        const std::vector<double> pt = pass_twiddle_table(tz.logn - lc);
+        std::vector<dfl> ptd(pt.size());
+        for (size_t i = 0; i < pt.size(); ++i) ptd[i] = dfl(pt[i]);
+        tz.ptw = dalloc<dfl>(ptd.size());
+        h2d(tz.ptw, ptd.data(), ptd.size() * sizeof(dfl), P.stream);
+        std::vector<dfl> H((size_t)P.npsd * (N + 1));
+        for (int p = 0; p < P.npsd; ++p) {
+            const std::vector<double> h = overlap_save_spectrum(P.rows[(size_t)p], N);
+            for (int64_t k = 0; k <= N; ++k) H[(size_t)p * (N + 1) + k] = dfl(h[(size_t)k]);
+        }
+        tz.H = dalloc<dfl>(H.size());
+        h2d(tz.H, H.data(), H.size() * sizeof(dfl), P.stream);
+        sync(P.stream);   // host vectors go out of scope
+    } catch (...) {
+        free_tz(tz);
+        tz = ToeplitzDev{};
+        throw;
+    }
 }
 
 // Average milliseconds of `reps` launches of f on the plan's stream (one untimed first).
@@ -645,6 +690,7 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
         if (P.tz32.logn != 0 && o->fft_log2_f32 <= 0)
             autotune_toeplitz<float>(P, P.tz32, P.tod32, reinterpret_cast<const float*>(P.x64), P.tuned_ms32);
     }
+    build_toeplitz_df(P);
     sync(s);
 }
 
@@ -1238,6 +1284,7 @@ static void build_coarse(PlanHolder& P, int k, const double* bprime, double tol,
 // -------------------------------------------------------------------------- solve
 static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
     if (!(so.tol >= 0.0) || so.maxit < 1) throw Error{MM_ERR_ARG, "tol must be >= 0 and maxit >= 1"};
+    if (so.residual != MM_RESID_DF32 && so.residual != MM_RESID_FP64) throw Error{MM_ERR_ARG, "bad residual arithmetic"};
     if (so.kind != MM_PREC_BD && so.kind != MM_PREC_TWOLEVEL && so.kind != MM_PREC_ADEF2)
         throw Error{MM_ERR_ARG, "bad preconditioner kind"};
     if (so.solver != MM_SOLVE_FP64 && so.solver != MM_SOLVE_MIXED) throw Error{MM_ERR_ARG, "bad solver"};
@@ -1247,12 +1294,16 @@ static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
 
 // FP64 residual r = b - A x: with the data d (device, FP64) as P^T N^-1 (d - P x) -- one
 // Toeplitz pass on the residual data, free of the cancellation between b and A x --
-// else as b - A x from P.b64.
-static void residual64(PlanHolder& P, const double* d, const double* x, double* r) {
+// else as b - A x from P.b64.  df: that Toeplitz pass in double-float arithmetic (FP64
+// data, ~48-bit FFT on the FP32 pipe) when the plan has the tables for it.
+static void residual64(PlanHolder& P, const double* d, const double* x, double* r, bool df = false) {
     cudaStream_t s = P.stream;
     if (d != nullptr) {
         int sl = prof_begin(P, ST_TZ64);
-        launch_toeplitz_any<double>(P, P.tz64, nullptr, d, x, 1, 0, P.tod64, 0, nullptr, s);
+        if (df && P.tzdf.logn != 0)
+            launch_toeplitz_df(P, nullptr, d, x, 1, 0, P.tod64, 0, s);
+        else
+            launch_toeplitz_any<double>(P, P.tz64, nullptr, d, x, 1, 0, P.tod64, 0, nullptr, s);
         prof_end(P, sl);
         sl = prof_begin(P, ST_SC64);
         launch_scatter<double>(P, P.tod64, r, nullptr, s);
@@ -1329,7 +1380,7 @@ static int solve_from_b(PlanHolder& P, const mm_solve_opts& so, double* xout, mm
         total += o.iters;
         last_rec = o.bb > 0 ? std::sqrt(o.rr / o.bb) : 0.0;
         launch_axpy_f32(xout, static_cast<const float*>(P.pcg.x), P.d_dot + DOT_BLOCKS, P.n, s);
-        residual64(P, d, xout, P.r64);
+        residual64(P, d, xout, P.r64, so.residual != MM_RESID_FP64);
         ++fp64;
         rr = dot64(P, P.r64, P.r64);
         ++outer;
@@ -1816,7 +1867,7 @@ static void solve_batch(PlanHolder& P, const double* D, int R, const mm_solve_op
                 fp64[(size_t)r] += 1;
                 double* x64 = bt.x64 + (size_t)r * n;
                 launch_axpy_host(x64, bt.x + (size_t)r * n, nrm[(size_t)r], (int64_t)n, s);
-                residual64(P, Dg + (size_t)r * nt, x64, bt.r64 + (size_t)r * n);
+                residual64(P, Dg + (size_t)r * nt, x64, bt.r64 + (size_t)r * n, so.residual != MM_RESID_FP64);
                 rr[(size_t)r] = dot64(P, bt.r64 + (size_t)r * n, bt.r64 + (size_t)r * n);
             }
             total += mx;
@@ -2131,6 +2182,17 @@ mm_status mm_coarse_vectors(mm_plan_t plan, double* Z) {
         if (P->coarse.k == 0) throw Error{MM_ERR_STATE, "no coarse space"};
         if (Z == nullptr) throw Error{MM_ERR_ARG, "null output"};
         check_cuda(cudaMemcpy(Z, P->coarse.Z64, (size_t)P->coarse.k * P->n * 8, cudaMemcpyDefault), "copy Z");
+    });
+}
+
+mm_status mm_residual(mm_plan_t plan, int arith, const double* d, const double* x, double* r) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (!d || !x || !r) throw Error{MM_ERR_ARG, "null vector"};
+        if (arith != MM_RESID_DF32 && arith != MM_RESID_FP64) throw Error{MM_ERR_ARG, "bad residual arithmetic"};
+        if (P->tz64.logn == 0) throw Error{MM_ERR_ARG, "no FP64 Toeplitz block fits this lambda"};
+        residual64(*P, d, x, r, arith == MM_RESID_DF32);
+        sync(*P);
     });
 }
 

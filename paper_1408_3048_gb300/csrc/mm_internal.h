@@ -136,6 +136,7 @@ struct Plan {
     double* t0 = nullptr;          // [npsd] diagonal of each row
 
     ToeplitzDev tz64, tz32;
+    ToeplitzDev tzdf;              // double-float tables on tz64's blocks (refinement residual)
 
     // block-Jacobi: inverse blocks, symmetric packed (a00 a01 a02 a11 a12 a22) or 1
     double* bd64 = nullptr;        // [npix_obs][ncomp == 3 ? 6 : 1]
@@ -210,6 +211,10 @@ void launch_toeplitz_rhs(const Plan& P, const ToeplitzDev& tz, const T* y_tod, c
 template <typename T>
 void launch_toeplitz_any(const Plan& P, const ToeplitzDev& tz, const T* y_tod, const double* d_tod, const T* x_map,
                          int R, int64_t in_stride, T* z, int64_t out_stride, const int* done, cudaStream_t s);
+// Double-float N^-1 on FP64 data (toeplitz_df.cu): y (time domain) given, or else the
+// residual data d - P x; output z FP64 [nt] (R right-hand sides as for launch_toeplitz_rhs)
+void launch_toeplitz_df(const Plan& P, const double* y, const double* d, const double* x, int R, int64_t in_stride,
+                        double* z, int64_t out_stride, cudaStream_t s);
 template <typename T>
 size_t toeplitz_smem_bytes(int logn);
 template <typename T>

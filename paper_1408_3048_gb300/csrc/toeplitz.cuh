@@ -23,6 +23,7 @@
 
 #include <cooperative_groups.h>
 
+#include "dfloat.cuh"
 #include "mm_internal.h"
 
 namespace mm {
@@ -30,6 +31,21 @@ namespace mm {
 template <typename T> struct Cx;
 template <> struct Cx<double> { using type = double2; };
 template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<dfl> { using type = dfl2; };
+
+// Type of the arrays a kernel of arithmetic T reads and writes: the double-float kernel
+// works on FP64 data.
+template <typename T> struct InT { using type = T; };
+template <> struct InT<dfl> { using type = double; };
+template <typename T> using In = typename InT<T>::type;
+
+// Read-only load of a complex table entry.
+__device__ __forceinline__ float2 ldc(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldc(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dfl2 ldc(const dfl2* p) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    return dfl2{dfl(f.x, f.y), dfl(f.z, f.w)};
+}
 
 template <typename T>
 struct TzArgs {
@@ -37,12 +53,12 @@ struct TzArgs {
     const T* twiddle;      // [N/2 + 1]: cos(2 pi k / B), real-FFT split
     const typename Cx<T>::type* ptw;  // per-pass FFT twiddles (ptw_offset)
     const T* H;            // [npsd][N + 1]
-    const T* y;            // time-domain input (mode 0)
+    const In<T>* y;        // time-domain input (mode 0)
     const double* yd;      // FP64 time-domain input (modes 2, 4, 5)
-    const T* x;            // map (gather modes)
+    const In<T>* x;        // map (gather modes)
     const int32_t* pixc;   // [nt]
-    const typename Cx<T>::type* w;  // [nt] (cos, sin) for ncomp = 3
-    T* z;                  // [nt] output
+    const typename Cx<In<T>>::type* w;  // [nt] (cos, sin) for ncomp = 3
+    In<T>* z;              // [nt] output
     const int* done;       // early-exit flag (PCG) or nullptr
     int lambda;
     int R;                 // right-hand sides (grid: tile-major, RHS fastest)
@@ -86,9 +102,6 @@ __device__ __forceinline__ void twiddle(const T* tab, int m, T& c, T& s) {
     }
 }
 
-template <typename T, int R>
-__device__ __forceinline__ void dft(typename Cx<T>::type* v);
-
 template <typename T>
 __device__ __forceinline__ void bfly2(typename Cx<T>::type& a, typename Cx<T>::type& b) {
     typename Cx<T>::type t = a;
@@ -96,10 +109,6 @@ __device__ __forceinline__ void bfly2(typename Cx<T>::type& a, typename Cx<T>::t
     b.x = t.x - b.x; b.y = t.y - b.y;
 }
 
-template <>
-__device__ __forceinline__ void dft<double, 2>(double2* v) { bfly2<double>(v[0], v[1]); }
-template <>
-__device__ __forceinline__ void dft<float, 2>(float2* v) { bfly2<float>(v[0], v[1]); }
 
 template <typename T>
 __device__ __forceinline__ void dft4(typename Cx<T>::type& a0, typename Cx<T>::type& a1,
@@ -117,10 +126,6 @@ __device__ __forceinline__ void dft4(typename Cx<T>::type& a0, typename Cx<T>::t
     a3.x = t1.x - t3.x; a3.y = t1.y - t3.y;
 }
 
-template <>
-__device__ __forceinline__ void dft<double, 4>(double2* v) { dft4<double>(v[0], v[1], v[2], v[3]); }
-template <>
-__device__ __forceinline__ void dft<float, 4>(float2* v) { dft4<float>(v[0], v[1], v[2], v[3]); }
 
 template <typename T>
 __device__ __forceinline__ void dft8(typename Cx<T>::type* v) {
@@ -145,10 +150,6 @@ __device__ __forceinline__ void dft8(typename Cx<T>::type* v) {
     v[7].x = e3.x - o3.x; v[7].y = e3.y - o3.y;
 }
 
-template <>
-__device__ __forceinline__ void dft<double, 8>(double2* v) { dft8<double>(v); }
-template <>
-__device__ __forceinline__ void dft<float, 8>(float2* v) { dft8<float>(v); }
 
 // 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle W16^(n2 k1), DFT4 over
 // n2; outputs in natural order.  (c, s) below are cos and sin of 2 pi m / 16.
@@ -191,10 +192,14 @@ __device__ __forceinline__ void dft16(typename Cx<T>::type* v) {
     }
 }
 
-template <>
-__device__ __forceinline__ void dft<double, 16>(double2* v) { dft16<double>(v); }
-template <>
-__device__ __forceinline__ void dft<float, 16>(float2* v) { dft16<float>(v); }
+// R-point forward DFT of v in place (natural order out).
+template <typename T, int R>
+__device__ __forceinline__ void dft(typename Cx<T>::type* v) {
+    if constexpr (R == 2) bfly2<T>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<T>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<T>(v);
+    else dft16<T>(v);
+}
 
 // Padding: one slot after every 16 elements, so the stride-16 stores of a first radix-16
 // pass (thread j writes 16 j + r) hit distinct banks within every 128-byte wavefront for
@@ -202,6 +207,7 @@ __device__ __forceinline__ void dft<float, 16>(float2* v) { dft16<float>(v); }
 template <typename T> struct PadLog;
 template <> struct PadLog<double> { static constexpr int v = 4; };
 template <> struct PadLog<float> { static constexpr int v = 4; };
+template <> struct PadLog<dfl> { static constexpr int v = 4; };
 
 template <typename T>
 __device__ __forceinline__ int pad(int i) { return i + (i >> PadLog<T>::v); }
@@ -297,7 +303,7 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename
                 const C2* tw = ptw + ptw_offset<LOGN>(LOGNS) + k;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const C2 w = __ldg(tw + (r - 1) * Ns);
+                    const C2 w = ldc(tw + (r - 1) * Ns);
                     v[b][r] = cmul<T>(v[b][r], w.x, w.y);
                 }
             }
@@ -347,8 +353,9 @@ __device__ __forceinline__ int64_t seg_d(const Tile& tl, int g) {
 template <typename T, int NT, int MODE>
 __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile, T* ar, int s0, int count,
                                            int64_t roff) {
-    const T* __restrict__ y = A.y + roff;
-    const T* __restrict__ x = A.x + roff;
+    using I = In<T>;
+    const I* __restrict__ y = A.y + roff;
+    const I* __restrict__ x = A.x + roff;
     const double* __restrict__ yd = A.yd + roff;
     const int tid = threadIdx.x;
     const int PER = count / NT;
@@ -377,34 +384,35 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
         if constexpr (MODE == 0 || MODE == 2) {
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-                if constexpr (MODE == 0) v[u] = okv[u] ? y[tt[u]] : (T)0;
+                if constexpr (MODE == 0) v[u] = okv[u] ? (T)y[tt[u]] : (T)0;
                 else v[u] = okv[u] ? (T)yd[tt[u]] : (T)0;
             }
         } else {
+            // the gather (and d - P x) is formed in the precision of the data, I
             int q[UMAX];
-            typename Cx<T>::type w[UMAX];
-            T dv[UMAX];
+            typename Cx<I>::type w[UMAX];
+            I dv[UMAX];
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
                 q[u] = okv[u] ? __ldg(A.pixc + tt[u]) : -1;
                 if constexpr (IQU) {
                     if (okv[u]) w[u] = A.w[tt[u]];
                 }
-                if constexpr (MODE >= 4) dv[u] = okv[u] ? (T)yd[tt[u]] : (T)0;
+                if constexpr (MODE >= 4) dv[u] = okv[u] ? (I)yd[tt[u]] : (I)0;
             }
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-                T r = (T)0;
+                I r = (I)0;
                 if (q[u] >= 0) {
                     if constexpr (!IQU) {
                         r = __ldg(x + q[u]);
                     } else {
-                        const T* xq = x + 3 * (int64_t)q[u];
+                        const I* xq = x + 3 * (int64_t)q[u];
                         r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
                     }
                 }
-                if constexpr (MODE >= 4) v[u] = dv[u] - r;
-                else v[u] = r;
+                if constexpr (MODE >= 4) v[u] = (T)(dv[u] - r);
+                else v[u] = (T)r;
             }
         }
 #pragma unroll
@@ -419,11 +427,11 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
 
 // Store output n (block position lambda + n) at its time, unless it falls between segments.
 template <typename T>
-__device__ __forceinline__ void store_out(const Tile& tile, T* z, int lambda, int n, T v) {
+__device__ __forceinline__ void store_out(const Tile& tile, In<T>* z, int lambda, int n, T v) {
     bool in;
     const int p = n + lambda;
     const int g = tile_seg(tile, p, in);
-    if (in) z[p + seg_d(tile, g)] = v;
+    if (in) z[p + seg_d(tile, g)] = (In<T>)v;
 }
 
 // Real-FFT split of the packed spectrum at the bin pair (k, N - k), product with the real
@@ -496,7 +504,7 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // outputs: real block positions lambda .. lambda + nout - 1, stored at their times
-    T* zo = A.z + tr.rhs * A.out_stride;
+    In<T>* zo = A.z + tr.rhs * A.out_stride;
     for (int n = tid; n < tile.nout; n += NT) {
         const int i = n + A.lambda;
         const C2 v = a[pad<T>(i >> 1)];
@@ -609,7 +617,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) toeplitz_oscl_k
     __syncthreads();
     fft_all<T, LOGM, NT, 0>(a, A.ptw);
     cl.sync();
-    T* zo = A.z + tr.rhs * A.out_stride;
+    In<T>* zo = A.z + tr.rhs * A.out_stride;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int n1 = u * NT + tid;

@@ -21,6 +21,7 @@ MM_FP64, MM_FP32 = 0, 1
 MM_WINDOW_GAUSS, MM_WINDOW_RECT = 0, 1
 MM_PREC_BD, MM_PREC_TWOLEVEL, MM_PREC_ADEF2 = 0, 1, 2
 MM_SOLVE_FP64, MM_SOLVE_MIXED = 0, 1
+MM_RESID_DF32, MM_RESID_FP64 = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 4: "MM_ERR_NOT_SPD",
                 5: "MM_ERR_NOT_CONVERGED", 6: "MM_ERR_NUMERIC", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_STATE"}
@@ -32,7 +33,7 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
            "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
            "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi", "mm_solve_history",
-           "mm_pcg_barrier_check"]
+           "mm_pcg_barrier_check", "mm_residual"]
 
 
 class mm_psd(ctypes.Structure):
@@ -58,7 +59,7 @@ class mm_stats(ctypes.Structure):
 class mm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol_min", ctypes.c_double),
-                ("first_inner_tol", ctypes.c_double)]
+                ("first_inner_tol", ctypes.c_double), ("residual", ctypes.c_int32)]
 
 
 class MMError(RuntimeError):
@@ -104,6 +105,7 @@ _SIGS = {
     "mm_profile_read": (I32, [P, P, P]),
     "mm_solve_history": (I32, [P, I32, P, P]),
     "mm_pcg_barrier_check": (I32, [P, I32, ctypes.c_double]),
+    "mm_residual": (I32, [P, ctypes.c_int, P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
     "mm_destroy": (None, [P]),
     "mm_version": (ctypes.c_char_p, []),
@@ -316,6 +318,10 @@ def mm_solve_history(plan):
     return h[: cnt.value]
 
 
+def mm_residual(plan, arith, d, x, r):
+    _check(lib().mm_residual(plan, int(arith), _ptr(d), _ptr(x), _ptr(r)), plan)
+
+
 def mm_pcg_barrier_check(plan, absent_blocks, wait_s):
     """Status of a PCG start whose grid barrier waits for `absent_blocks` blocks that are
     never launched, each wait limited to wait_s seconds (MM_ERR_TIMEOUT when > 0)."""
@@ -495,7 +501,7 @@ class Plan:
 
     def solve(self, d, tol=1e-6, maxit=1000, kind=MM_PREC_BD, solver=MM_SOLVE_FP64, out=None,
               raise_on_error=True, **extra):
-        """extra: max_outer, inner_tol_min, first_inner_tol (mm_solve_opts)."""
+        """extra: max_outer, inner_tol_min, first_inner_tol, residual (mm_solve_opts)."""
         _expect(d, "float64", self.nt, "d")
         _expect(out, "float64", self.n, "out")
         m = self._new(self.n, MM_FP64) if out is None else out
@@ -503,7 +509,8 @@ class Plan:
             o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=kind, solver=solver,
                               max_outer=int(extra.get("max_outer", 0)),
                               inner_tol_min=float(extra.get("inner_tol_min", 0.0)),
-                              first_inner_tol=float(extra.get("first_inner_tol", 0.0)))
+                              first_inner_tol=float(extra.get("first_inner_tol", 0.0)),
+                              residual=int(extra.get("residual", MM_RESID_DF32)))
             self._sync_in()
             status, st = mm_solve_ex(self.handle, d, o, m, raise_on_error)
         else:
@@ -553,7 +560,8 @@ class Plan:
         o = mm_solve_opts(tol=float(tol), maxit=int(maxit), kind=MM_PREC_BD, solver=MM_SOLVE_MIXED,
                           max_outer=int(extra.get("max_outer", 0)),
                           inner_tol_min=float(extra.get("inner_tol_min", 0.0)),
-                          first_inner_tol=float(extra.get("first_inner_tol", 0.0)))
+                          first_inner_tol=float(extra.get("first_inner_tol", 0.0)),
+                          residual=int(extra.get("residual", MM_RESID_DF32)))
         self._sync_in()
         status, st = mm_solve_batch(self.handle, D, R, o, M, raise_on_error)
         return M, st, status
@@ -570,6 +578,16 @@ class Plan:
     def solve_history(self):
         """Relative recursive residual after each A p of the last solve (Sec. 5.1)."""
         return mm_solve_history(self.handle)
+
+    def residual(self, d, x, arith=MM_RESID_DF32, out=None):
+        """r = P^T N^-1 (d - P x) (FP64 data; band product in double-float or FP64)."""
+        _expect(d, "float64", self.nt, "d")
+        _expect(x, "float64", self.n, "x")
+        _expect(out, "float64", self.n, "out")
+        r = self._new(self.n, MM_FP64) if out is None else out
+        self._sync_in()
+        mm_residual(self.handle, arith, d, x, r)
+        return r
 
     def barrier_check(self, absent_blocks, wait_s):
         """Status (int) of the bounded-wait diagnostic mm_pcg_barrier_check."""

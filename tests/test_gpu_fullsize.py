@@ -122,6 +122,15 @@ def test_operators_at_the_benchmark_kernel_shape(prec):
     ar = pr.A(x, route="fft")
     assert np.abs(ax - ar).max() <= tol_a * np.abs(ar).max()
     assert _rel(ax, ar) <= tol_a
+    if prec == mm.MM_FP64:
+        # the refinement residual of the mixed solver at this shape: double-float and FP64
+        # band products against the oracle's b - A x, within 1e-12 of ||b||
+        d = y + pr.P(rng.standard_normal(pr.n))
+        b = pr.rhs(d, route="fft")
+        ref = b - ar
+        for arith in (mm.MM_RESID_DF32, mm.MM_RESID_FP64):
+            r = plan.residual(torch.from_numpy(d).cuda(), torch.from_numpy(x).cuda(), arith).cpu().numpy()
+            assert np.linalg.norm(r - ref) <= 1e-12 * np.linalg.norm(b), arith
     plan.close()
 
 

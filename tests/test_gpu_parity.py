@@ -179,6 +179,23 @@ def test_solve_mixed_reaches_tolerance(case, tol):
     assert _rel(mm_, mstar) <= kappa_b * (tol + 1e-12)
 
 
+@pytest.mark.parametrize("arith", [mm.MM_RESID_FP64, mm.MM_RESID_DF32])
+def test_residual_from_data(case, arith):
+    """r = P^T N^-1 (d - P x) (Eq. 5, 7) against the oracle's b - A x: the FP64 band
+    product and the double-float one (pairs of FP32 numbers, ~48-bit significands) both
+    within 1e-12 of ||b||, x = 0 giving b itself."""
+    name, scan, pr, plan = case
+    d = _data(scan)
+    b = pr.rhs(d, route="fft")
+    x = np.random.default_rng(8).standard_normal(pr.n)
+    ref = b - pr.A(x, route="fft")
+    r = plan.residual(_cuda(d), _cuda(x), arith).cpu().numpy()
+    assert np.linalg.norm(r - ref) <= 1e-12 * np.linalg.norm(b)
+    assert np.abs(r - ref).max() <= 1e-12 * np.abs(b).max()
+    r0 = plan.residual(_cuda(d), _cuda(np.zeros(pr.n)), arith).cpu().numpy()
+    assert np.linalg.norm(r0 - b) <= 1e-12 * np.linalg.norm(b)
+
+
 def test_residual_history(case):
     """||r_j|| / ||b|| per step (the Sec. 5.1 convergence measure) against the oracle's
     PCG on the same system: equal start, the stopping rule on the last two entries, and
