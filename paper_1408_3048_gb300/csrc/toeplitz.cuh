@@ -283,13 +283,26 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename
     constexpr int BPT = NB / NT;
     constexpr int Ns = 1 << LOGNS;
     static_assert(BPT >= 1 && NB % NT == 0, "butterflies per thread");
+    // pad(i + r S) = pad(i) + r (S + S/16) when S is a multiple of 16 (and, for S = 1,
+    // when i is and r < 16): one base address per butterfly and constant offsets
+    constexpr int PADL = 1 << PadLog<T>::v;
+    constexpr bool LD_CONST = NB % PADL == 0;
+    constexpr bool ST_CONST = Ns % PADL == 0 || (Ns == 1 && R <= PADL);
+    constexpr int LD_STEP = NB + (NB >> PadLog<T>::v);
+    constexpr int ST_STEP = Ns % PADL == 0 ? Ns + (Ns >> PadLog<T>::v) : 1;
     C2 v[BPT][R];
     const int tid = threadIdx.x;
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int j = tid + b * NT;
+        if constexpr (LD_CONST) {
+            const C2* src = a + pad<T>(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b][r] = a[pad<T>(j + r * NB)];
+            for (int r = 0; r < R; ++r) v[b][r] = src[r * LD_STEP];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = a[pad<T>(j + r * NB)];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -310,8 +323,14 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::type* a, const typename
         }
         dft<T, R>(v[b]);
         const int idx = ((j - k) << LOGR) + k;
+        if constexpr (ST_CONST) {
+            C2* dst = a + pad<T>(idx);
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[pad<T>(idx + r * Ns)] = v[b][r];
+            for (int r = 0; r < R; ++r) dst[r * ST_STEP] = v[b][r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[pad<T>(idx + r * Ns)] = v[b][r];
+        }
     }
     __syncthreads();
 }
@@ -363,6 +382,7 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
     constexpr int UMAX = IQU ? 4 : 8;
     const bool whole = tile.pb[0] <= s0 && s0 + count <= tile.pe[0];
     const int64_t d0 = tile.d[0];
+    const int sbase = 2 * pad<T>(tid >> 1) + (tid & 1);   // real slot of local position tid
 #pragma unroll 1
     for (int base = 0; base < PER; base += UMAX) {
         T v[UMAX];
@@ -418,8 +438,15 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
 #pragma unroll
         for (int u = 0; u < UMAX; ++u) {
             if (base + u < PER) {
-                const int sidx = (base + u) * NT + tid;
-                ar[2 * pad<T>(sidx >> 1) + (sidx & 1)] = v[u];
+                if constexpr (NT % (2 << PadLog<T>::v) == 0) {
+                    // sidx = (base + u) NT + tid with NT a multiple of 2 * 16: the padded
+                    // slot is a per-thread base plus a per-round constant
+                    constexpr int RSTEP = 2 * (NT / 2 + (NT >> (PadLog<T>::v + 1)));
+                    ar[sbase + (base + u) * RSTEP] = v[u];
+                } else {
+                    const int sidx = (base + u) * NT + tid;
+                    ar[2 * pad<T>(sidx >> 1) + (sidx & 1)] = v[u];
+                }
             }
         }
     }
@@ -505,10 +532,20 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // outputs: real block positions lambda .. lambda + nout - 1, stored at their times
     In<T>* zo = A.z + tr.rhs * A.out_stride;
-    for (int n = tid; n < tile.nout; n += NT) {
-        const int i = n + A.lambda;
-        const C2 v = a[pad<T>(i >> 1)];
-        store_out<T>(tile, zo, A.lambda, n, (i & 1) ? -v.y : v.x);
+    if (tile.pb[0] <= A.lambda && A.lambda + tile.nout <= tile.pe[0]) {
+        // every output inside the first segment: time = position + d[0]
+        In<T>* z0 = zo + tile.d[0];
+        for (int n = tid; n < tile.nout; n += NT) {
+            const int i = n + A.lambda;
+            const C2 v = a[pad<T>(i >> 1)];
+            z0[i] = (In<T>)((i & 1) ? -v.y : v.x);
+        }
+    } else {
+        for (int n = tid; n < tile.nout; n += NT) {
+            const int i = n + A.lambda;
+            const C2 v = a[pad<T>(i >> 1)];
+            store_out<T>(tile, zo, A.lambda, n, (i & 1) ? -v.y : v.x);
+        }
     }
 }
 
