@@ -701,11 +701,14 @@ def run_batched(scan, dev, lams=(1024, 4096, 16384), R=BATCH_R, nbase=4):
     C /= np.linalg.norm(C, axis=1, keepdims=True)
     D = signal[None, :] + torch.from_numpy(C).to(dev) @ base
     del base
-    out = {"R": R, "tol": TOL, "noise": f"unit-norm combinations of {nbase} realisations (seeds 2400..)"}
+    out = {"R": R, "tol": TOL, "noise": f"unit-norm combinations of {nbase} realisations (seeds 2400..)",
+           "forms": "the plan autotunes: one batched A X timed per form (0 pair FFT, 1 real FFT, 2 tensor-core "
+                    "band product), the fastest kept"}
     for lam in lams:
         sc = synth.config(CONFIG)
         sc.lam = lam
-        plan = mm.Plan(sc.pix, sc.npix_sky, sc.weights, sc.offsets, sc.interval_psd, sc.psds, lam, sc.fsamp)
+        plan = mm.Plan(sc.pix, sc.npix_sky, sc.weights, sc.offsets, sc.interval_psd, sc.psds, lam, sc.fsamp,
+                       autotune=True)
         kind, logb, tm = plan.batch_config(R)
         M = torch.empty((R, plan.n), dtype=torch.float64, device=dev)
         plan.solve_batch(D, tol=TOL, maxit=5000, out=M)     # warm-up (graph capture)
@@ -727,7 +730,9 @@ def run_batched(scan, dev, lams=(1024, 4096, 16384), R=BATCH_R, nbase=4):
         out[f"lambda_{lam}"] = {"s_per_map": ts / R, "s_total": ts, "status": int(status),
                                 "converged": int(sum(x["converged"] for x in st)),
                                 "iters_max": int(max(x["iters"] for x in st)),
-                                "form": "pair" if kind == 0 else "real", "log2_block": int(logb),
+                                "form": ["pair", "real", "tensor"][kind], "log2_block": int(logb),
+                                "form_ax_ms": {"pair": round(tm[0], 3), "real": round(tm[1], 3),
+                                               "tensor": round(tm[2], 3)},
                                 "ax_batch_ms_per_column": ax_ms / R}
         plan.close()
         del M, X, Y

@@ -140,16 +140,22 @@ mm_status mm_autotune_read(mm_plan_t plan, float* ms_f64, float* ms_f32);
 /*
  * Form of the batched operator (mm_apply_A_batch, mm_solve_batch), fixed once per plan by
  * its first batched call or by this call; the paper has no counterpart.
- *   kind  (host, in/out) in: -1 = choose, 0 or 1 = use that form; out: the form in use.
+ *   kind  (host, in/out) in: -1 = choose, 0, 1 or 2 = use that form; out: the form in use.
  *         0: two right-hand sides per complex FFT of 2^log2_block points (real kernel
  *         spectrum: real and imaginary parts convolve independently);
  *         1: one real FFT per right-hand side with the FP32 block of mm_plan_info, the
- *         right-hand side as the fastest grid index.
- *         Choosing times both forms at R columns when the plan autotunes, else takes the
- *         cheaper by the cost model.  Asking for a form other than the fixed one, or one
- *         that no block supports for this lambda, is MM_ERR_ARG.
+ *         right-hand side as the fastest grid index;
+ *         2: the band product as a dense contraction on the tensor cores (tcgen05 MMAs in
+ *         FP16 on operands split as hi + 2^-11 lo after power-of-two scaling, FP32
+ *         accumulators in tensor memory; 128-row tiles, window 128 + 2 lambda; the maps
+ *         are de-pointed into a [R][nt] buffer first); log2_block reports 7 (the tile).
+ *         Choosing times all three forms at R columns when the plan autotunes, else takes
+ *         the cheaper FFT form by the cost model (the contraction costs 2 (2 lambda + 128)
+ *         flops per sample and column against ~10 log2 B for the FFT).  Asking for a form
+ *         other than the fixed one, or one that no block supports for this lambda, is
+ *         MM_ERR_ARG.
  *   R     1..64, the column count for the timing (and the buffers it allocates).
- *   log2_block, ms (host float[2]: timed launches of forms 0 and 1, or 0): may be NULL.
+ *   log2_block, ms (host float[3]: timed launches of forms 0, 1 and 2, or 0): may be NULL.
  */
 mm_status mm_batch_config(mm_plan_t plan, int32_t R, int32_t* kind, int32_t* log2_block, float* ms);
 

@@ -123,11 +123,11 @@ void prof_flush(Plan& P) {
 
 // ----------------------------------------------------------------------------- plan
 // Buffers of the batched (many right-hand sides) solver, allocated on first use.
-enum { BATCH_PAIR = 0, BATCH_REAL = 1 };
+enum { BATCH_PAIR = 0, BATCH_REAL = 1, BATCH_TENSOR = 2 };
 
 struct BatchState {
-    int kind = -1;                // BATCH_PAIR / BATCH_REAL, -1 before the first batched call
-    float tuned_ms[2] = {};       // timed forms (autotuning), 0 when not timed
+    int kind = -1;                // BATCH_PAIR / BATCH_REAL / BATCH_TENSOR, -1 before the first call
+    float tuned_ms[3] = {};       // timed forms (autotuning), 0 when not timed
     int logb = 0;                 // complex FFT length of the pair kernel
     int ntiles = 0;
     SpanTile* tiles = nullptr;
@@ -143,6 +143,15 @@ struct BatchState {
     int* flags = nullptr;
     unsigned* bar = nullptr;
     int nblocks = 0;
+    // tensor-core form (batch_tc.cu)
+    SpanTile* tc_groups = nullptr;
+    int tc_ngroups = 0;
+    int tc_nchunk = 0;
+    __half* tc_atab = nullptr;    // [npsd][nchunk][hi, lo][128 x 64] band chunks
+    float* tc_invc = nullptr;     // [npsd]
+    float* tc_y = nullptr;        // [cap][nt] P X
+    float* tc_scale = nullptr;    // [2][BATCH_RMAX] column scales, inverses
+    int tc_cap = 0;
     cudaGraphExec_t graph = nullptr;   // `graph_iters` batched iterations, or null
     int graph_R = -1;             // R and maxit the graph was captured with
     int graph_maxit = -1;
@@ -230,7 +239,8 @@ static void destroy_plan(PlanHolder* P) {
                     (void*)bt.p, (void*)bt.q, (void*)bt.z,
                     (void*)bt.tod, (void*)bt.x64, (void*)bt.b64, (void*)bt.r64, (void*)bt.partial, (void*)bt.rho,
                     (void*)bt.bb, (void*)bt.rr, (void*)bt.tol2, (void*)bt.iters, (void*)bt.state, (void*)bt.flags,
-                    (void*)bt.bar})
+                    (void*)bt.bar, (void*)bt.tc_groups, (void*)bt.tc_atab, (void*)bt.tc_invc, (void*)bt.tc_y,
+                    (void*)bt.tc_scale})
         dfree(p);
     delete P;
 }
@@ -1581,6 +1591,82 @@ static void build_batch_pair(PlanHolder& P, int logb) {
     sync(P.stream);
 }
 
+// Tables of the tensor-core form: groups of four 128-row tiles per interval, and per PSD
+// the K-chunks (64 wide) of the band matrix A[m][k] = c[k - m], c[j] = t_|j - lambda|
+// (0 <= j <= 2 lambda), scaled by a power of two (largest |c| below 2^14) and split into
+// FP16 hi + 2^-11 lo, each chunk in the no-swizzle K-major core-matrix layout (element
+// (m, kk) at byte (m / 8) 1024 + (kk / 8) 128 + (m % 8) 16 + (kk % 8) 2).
+static void build_batch_tc(PlanHolder& P) {
+    BatchState& bt = P.batch;
+    if (bt.tc_atab != nullptr) return;
+    constexpr int M = 128, KC = 64, G = 4;
+    const int64_t lam = P.lambda;
+    const int nchunk = (int)((M + 2 * lam + KC - 1) / KC);
+    std::vector<SpanTile> groups;
+    for (int i = 0; i < P.K; ++i) {
+        const int64_t a = P.h_ioff[i], b = P.h_ioff[i + 1];
+        for (int64_t s0 = a; s0 < b; s0 += M * G)
+            groups.push_back(SpanTile{s0, a, b, (int32_t)std::min<int64_t>(M * G, b - s0), P.h_ipsd[i]});
+    }
+    const size_t per_chunk = 2 * (size_t)M * KC;   // halves
+    std::vector<__half> tab((size_t)P.npsd * nchunk * per_chunk);
+    std::vector<float> invc((size_t)P.npsd);
+    for (int p = 0; p < P.npsd; ++p) {
+        const std::vector<double>& row = P.rows[(size_t)p];
+        double mx = 0.0;
+        for (double v : row) mx = std::max(mx, std::fabs(v));
+        int e = 0;
+        if (mx > 0.0) std::frexp(mx, &e);   // mx < 2^e
+        const double sc = std::ldexp(1.0, 14 - e);
+        invc[(size_t)p] = (float)std::ldexp(1.0, e - 14);
+        for (int c = 0; c < nchunk; ++c) {
+            __half* hi = tab.data() + ((size_t)p * nchunk + c) * per_chunk;
+            __half* lo = hi + (size_t)M * KC;
+            for (int m = 0; m < M; ++m)
+                for (int kk = 0; kk < KC; ++kk) {
+                    const int64_t j = (int64_t)c * KC + kk - m;
+                    const double v = (j >= 0 && j <= 2 * lam) ? row[(size_t)std::llabs(j - lam)] * sc : 0.0;
+                    const float vf = (float)v;
+                    const __half h = __float2half_rn(vf);
+                    const __half l = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
+                    const size_t off = (size_t)((m / 8) * 1024 + (kk / 8) * 128 + (m % 8) * 16 + (kk % 8) * 2) / 2;
+                    hi[off] = h;
+                    lo[off] = l;
+                }
+        }
+    }
+    try {
+        bt.tc_groups = dalloc<SpanTile>(groups.size());
+        h2d(bt.tc_groups, groups.data(), groups.size() * sizeof(SpanTile), P.stream);
+        bt.tc_atab = dalloc<__half>(tab.size());
+        h2d(bt.tc_atab, tab.data(), tab.size() * sizeof(__half), P.stream);
+        bt.tc_invc = dalloc<float>(invc.size());
+        h2d(bt.tc_invc, invc.data(), invc.size() * 4, P.stream);
+        bt.tc_scale = dalloc<float>(2 * BATCH_RMAX);
+        sync(P.stream);
+    } catch (...) {
+        for (void* q : {(void*)bt.tc_groups, (void*)bt.tc_atab, (void*)bt.tc_invc, (void*)bt.tc_scale}) dfree(q);
+        bt.tc_groups = nullptr;
+        bt.tc_atab = nullptr;
+        bt.tc_invc = nullptr;
+        bt.tc_scale = nullptr;
+        throw;
+    }
+    bt.tc_ngroups = (int)groups.size();
+    bt.tc_nchunk = nchunk;
+}
+
+static void ensure_batch_tc_buffer(PlanHolder& P, int R) {
+    BatchState& bt = P.batch;
+    if (bt.tc_cap >= R) return;
+    dfree(bt.tc_y);
+    bt.tc_y = nullptr;
+    bt.tc_cap = 0;
+    bt.tc_y = dalloc<float>((size_t)P.nt * R);
+    bt.tc_cap = R;
+}
+
+static void launch_batch_tz(PlanHolder& P, int R, const float* X, float* Z, const int* done);
 static void launch_batch_tz(PlanHolder& P, int R, const float* X, float* Z, const int* done);
 
 // Batched Toeplitz form, chosen once per plan (before any graph capture), after the
@@ -1595,6 +1681,13 @@ static void ensure_batch_tables(PlanHolder& P, int R, int want = -1) {
     BatchState& bt = P.batch;
     if (bt.kind >= 0) {
         if (want >= 0 && want != bt.kind) throw Error{MM_ERR_ARG, "the batched form is already fixed"};
+        if (bt.kind == BATCH_TENSOR) ensure_batch_tc_buffer(P, R);
+        return;
+    }
+    if (want == BATCH_TENSOR) {
+        build_batch_tc(P);
+        ensure_batch_tc_buffer(P, R);
+        bt.kind = BATCH_TENSOR;
         return;
     }
     int best = -1;
@@ -1626,12 +1719,29 @@ static void ensure_batch_tables(PlanHolder& P, int R, int want = -1) {
     } else if (real_cost < 0.0) {
         bt.kind = BATCH_PAIR;
     } else if (P.autotune) {
-        check_cuda(cudaMemsetAsync(bt.x, 0, (size_t)R * P.n * 4, P.stream), "memset");
+        // every form timed on the same R columns (random maps: the tensor form scales
+        // its columns by their largest value); the fastest is kept
+        {
+            std::vector<float> hx((size_t)R * P.n);
+            uint64_t st = 0x2545F4914F6CDD1Dull;
+            for (auto& v : hx) {
+                st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+                v = (float)((double)(st >> 11) / 9007199254740992.0 - 0.5);
+            }
+            h2d(bt.x, hx.data(), hx.size() * 4, P.stream);
+            sync(P.stream);
+        }
         bt.kind = BATCH_PAIR;
         bt.tuned_ms[0] = time_launches(P, [&] { launch_batch_tz(P, R, bt.x, bt.tod, nullptr); }, 3);
         bt.kind = BATCH_REAL;
         bt.tuned_ms[1] = time_launches(P, [&] { launch_batch_tz(P, R, bt.x, bt.tod, nullptr); }, 3);
-        bt.kind = bt.tuned_ms[0] <= bt.tuned_ms[1] ? BATCH_PAIR : BATCH_REAL;
+        build_batch_tc(P);
+        ensure_batch_tc_buffer(P, R);
+        bt.kind = BATCH_TENSOR;
+        bt.tuned_ms[2] = time_launches(P, [&] { launch_batch_tz(P, R, bt.x, bt.tod, nullptr); }, 3);
+        int k = bt.tuned_ms[0] <= bt.tuned_ms[1] ? BATCH_PAIR : BATCH_REAL;
+        if (bt.tuned_ms[2] < bt.tuned_ms[k]) k = BATCH_TENSOR;
+        bt.kind = k;
     } else {
         bt.kind = best_cost <= real_cost ? BATCH_PAIR : BATCH_REAL;
     }
@@ -1687,10 +1797,32 @@ static BatchTzArgs batch_tz_args(PlanHolder& P, int R, const float* X, float* Z,
 
 // Z_r = N^-1 P X_r (FP32) in the plan's batched form
 static void launch_batch_tz(PlanHolder& P, int R, const float* X, float* Z, const int* done) {
-    if (P.batch.kind == BATCH_REAL)
+    BatchState& bt = P.batch;
+    if (bt.kind == BATCH_REAL) {
         launch_toeplitz_rhs<float>(P, P.tz32, nullptr, X, R, P.n, Z, P.nt, done, P.stream);
-    else
-        launch_batch_toeplitz(batch_tz_args(P, R, X, Z, done), P.batch.logb, P.batch.ntiles, P.ncomp, P.stream);
+    } else if (bt.kind == BATCH_TENSOR) {
+        // column scales from the maps, Y = P X, then the band product on the tensor cores
+        launch_batch_colscale(X, P.n, R, bt.tc_scale, bt.tc_scale + BATCH_RMAX, P.stream);
+        launch_batch_gather(P, X, R, bt.tc_y, P.stream);
+        BatchTcArgs A{};
+        A.groups = bt.tc_groups;
+        A.atab = bt.tc_atab;
+        A.inv_cscale = bt.tc_invc;
+        A.Y = bt.tc_y;
+        A.Z = Z;
+        A.scale = bt.tc_scale;
+        A.inv_scale = bt.tc_scale + BATCH_RMAX;
+        A.done = done;
+        A.flags = bt.flags;
+        A.nt = P.nt;
+        A.R = R;
+        A.RB = (R + 15) / 16 * 16;
+        A.lambda = P.lambda;
+        A.nchunk = bt.tc_nchunk;
+        launch_batch_tc(A, bt.tc_ngroups, P.stream);
+    } else {
+        launch_batch_toeplitz(batch_tz_args(P, R, X, Z, done), bt.logb, bt.ntiles, P.ncomp, P.stream);
+    }
 }
 
 // Y_r = A X_r (FP32), r < R <= BATCH_RMAX
@@ -2283,16 +2415,17 @@ mm_status mm_batch_config(mm_plan_t plan, int32_t R, int32_t* kind, int32_t* log
     return guarded(plan, [&] {
         PlanHolder* P = get(plan);
         if (R < 1 || R > BATCH_RMAX) throw Error{MM_ERR_ARG, "need 1 <= R <= 64"};
-        if (kind == nullptr || *kind < -1 || *kind > 1) throw Error{MM_ERR_ARG, "kind must point to -1, 0 or 1"};
+        if (kind == nullptr || *kind < -1 || *kind > 2) throw Error{MM_ERR_ARG, "kind must point to -1, 0, 1 or 2"};
         ensure_batch_buffers(*P, R);
         ensure_batch_tables(*P, R, *kind);
         sync(*P);
         const BatchState& bt = P->batch;
         *kind = bt.kind;
-        if (log2_block) *log2_block = bt.kind == BATCH_REAL ? P->tz32.logn + 1 : bt.logb;
+        if (log2_block) *log2_block = bt.kind == BATCH_REAL ? P->tz32.logn + 1 : (bt.kind == BATCH_TENSOR ? 7 : bt.logb);
         if (ms) {
             ms[0] = bt.tuned_ms[0];
             ms[1] = bt.tuned_ms[1];
+            ms[2] = bt.tuned_ms[2];
         }
     });
 }

@@ -1,6 +1,8 @@
 // Batched (many right-hand sides) kernels and their arguments (see batch.cu).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "mm_internal.h"
 
 namespace mm {
@@ -50,6 +52,30 @@ struct BatchPcgArgs {
     unsigned bar_absent;           // 0 (see grid_sync)
     unsigned long long wait_ns;    // limit of each barrier wait
 };
+
+// Tensor-core form (batch_tc.cu): banded product as FP16 split-operand MMAs, four
+// 128-row tiles of one interval and up to 64 columns per CTA (groups: out0 = first
+// output, [ibeg, iend) = its interval, nout <= 512 outputs).
+struct BatchTcArgs {
+    const SpanTile* groups;
+    const __half* atab;        // [npsd][nchunk][hi, lo][128 x 64] band chunks, canonical layout
+    const float* inv_cscale;   // [npsd] 1 / (power-of-two scale of the band row)
+    const float* Y;            // [R][nt] P X
+    float* Z;                  // [R][nt] N^-1 P X
+    const float* scale;        // [R] power-of-two column scales and their inverses
+    const float* inv_scale;
+    const int* done;
+    int* flags;                // F_STATUS / F_DONE on a wait that runs out
+    int64_t nt;
+    int R;
+    int RB;                    // columns per tile: R rounded up to 16
+    int lambda;
+    int nchunk;                // K chunks of 64: (128 + 2 lambda) / 64 rounded up
+};
+size_t batch_tc_smem();
+void launch_batch_tc(const BatchTcArgs& A, int ngroups, cudaStream_t s);
+void launch_batch_gather(const Plan& P, const float* X, int R, float* Y, cudaStream_t s);
+void launch_batch_colscale(const float* X, int64_t n, int R, float* scale, float* inv_scale, cudaStream_t s);
 
 size_t batch_toeplitz_smem(int logb);
 void launch_batch_toeplitz(const BatchTzArgs& A, int logb, int ntiles, int ncomp, cudaStream_t s);

@@ -21,6 +21,7 @@ MM_FP64, MM_FP32 = 0, 1
 MM_WINDOW_GAUSS, MM_WINDOW_RECT = 0, 1
 MM_PREC_BD, MM_PREC_TWOLEVEL, MM_PREC_ADEF2 = 0, 1, 2
 MM_SOLVE_FP64, MM_SOLVE_MIXED = 0, 1
+MM_BATCH_PAIR, MM_BATCH_REAL, MM_BATCH_TENSOR = 0, 1, 2
 MM_RESID_DF32, MM_RESID_FP64 = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_CUDA", 3: "MM_ERR_OOM", 4: "MM_ERR_NOT_SPD",
@@ -212,10 +213,10 @@ def mm_autotune_read(plan):
 
 
 def mm_batch_config(plan, R, kind=-1):
-    """(kind, log2_block, [ms_pair, ms_real]) of the batched operator for R columns."""
+    """(kind, log2_block, [ms_pair, ms_real, ms_tensor]) of the batched operator for R columns."""
     kind = ctypes.c_int32(int(kind))
     lb = ctypes.c_int32()
-    ms = (ctypes.c_float * 2)()
+    ms = (ctypes.c_float * 3)()
     _check(lib().mm_batch_config(plan, int(R), ctypes.byref(kind), ctypes.byref(lb), ms), plan)
     return kind.value, lb.value, list(ms)
 

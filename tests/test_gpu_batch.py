@@ -27,11 +27,12 @@ def _plan(scan, stream=None, **kw):
                    scan.lam, scan.fsamp, stream=stream, **kw)
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("R", [1, 2, 5, 64])
 def test_batched_operator(name, R, kind):
-    # kind 0: two columns per complex FFT; kind 1: one real FFT per column
+    # kind 0: two columns per complex FFT; kind 1: one real FFT per column; kind 2: the
+    # band product on the tensor cores (FP16 split operands, FP32 accumulators)
     scan = CASES[name]()
     pr = oracle_problem(scan)
     plan = _plan(scan)
@@ -113,12 +114,32 @@ def test_batched_form_autotuned_and_fixed():
     scan = CASES["P"]()
     plan = _plan(scan, autotune=True)
     kind, lb, ms = plan.batch_config(8)
-    assert kind in (0, 1) and ms[0] > 0 and ms[1] > 0
-    assert kind == (0 if ms[0] <= ms[1] else 1)
+    assert kind in (0, 1, 2) and ms[0] > 0 and ms[1] > 0 and ms[2] > 0
+    assert kind == int(np.argmin(ms))
     with pytest.raises(mm.MMError) as e:          # the form is fixed once chosen
-        plan.batch_config(8, 1 - kind)
+        plan.batch_config(8, (kind + 1) % 3)
     assert e.value.status == mm.MM_ERR_ARG
     assert plan.batch_config(8, kind)[0] == kind
+    plan.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_batched_solve_tensor_form(name):
+    # the batched solver on the tensor-core operator: every column reaches the tolerance
+    # in the oracle's FP64 arithmetic
+    scan = CASES[name]()
+    pr = oracle_problem(scan)
+    R = 5
+    D = _data(scan, R, 300)
+    plan = _plan(scan, stream=torch.cuda.Stream())
+    assert plan.batch_config(R, 2)[0] == 2
+    M, st, status = plan.solve_batch(torch.from_numpy(D).cuda(), tol=1e-6, maxit=5000)
+    assert status == mm.MM_OK
+    Mh = M.cpu().numpy()
+    for r in range(R):
+        b = pr.rhs(D[r])
+        assert st[r]["converged"] == 1
+        assert np.linalg.norm(b - pr.A(Mh[r])) / np.linalg.norm(b) <= 1e-6, r
     plan.close()
 
 
@@ -134,7 +155,7 @@ def test_batched_rejects_unsupported_options():
     plan.close()
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("lam", [8192, 16384])
 def test_batched_operator_cluster_blocks(lam, kind):
     # bands beyond the single-CTA complex block (2^14 points) take the 2-CTA (2^15) and
@@ -146,7 +167,7 @@ def test_batched_operator_cluster_blocks(lam, kind):
     plan = _plan(scan)
     R = 3
     k, lb, _ = plan.batch_config(R, kind)
-    assert k == kind and lb >= (15 if lam == 8192 else 16)
+    assert k == kind and (lb >= (15 if lam == 8192 else 16) if kind != 2 else lb == 7)
     X = torch.randn(R, plan.n, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(lam))
     Y = plan.apply_A_batch(X).cpu().numpy()
     Xh = X.double().cpu().numpy()
