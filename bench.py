@@ -146,10 +146,34 @@ def peaks():
 ALU_PEAK = {"f64": 1.25e12, "f32": 152 * 128 * 2 * 2.07e9}
 
 
-def fft_tiles(scan, B):
-    Lv = B - 2 * scan.lam
-    lens = np.diff(scan.offsets)
-    return int(np.sum((lens + Lv - 1) // Lv))
+def fft_tiles(scan, B, max_segments=3):
+    """Overlap-save tiles of B-sample blocks as the plan lays them out: consecutive
+    intervals with the same PSD are packed into one sequence with lambda zeros between
+    them when that needs fewer tiles (and no tile holds more than `max_segments`
+    intervals), else every interval is tiled on its own."""
+    lam = int(scan.lam)
+    Lv = B - 2 * lam
+    lens = np.diff(np.asarray(scan.offsets, dtype=np.int64))
+    psd = np.asarray(getattr(scan, "interval_psd", np.arange(lens.size)))
+    total, i0 = 0, 0
+    while i0 < lens.size:
+        i1 = i0 + 1
+        while i1 < lens.size and psd[i1] == psd[i0]:
+            i1 += 1
+        single = int(np.sum((lens[i0:i1] + Lv - 1) // Lv))
+        starts = np.concatenate([[0], np.cumsum(lens[i0:i1] + lam)[:-1]])
+        vlen = int(lens[i0:i1].sum() + (i1 - i0 - 1) * lam)
+        packed = (vlen + Lv - 1) // Lv
+        ok = True
+        for k in range(packed):
+            w0 = k * Lv - lam
+            seg = np.sum((starts < w0 + B) & (starts + lens[i0:i1] > w0))
+            if seg > max_segments:
+                ok = False
+                break
+        total += packed if (i1 - i0 > 1 and ok and packed < single) else single
+        i0 = i1
+    return total
 
 
 # Sources whose text fixes each profiled kernel: the DRAM traffic recorded from an ncu capture
@@ -157,6 +181,7 @@ def fft_tiles(scan, B):
 KERNEL_SOURCES = {
     "toeplitz_f32": ["toeplitz.cuh", "toeplitz_f32.cu"],
     "toeplitz_f64": ["toeplitz.cuh", "toeplitz_f64.cu"],
+    "toeplitz_df": ["toeplitz.cuh", "dfloat.cuh", "toeplitz_df.cu", "toeplitz_df_cluster.cu"],
     "scatter_f32": ["pointing.cu"],
     "scatter_f64": ["pointing.cu"],
     "pcg_f32": ["pcg.cu", "pcg.cuh"],

@@ -336,8 +336,9 @@ mm_status mm_solve(mm_plan_t plan, const double* d, double tol, int maxit, int k
 /*
  * Per-stage device timers.  mm_profile(plan, 1) clears and enables them: every later
  * launch of the Toeplitz kernel (stage 0 FP64, 1 FP32; de-pointing fused or not), the
- * scatter kernel (2 FP64, 3 FP32) and the PCG vector kernel (4 FP64, 5 FP32) is
- * bracketed by CUDA events on the plan's stream (stages 6-7 are reserved).
+ * scatter kernel (2 FP64, 3 FP32), the PCG vector kernel (4 FP64, 5 FP32) and the
+ * double-float Toeplitz kernel of the refinement residual (6) is bracketed by CUDA events
+ * on the plan's stream (stage 7 is reserved).
  * mm_profile_read returns the summed milliseconds (host double[8]) and launch counts
  * (host int64[8]); either may be NULL.
  * The events add a few microseconds per launch; mm_profile(plan, 0) turns them off.

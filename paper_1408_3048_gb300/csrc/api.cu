@@ -1309,8 +1309,9 @@ static void check_solve_opts(const PlanHolder& P, const mm_solve_opts& so) {
 static void residual64(PlanHolder& P, const double* d, const double* x, double* r, bool df = false) {
     cudaStream_t s = P.stream;
     if (d != nullptr) {
-        int sl = prof_begin(P, ST_TZ64);
-        if (df && P.tzdf.logn != 0)
+        const bool use_df = df && P.tzdf.logn != 0;
+        int sl = prof_begin(P, use_df ? ST_TZDF : ST_TZ64);
+        if (use_df)
             launch_toeplitz_df(P, nullptr, d, x, 1, 0, P.tod64, 0, s);
         else
             launch_toeplitz_any<double>(P, P.tz64, nullptr, d, x, 1, 0, P.tod64, 0, nullptr, s);

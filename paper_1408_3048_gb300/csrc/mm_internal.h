@@ -85,7 +85,7 @@ struct PcgDev {
 };
 
 // Per-stage CUDA-event timers (enabled by mm_profile).
-enum { ST_TZ64 = 0, ST_TZ32 = 1, ST_SC64 = 2, ST_SC32 = 3, ST_PCG64 = 4, ST_PCG32 = 5, ST_COUNT = 8 };
+enum { ST_TZ64 = 0, ST_TZ32 = 1, ST_SC64 = 2, ST_SC32 = 3, ST_PCG64 = 4, ST_PCG32 = 5, ST_TZDF = 6, ST_COUNT = 8 };
 struct Prof {
     bool on = false;
     struct Pending {

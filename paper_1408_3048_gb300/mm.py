@@ -598,7 +598,7 @@ class Plan:
     def profile_read(self):
         """{stage: (total ms, launches)} per kernel and precision."""
         ms, n = mm_profile_read(self.handle)
-        names = ["toeplitz_f64", "toeplitz_f32", "scatter_f64", "scatter_f32", "pcg_f64", "pcg_f32"]
+        names = ["toeplitz_f64", "toeplitz_f32", "scatter_f64", "scatter_f32", "pcg_f64", "pcg_f32", "toeplitz_df"]
         return {nm: (float(ms[i]), int(n[i])) for i, nm in enumerate(names)}
 
     def close(self):

@@ -66,7 +66,7 @@ def test_roofline_algorithmic_bytes(kernel, ncomp):
         alu = r["alu"] if r["bound"] == "hbm" else r
         assert r["frac"] == max(hbm["frac"], alu["frac"])
         B = plan.fft_block_f32 if s == 4 else plan.fft_block_f64
-        assert bench.fft_tiles(scan, B) == 2 * -(-(1 << 19) // (B - 2 * 4096))
+        assert bench.fft_tiles(scan, B) == 2 * -(-(1 << 19) // (B - 2 * 4096))   # one PSD per interval
     else:
         assert r["bound"] == "hbm" and "alu" not in r
 
@@ -125,3 +125,20 @@ def test_peak_bandwidth_source(tmp_path, monkeypatch):
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6769.4}))
     assert bench.peaks() == (6769.4, "measured")
+
+
+def test_fft_tiles_packs_runs_of_one_psd():
+    """Two intervals of one PSD share tiles when the lambda gap between them saves a tile;
+    other PSDs stay apart; the count is that of the library's layout on the 2^24-sample
+    workload (736 tiles of 2^15 at lambda 4096, 821 without packing)."""
+    lam, B = 100, 1000   # 800 valid outputs per tile
+    scan = SimpleNamespace(lam=lam, offsets=np.array([0, 900, 1800, 2700]), interval_psd=np.array([0, 0, 1]))
+    # run [0, 1]: 2 x 2 single tiles vs ceil((1800 + 100) / 800) = 3 packed; interval 2: 2
+    assert bench.fft_tiles(scan, B) == 3 + 2
+    scan.interval_psd = np.array([0, 1, 2])
+    assert bench.fft_tiles(scan, B) == 6
+    from paper_1408_3048_gb300 import synth
+    c2 = synth.config(2)
+    assert bench.fft_tiles(c2, 1 << 15) == 736
+    c2.interval_psd = np.arange(len(c2.offsets) - 1)
+    assert bench.fft_tiles(c2, 1 << 15) == 821
