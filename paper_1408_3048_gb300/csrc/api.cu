@@ -803,13 +803,25 @@ static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstor
     check_cuda(cudaMemsetAsync(P.pcg.barrier, 0, sizeof(unsigned), s), "memset barrier");
     launch_pcg<T>(0, P.ncomp, cm, a, nb, s);
     int launched = 0;
-    int chunk = 4;
     PcgOutcome out;
     while (true) {
+        // poll the done flag, the step count and the residual; launch as many steps as the
+        // residual's average decay so far predicts are left (one more for margin, 2..16;
+        // 4 before any step): a step launched after convergence exits at once, a poll
+        // costs a host round trip
         d2h(P.h_flags, P.pcg.flags, 16, s);
+        d2h(P.h_scal + 4, P.pcg.scal, 4 * 8, s);
         sync(P);
         if (P.h_flags[F_DONE]) break;
         if (launched >= maxit) break;   // defensive: device counter stops at maxit
+        int chunk = 4;
+        const int done_steps = P.h_flags[F_ITER];
+        const double rr = P.h_scal[4 + SC_RR], bb0 = P.h_scal[4 + SC_BB], tol2 = P.h_scal[4 + SC_TOL2];
+        if (done_steps >= 2 && rr > 0.0 && bb0 > 0.0 && rr < bb0 && tol2 > 0.0) {
+            const double rate = std::log(rr / bb0) / done_steps;   // < 0
+            const double left = std::log(tol2 * bb0 / rr) / rate;
+            chunk = left <= 0.0 ? 2 : (int)std::min(16.0, std::max(2.0, std::ceil(left) + 1.0));
+        }
         const int c = std::min(chunk, maxit - launched + 1);
         for (int i = 0; i < c; ++i) {
             // q = A p with p^T q fused into the scatter (scal[SC_PQ])
@@ -826,7 +838,6 @@ static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstor
             prof_end(P, sl);
         }
         launched += c;
-        chunk = std::min(chunk * 2, 16);
     }
     d2h(P.h_scal + 4, P.pcg.scal, 4 * 8, s);
     sync(P);

@@ -178,69 +178,117 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
 }
 
 // z = M_BD r (CM 0), M_BD (r - AZ v) + Z v (CM 1) or y + Z v with y = M_BD r in a.z
-// (CM 2) on this block's pixels; returns partial r^T z.
+// (CM 2) on this block's pixels; returns partial r^T z.  With a coarse space, G = 2 or 4
+// consecutive lanes share a pixel when the block has that many threads per pixel: lane
+// g of the group sums the coarse columns j = g, g + G, ... and the group combines its
+// partial sums by a fixed xor-shuffle tree (G fixed by the plan's sizes, so results are
+// reproducible); the group's first lane finishes the pixel.
 template <typename T, int NC, int CM>
 __device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int p0, int p1) {
     __shared__ T vt[KMAX];
-    if constexpr (CM != 0) {
-        if (threadIdx.x < a.k) vt[threadIdx.x] = (T)v_sh[threadIdx.x];
-        __syncthreads();
-    }
     DotAcc<T> rz;
-    for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-        const int64_t e = (int64_t)q * NC;
-        T t[NC], zc[NC], t0[NC];
+    if constexpr (CM == 0) {
+        for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+            const int64_t e = (int64_t)q * NC;
+            T t[NC], out[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            t[c] = a.r[e + c];
-            t0[c] = t[c];
-            zc[c] = (T)0;
-        }
-        if constexpr (CM == 2) {
-#pragma unroll 8
-            for (int j = 0; j < a.k; ++j) {
-                const T vj = vt[j];
-                const T* zz = a.Z + (size_t)j * a.n + e;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) zc[c] += __ldg(zz + c) * vj;
+            for (int c = 0; c < NC; ++c) t[c] = a.r[e + c];
+            if constexpr (NC == 1) {
+                out[0] = a.bd[q] * t[0];
+            } else {
+                const T* m = a.bd + 6 * (int64_t)q;
+                out[0] = m[0] * t[0] + m[1] * t[1] + m[2] * t[2];
+                out[1] = m[1] * t[0] + m[3] * t[1] + m[4] * t[2];
+                out[2] = m[2] * t[0] + m[4] * t[1] + m[5] * t[2];
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const T out = a.z[e + c] + zc[c];
-                a.z[e + c] = out;
-                rz.add(t0[c], out);
+                a.z[e + c] = out[c];
+                rz.add(t[c], out[c]);
             }
-            continue;
         }
-        if constexpr (CM == 1) {
-#pragma unroll 8
-            for (int j = 0; j < a.k; ++j) {
-                const T vj = vt[j];
-                const T* az = a.AZ + (size_t)j * a.n + e;
-                const T* zz = a.Z + (size_t)j * a.n + e;
+        return rz;
+    } else {
+        if (threadIdx.x < a.k) vt[threadIdx.x] = (T)v_sh[threadIdx.x];
+        __syncthreads();
+        const int np = p1 - p0;
+        const int nt = (int)blockDim.x;
+        const int G = np * 4 <= nt ? 4 : (np * 2 <= nt ? 2 : 1);   // the same in every lane
+        const int lg = threadIdx.x % G;
+        const int per = nt / G;   // pixels per round
+        for (int base = 0; base < np; base += per) {
+            const int qi = base + (int)threadIdx.x / G;
+            const bool valid = qi < np;
+            const int q = p0 + (valid ? qi : 0);
+            const int64_t e = (int64_t)q * NC;
+            T t[NC], zc[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                t[c] = (T)0;
+                zc[c] = (T)0;
+            }
+            if (valid) {
+                if constexpr (CM == 2) {
+#pragma unroll 4
+                    for (int j = lg; j < a.k; j += G) {
+                        const T vj = vt[j];
+                        const T* zz = a.Z + (size_t)j * a.n + e;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) zc[c] += __ldg(zz + c) * vj;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = lg; j < a.k; j += G) {
+                        const T vj = vt[j];
+                        const T* az = a.AZ + (size_t)j * a.n + e;
+                        const T* zz = a.Z + (size_t)j * a.n + e;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            t[c] -= __ldg(az + c) * vj;
+                            zc[c] += __ldg(zz + c) * vj;
+                        }
+                    }
+                }
+            }
+            for (int o = 1; o < G; o <<= 1) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    t[c] -= __ldg(az + c) * vj;
-                    zc[c] += __ldg(zz + c) * vj;
+                    t[c] += __shfl_xor_sync(0xffffffffu, t[c], o);
+                    zc[c] += __shfl_xor_sync(0xffffffffu, zc[c], o);
+                }
+            }
+            if (!valid || lg != 0) continue;
+            T r0[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) r0[c] = a.r[e + c];
+            if constexpr (CM == 2) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const T out = a.z[e + c] + zc[c];
+                    a.z[e + c] = out;
+                    rz.add(r0[c], out);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) t[c] += r0[c];
+                T out[NC];
+                if constexpr (NC == 1) {
+                    out[0] = a.bd[q] * t[0] + zc[0];
+                } else {
+                    const T* m = a.bd + 6 * (int64_t)q;
+                    out[0] = m[0] * t[0] + m[1] * t[1] + m[2] * t[2] + zc[0];
+                    out[1] = m[1] * t[0] + m[3] * t[1] + m[4] * t[2] + zc[1];
+                    out[2] = m[2] * t[0] + m[4] * t[1] + m[5] * t[2] + zc[2];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    a.z[e + c] = out[c];
+                    rz.add(r0[c], out[c]);
                 }
             }
         }
-        T out[NC];
-        if constexpr (NC == 1) {
-            out[0] = a.bd[q] * t[0] + zc[0];
-        } else {
-            const T* m = a.bd + 6 * (int64_t)q;
-            out[0] = m[0] * t[0] + m[1] * t[1] + m[2] * t[2] + zc[0];
-            out[1] = m[1] * t[0] + m[3] * t[1] + m[4] * t[2] + zc[1];
-            out[2] = m[2] * t[0] + m[4] * t[1] + m[5] * t[2] + zc[2];
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            a.z[e + c] = out[c];
-            rz.add(t0[c], out[c]);
-        }
+        return rz;
     }
-    return rz;
 }
 
 // y = M_BD r into a.z on this block's pixels (the first step of the A-DEF2 form).

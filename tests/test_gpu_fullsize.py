@@ -92,6 +92,19 @@ def test_polarised_2e24_matches_oracle_iterations_and_map():
         assert errs[f"{name}_vs_m*"] <= bound, (name, errs, bound)
     for nm in ("fp64_bd", "fp64_2lvl"):
         assert g[f"err_{nm.split('_')[1]}_vs_star"] <= bound      # the oracle's own maps obey it too
+    if "iters_2lvl_z1e-10" in g:
+        # the bench's coarse space: Ritz vectors from the first solve run to 1e-10 in FP64
+        kk, ritz = plan.build_coarse(g["k"], mm.MM_FP64, bprime=plan.rhs(d0), tol=1e-10, maxit=5000)
+        np.testing.assert_allclose(ritz[:3], g["ritz_z1e-10"][:3], rtol=1e-4)
+        m4, st4, status4 = plan.solve(d1, tol=1e-6, maxit=5000, kind=mm.MM_PREC_TWOLEVEL)
+        assert status4 == mm.MM_OK and abs(st4["iters"] - g["iters_2lvl_z1e-10"]) <= 2
+        errs["fp64_2lvl_z1e-10_vs_oracle"] = _rel(m4.cpu().numpy(), mstar + maps["d_2lvl_z1e10"].astype(np.float64))
+        errs["fp64_2lvl_z1e-10_vs_m*"] = _rel(m4.cpu().numpy(), mstar)
+        assert errs["fp64_2lvl_z1e-10_vs_m*"] <= bound
+        mx, stx, sx = plan.solve(d1, tol=1e-6, maxit=5000, kind=mm.MM_PREC_TWOLEVEL, solver=mm.MM_SOLVE_MIXED)
+        assert sx == mm.MM_OK and stx["rel_resid"] <= 1e-6
+        errs["mixed_2lvl_z1e-10_vs_m*"] = _rel(mx.cpu().numpy(), mstar)
+        assert errs["mixed_2lvl_z1e-10_vs_m*"] <= bound
     print(f"\nmap errors (bound {bound:.2e}): {errs}")
     plan.close()
 
