@@ -513,7 +513,10 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const TileRhs tr = tile_rhs(blockIdx.x, A.R);
     const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
-    for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
+    // FP32: the split twiddles are computed (sincospif), which leaves the table's 32 KB of
+    // shared memory to the L1 cache that serves the de-pointing gathers
+    if constexpr (sizeof(T) != 4)
+        for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
     __syncthreads();
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
@@ -522,7 +525,14 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     for (int k = tid; k <= N / 2; k += NT) {
         const int k2 = (N - k) & (N - 1);
         T cw, sw;                         // W = cw - i sw = exp(-2 pi i k / B)
-        twiddle<T, LOGN - 1>(tab, k, cw, sw);
+        if constexpr (sizeof(T) == 4) {
+            float sv, cv;
+            sincospif((float)k * (1.f / (float)N), &sv, &cv);   // 2 pi k / B = pi k / N
+            cw = cv;
+            sw = sv;
+        } else {
+            twiddle<T, LOGN - 1>(tab, k, cw, sw);
+        }
         C2 V1, V2;
         split_product<T>(a[pad<T>(k)], a[pad<T>(k2)], cw, sw, H[k], H[N - k], V1, V2);
         a[pad<T>(k)] = V1;
@@ -722,7 +732,9 @@ void launch_mode_cl(const TzArgs<T>& A, int ntiles, int mode, cudaStream_t s) {
 template <typename T>
 size_t toeplitz_smem_bytes_impl(int logn) {
     const size_t N = size_t(1) << logn;
-    return sizeof(typename Cx<T>::type) * (N + (N >> PadLog<T>::v)) + sizeof(T) * (N / 2 + 1);
+    // the FP32 kernel computes its split twiddles and holds no cosine table
+    const size_t table = sizeof(T) == 4 ? 0 : sizeof(T) * (N / 2 + 1);
+    return sizeof(typename Cx<T>::type) * (N + (N >> PadLog<T>::v)) + table;
 }
 
 template <typename T, int LOGN, int MODE>
