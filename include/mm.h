@@ -74,6 +74,8 @@ typedef struct {
     double fsamp;           /* sampling frequency in Hz (> 0)                             */
     double rcond_min;       /* I/Q/U pixel acceptance (<= 0: 1e-6), see mm_plan           */
     void* stream;           /* cudaStream_t; NULL = legacy default stream                 */
+    int32_t scatter_lanes;  /* 0: automatic (32, or timed when autotuning); else 32, 16 or 8
+                               lanes per observed pixel in the scatter (mm_scatter_config)  */
 } mm_opts;
 
 typedef struct {
@@ -136,6 +138,15 @@ mm_status mm_plan_info(mm_plan_t plan, int32_t* npix_obs, int64_t* n, int64_t* n
  * is kept.  Either pointer (host float[16]) may be NULL.
  */
 mm_status mm_autotune_read(mm_plan_t plan, float* ms_f64, float* ms_f32);
+
+/*
+ * Pixel tile of the scatter P^T z: the number of lanes that share an observed pixel's
+ * sorted samples (32, 16 or 8: one, two or four pixels per warp).  32 unless the plan
+ * autotunes (opts.autotune), which times the FP32 scatter with each and keeps the
+ * fastest.  lanes_per_pixel (host), ms (host float[3]: the timed launches for 32, 16 and
+ * 8 lanes, or 0 when not timed); either may be NULL.  The paper has no counterpart.
+ */
+mm_status mm_scatter_config(mm_plan_t plan, int32_t* lanes_per_pixel, float* ms);
 
 /*
  * Form of the batched operator (mm_apply_A_batch, mm_solve_batch), fixed once per plan by

@@ -178,6 +178,7 @@ struct PlanHolder : Plan {
     bool autotune = false;      // measured block / batched-kernel choice (mm_opts.autotune)
     float tuned_ms64[16] = {};  // timed candidates by logn - 8 (0: not tried)
     float tuned_ms32[16] = {};
+    float tuned_scatter_ms[3] = {};   // FP32 scatter timed with 32, 16, 8 lanes per pixel
     // Residual history of the last solve: PCG run j wrote r^T r of its steps to
     // pcg.hist_rr[off ..]; relative residual = sqrt(rr / bb) * scale (mm_solve_history).
     // A run with bb = 0 took no step: its entry 0 is `scale` itself (the relative
@@ -678,7 +679,7 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     g.n = P.n;
     g.nblocks = std::max(1, std::min(pcg_max_blocks(P.num_sms), (P.npix_obs + 31) / 32));
     g.partial = dalloc<double>((size_t)g.nblocks * PSTRIDE);
-    g.sc_part = dalloc<double>((size_t)scatter_blocks(P));
+    g.sc_part = dalloc<double>((size_t)scatter_blocks(P));   // 32 lanes per pixel: the most blocks
     g.sc_count = dalloc<unsigned>(1);
     check_cuda(cudaMemsetAsync(g.sc_count, 0, 4, s), "memset");
     g.scal = dalloc<double>(16);
@@ -693,12 +694,31 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     check_cuda(cudaEventCreate(&P.ev1), "event");
     check_cuda(cudaEventCreate(&P.ev2), "event");
     P.autotune = o->autotune != 0;
+    if (o->scatter_lanes != 0) {
+        if (o->scatter_lanes != 32 && o->scatter_lanes != 16 && o->scatter_lanes != 8)
+            throw Error{MM_ERR_ARG, "scatter_lanes must be 0, 32, 16 or 8"};
+        P.scatter_lpp = o->scatter_lanes;
+    }
     if (P.autotune) {
         // zero maps for the timed launches (x64 / the first half of r64 as FP32)
         check_cuda(cudaMemsetAsync(P.x64, 0, (size_t)P.n * 8, s), "memset");
         if (P.tz64.logn != 0 && o->fft_log2_f64 <= 0) autotune_toeplitz<double>(P, P.tz64, P.tod64, P.x64, P.tuned_ms64);
         if (P.tz32.logn != 0 && o->fft_log2_f32 <= 0)
             autotune_toeplitz<float>(P, P.tz32, P.tod32, reinterpret_cast<const float*>(P.x64), P.tuned_ms32);
+        // the pixel tile of the scatter: lanes per observed pixel, timed on the FP32
+        // scatter of a zero time-domain array (its cost does not depend on the values)
+        if (P.npix_obs > 0 && o->scatter_lanes == 0) {
+            check_cuda(cudaMemsetAsync(P.tod32, 0, (size_t)P.nt * 4, s), "memset");
+            const int lpp[3] = {32, 16, 8};
+            int best = 0;
+            for (int i = 0; i < 3; ++i) {
+                P.scatter_lpp = lpp[i];
+                P.tuned_scatter_ms[i] = time_launches(
+                    P, [&] { launch_scatter<float>(P, P.tod32, reinterpret_cast<float*>(P.r64), nullptr, s); }, 5);
+                if (P.tuned_scatter_ms[i] < P.tuned_scatter_ms[best]) best = i;
+            }
+            P.scatter_lpp = lpp[best];
+        }
     }
     build_toeplitz_df(P);
     sync(s);
@@ -2420,6 +2440,14 @@ mm_status mm_autotune_read(mm_plan_t plan, float* ms_f64, float* ms_f32) {
         PlanHolder* P = get(plan);
         if (ms_f64) std::memcpy(ms_f64, P->tuned_ms64, sizeof(P->tuned_ms64));
         if (ms_f32) std::memcpy(ms_f32, P->tuned_ms32, sizeof(P->tuned_ms32));
+    });
+}
+
+mm_status mm_scatter_config(mm_plan_t plan, int32_t* lanes_per_pixel, float* ms) {
+    return guarded(plan, [&] {
+        PlanHolder* P = get(plan);
+        if (lanes_per_pixel) *lanes_per_pixel = P->scatter_lpp;
+        if (ms) std::memcpy(ms, P->tuned_scatter_ms, sizeof(P->tuned_scatter_ms));
     });
 }
 

@@ -112,6 +112,7 @@ struct Plan {
     cudaStream_t stream = 0;
     int device = 0;                // device current when the plan was made
     int num_sms = 0;
+    int scatter_lpp = 32;          // scatter lanes per pixel (32, 16 or 8; the pixel tile)
     int64_t L_grid = 0;
 
     // observed pixels

@@ -75,14 +75,16 @@ template void launch_gather<double>(const Plan&, const double*, double*, cudaStr
 template void launch_gather<float>(const Plan&, const float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------- scatter
-// One warp per observed pixel.  Lanes stride over the pixel's sorted samples and keep
-// per-lane partial sums in T.  The warp tree (xor shuffles, fixed order) runs in double
-// for T = double and on exact FP32 (hi, lo) pairs for T = float -- GB300 issues a warp's
-// FP64 instruction at 1/64 of the FP32 rate, and a double tree per pixel would cost more
-// SM time than the pixel's memory traffic.  The sample loop issues SCATTER_U (index,
-// weight) loads per lane before their dependent TOD loads, so each warp keeps several
-// random TOD reads in flight; every lane still adds its samples j, j + 32, j + 64, ... in
-// ascending order (the result does not depend on the unrolling).
+// LPP lanes per observed pixel (the pixel tile: 32, 16 or 8, so a warp holds 1, 2 or 4
+// pixels; plan.scatter_lpp, chosen by timing in an autotuned plan).  The lanes of a pixel
+// stride over its sorted samples and keep per-lane partial sums in T.  The tree over the
+// LPP lanes (xor shuffles, fixed order) runs in double for T = double and on exact FP32
+// (hi, lo) pairs for T = float -- GB300 issues a warp's FP64 instruction at 1/64 of the
+// FP32 rate, and a double tree per pixel would cost more SM time than the pixel's memory
+// traffic.  The sample loop issues SCATTER_U (index, weight) loads per lane before their
+// dependent TOD loads, so each lane keeps several random TOD reads in flight; every lane
+// still adds its samples j, j + LPP, j + 2 LPP, ... in ascending order (the result does
+// not depend on the unrolling, only on LPP).
 constexpr int SCATTER_U = 4;
 constexpr int SCATTER_THREADS = 256;
 
@@ -94,44 +96,55 @@ struct ScatterDot {
     double* pq;
 };
 
-template <typename T>
-__device__ __forceinline__ T warp_total(T v) {
+// Sum over the LPP lanes of a pixel group (every lane gets it); call with all 32 lanes.
+template <typename T, int LPP>
+__device__ __forceinline__ T group_total(T v) {
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o = LPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     } else {
         float hi = v, lo = 0.f;
-        warp_pair_reduce(hi, lo);
+#pragma unroll
+        for (int o = LPP / 2; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            pair_add(hi, lo, h2, l2);
+        }
         return hi + lo;
     }
 }
 
-template <typename T, int NC, bool DOT>
+template <typename T, int NC, bool DOT, int LPP>
 __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t* __restrict__ off,
                                                                   const int32_t* __restrict__ tsort,
                                                                   const typename V2<T>::type* __restrict__ ws,
                                                                   const T* __restrict__ z, T* __restrict__ w,
                                                                   int npix, const int* done, ScatterDot sd) {
     using W2 = typename V2<T>::type;
+    constexpr int PPW = 32 / LPP;                 // pixels per warp
     if (done != nullptr && *(volatile const int*)done) return;
     const int lane = threadIdx.x & 31;
+    const int sl = lane % LPP, seg = lane / LPP;
     const int warps = blockDim.x >> 5;
-    DotAcc<T> dacc;   // DOT: this warp's pixels, ascending (lane 0)
-    for (int q = blockIdx.x * warps + (threadIdx.x >> 5); q < npix; q += gridDim.x * warps) {
-        const int b = off[q];
-        const int e = off[q + 1];
+    DotAcc<T> dacc;   // DOT: this lane group's pixels, ascending (lane sl == 0)
+    const int stride = gridDim.x * warps * PPW;
+    for (int qb = (blockIdx.x * warps + (threadIdx.x >> 5)) * PPW; qb < npix; qb += stride) {
+        const int q = qb + seg;
+        const bool valid = q < npix;
+        const int b = valid ? off[q] : 0;
+        const int e = valid ? off[q + 1] : 0;
         T a0 = 0, a1 = 0, a2 = 0;
-        int j = b + lane;
-        for (; j + 32 * (SCATTER_U - 1) < e; j += 32 * SCATTER_U) {
+        int j = b + sl;
+        for (; j + LPP * (SCATTER_U - 1) < e; j += LPP * SCATTER_U) {
             int t[SCATTER_U];
             W2 ww[SCATTER_U];
             T v[SCATTER_U];
 #pragma unroll
-            for (int u = 0; u < SCATTER_U; ++u) t[u] = __ldg(tsort + j + 32 * u);
+            for (int u = 0; u < SCATTER_U; ++u) t[u] = __ldg(tsort + j + LPP * u);
             if constexpr (NC == 3) {
 #pragma unroll
-                for (int u = 0; u < SCATTER_U; ++u) ww[u] = __ldg(ws + j + 32 * u);
+                for (int u = 0; u < SCATTER_U; ++u) ww[u] = __ldg(ws + j + LPP * u);
             }
 #pragma unroll
             for (int u = 0; u < SCATTER_U; ++u) v[u] = z[t[u]];
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
                 }
             }
         }
-        for (; j < e; j += 32) {
+        for (; j < e; j += LPP) {
             const T v = z[__ldg(tsort + j)];
             a0 += v;
             if constexpr (NC == 3) {
@@ -153,13 +166,13 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
                 a2 += ww.y * v;
             }
         }
-        const T s0 = warp_total<T>(a0);
+        const T s0 = group_total<T, LPP>(a0);
         T s1 = 0, s2 = 0;
         if constexpr (NC == 3) {
-            s1 = warp_total<T>(a1);
-            s2 = warp_total<T>(a2);
+            s1 = group_total<T, LPP>(a1);
+            s2 = group_total<T, LPP>(a2);
         }
-        if (lane == 0) {
+        if (sl == 0 && valid) {
             if constexpr (NC == 1) {
                 w[q] = s0;
                 if constexpr (DOT) dacc.add(static_cast<const T*>(sd.p)[q], s0);
@@ -177,14 +190,14 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
         }
     }
     if constexpr (DOT) {
-        __shared__ DotAcc<T> wacc[SCATTER_THREADS / 32];
+        __shared__ DotAcc<T> wacc[SCATTER_THREADS];
         __shared__ double wsum[SCATTER_THREADS / 32];
         __shared__ bool last;
-        if (lane == 0) wacc[threadIdx.x >> 5] = dacc;
+        if (sl == 0) wacc[(threadIdx.x >> 5) * PPW + seg] = dacc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double b = 0.0;
-            for (int i = 0; i < warps; ++i) b += wacc[i].total();
+            for (int i = 0; i < warps * PPW; ++i) b += wacc[i].total();
             sd.part[blockIdx.x] = b;
             __threadfence();
             last = atomicAdd(sd.count, 1u) == gridDim.x - 1;
@@ -212,22 +225,32 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
     }
 }
 
-// Grid: one warp per pixel up to 8 resident blocks of 256 threads per SM (full
-// occupancy), warps loop over pixels beyond that.
+// Grid: LPP lanes per pixel up to 8 resident blocks of 256 threads per SM (full
+// occupancy), lane groups loop over pixels beyond that.
 int scatter_blocks(const Plan& P) {
-    const int wpb = SCATTER_THREADS / 32;
-    int g = (int)(((int64_t)P.npix_obs + wpb - 1) / wpb);
+    const int ppb = (SCATTER_THREADS / 32) * (32 / P.scatter_lpp);
+    int g = (int)(((int64_t)P.npix_obs + ppb - 1) / ppb);
     return std::max(1, std::min(g, P.num_sms * 8));
+}
+
+template <typename T, bool DOT, int LPP>
+static void scatter_launch_lpp(const Plan& P, const T* z, T* w, const int* done, ScatterDot sd, cudaStream_t s) {
+    const int g = scatter_blocks(P);
+    if (P.ncomp == 1)
+        scatter_kernel<T, 1, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs,
+                                                                     done, sd);
+    else
+        scatter_kernel<T, 3, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z,
+                                                                     w, P.npix_obs, done, sd);
 }
 
 template <typename T, bool DOT>
 static void scatter_launch(const Plan& P, const T* z, T* w, const int* done, ScatterDot sd, cudaStream_t s) {
-    const int g = scatter_blocks(P);
-    if (P.ncomp == 1)
-        scatter_kernel<T, 1, DOT><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs, done, sd);
-    else
-        scatter_kernel<T, 3, DOT><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z, w,
-                                                                P.npix_obs, done, sd);
+    switch (P.scatter_lpp) {
+        case 8: scatter_launch_lpp<T, DOT, 8>(P, z, w, done, sd, s); break;
+        case 16: scatter_launch_lpp<T, DOT, 16>(P, z, w, done, sd, s); break;
+        default: scatter_launch_lpp<T, DOT, 32>(P, z, w, done, sd, s); break;
+    }
     check_cuda(cudaGetLastError(), "scatter launch");
     note_launch();
 }

@@ -34,7 +34,7 @@ EXPORTS = ["mm_plan", "mm_plan_info", "mm_plan_pixels", "mm_plan_row", "mm_gathe
            "mm_version", "mm_launch_count", "mm_apply_A_static", "mm_solve_ex", "mm_grad", "mm_apply_A_batch",
            "mm_solve_batch", "mm_autotune_read", "mm_batch_config", "mm_build_coarse_apriori",
            "mm_build_coarse_eps", "mm_coarse_import", "mm_build_coarse_arnoldi", "mm_solve_history",
-           "mm_pcg_barrier_check", "mm_residual"]
+           "mm_pcg_barrier_check", "mm_residual", "mm_scatter_config"]
 
 
 class mm_psd(ctypes.Structure):
@@ -45,7 +45,7 @@ class mm_opts(ctypes.Structure):
     _fields_ = [("ncomp", ctypes.c_int32), ("lambda_", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("fft_log2_f64", ctypes.c_int32), ("fft_log2_f32", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("fsamp", ctypes.c_double), ("rcond_min", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("scatter_lanes", ctypes.c_int32)]
 
 
 class mm_stats(ctypes.Structure):
@@ -107,6 +107,7 @@ _SIGS = {
     "mm_solve_history": (I32, [P, I32, P, P]),
     "mm_pcg_barrier_check": (I32, [P, I32, ctypes.c_double]),
     "mm_residual": (I32, [P, ctypes.c_int, P, P, P]),
+    "mm_scatter_config": (I32, [P, P, P]),
     "mm_last_error": (ctypes.c_char_p, [P]),
     "mm_destroy": (None, [P]),
     "mm_version": (ctypes.c_char_p, []),
@@ -319,6 +320,14 @@ def mm_solve_history(plan):
     return h[: cnt.value]
 
 
+def mm_scatter_config(plan):
+    """(lanes per pixel of the scatter, [ms at 32, 16, 8 lanes] or zeros)."""
+    lpp = ctypes.c_int32()
+    ms = (ctypes.c_float * 3)()
+    _check(lib().mm_scatter_config(plan, ctypes.byref(lpp), ms), plan)
+    return lpp.value, list(ms)
+
+
 def mm_residual(plan, arith, d, x, r):
     _check(lib().mm_residual(plan, int(arith), _ptr(d), _ptr(x), _ptr(r)), plan)
 
@@ -370,7 +379,8 @@ class Plan:
     """One map-making problem on the current CUDA device (torch tensors in and out)."""
 
     def __init__(self, pix, npix_sky, weights, offsets, interval_psd, psds, lam, fsamp=100.0, ncomp=None,
-                 window=MM_WINDOW_GAUSS, rcond_min=1e-6, fft_log2=(0, 0), stream=None, autotune=False):
+                 window=MM_WINDOW_GAUSS, rcond_min=1e-6, fft_log2=(0, 0), stream=None, autotune=False,
+                 scatter_lanes=0):
         torch = _torch()
         self._torch = torch
         pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32))
@@ -386,7 +396,7 @@ class Plan:
         self.stream = stream
         o = mm_opts(ncomp=ncomp, lambda_=int(lam), window=window, fft_log2_f64=int(fft_log2[0]),
                     fft_log2_f32=int(fft_log2[1]), autotune=int(bool(autotune)), fsamp=float(fsamp), rcond_min=float(rcond_min),
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, scatter_lanes=int(scatter_lanes))
         self.handle = mm_plan(pix, pix.size, npix_sky, w, off, off.size - 1, ipsd, arr, len(ps), o)
         info = mm_plan_info(self.handle)
         self.npix_obs = info["npix_obs"]
@@ -589,6 +599,10 @@ class Plan:
         self._sync_in()
         mm_residual(self.handle, arith, d, x, r)
         return r
+
+    def scatter_config(self):
+        """(lanes per pixel of the scatter, timings at 32 / 16 / 8 lanes when autotuned)."""
+        return mm_scatter_config(self.handle)
 
     def barrier_check(self, absent_blocks, wait_s):
         """Status (int) of the bounded-wait diagnostic mm_pcg_barrier_check."""

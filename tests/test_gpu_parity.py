@@ -196,6 +196,42 @@ def test_residual_from_data(case, arith):
     assert np.linalg.norm(r0 - b) <= 1e-12 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("lanes", [32, 16, 8])
+def test_scatter_pixel_tiles(lanes):
+    # the scatter with 32, 16 or 8 lanes per observed pixel (one, two or four pixels per
+    # warp) against the oracle's P^T, FP64 and FP32, and inside A x; the fused p^T q of the
+    # PCG scatter through a solve
+    scan = SCANS["P_ragged"]()
+    pr = oracle_problem(scan)
+    plan = _plan(scan, scatter_lanes=lanes)
+    assert plan.scatter_config()[0] == lanes
+    rng = np.random.default_rng(lanes)
+    z = rng.standard_normal(pr.nt)
+    ref = pr.PT(z)
+    assert _rel(plan.scatter(_cuda(z)).cpu().numpy(), ref) <= 1e-12
+    assert _rel(plan.scatter(_cuda(z, torch.float32), mm.MM_FP32).double().cpu().numpy(), ref) <= 2e-5
+    x = rng.standard_normal(pr.n)
+    assert _rel(plan.apply_A(_cuda(x)).cpu().numpy(), pr.A(x)) <= 1e-12
+    d = _data(scan)
+    m, st, status = plan.solve(_cuda(d), tol=1e-8, maxit=3000)
+    ref_m = pcg(pr.A, oprec.BlockJacobi(pr).apply, pr.rhs(d), 1e-8, 3000)
+    assert status == mm.MM_OK and abs(st["iters"] - ref_m.iters) <= 2
+    assert _rel(m.cpu().numpy(), ref_m.x) <= 1e-6
+    plan.close()
+
+
+def test_scatter_pixel_tile_autotuned():
+    scan = SCANS["c2_small"]()
+    plan = _plan(scan, autotune=True)
+    lanes, ms = plan.scatter_config()
+    assert lanes in (32, 16, 8) and min(ms) > 0
+    assert lanes == (32, 16, 8)[int(np.argmin(ms))]
+    with pytest.raises(mm.MMError) as e:
+        _plan(scan, scatter_lanes=12)
+    assert e.value.status == mm.MM_ERR_ARG
+    plan.close()
+
+
 def test_residual_history(case):
     """||r_j|| / ||b|| per step (the Sec. 5.1 convergence measure) against the oracle's
     PCG on the same system: equal start, the stopping rule on the last two entries, and
