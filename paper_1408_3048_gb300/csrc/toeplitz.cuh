@@ -21,6 +21,7 @@
 // The tile load can evaluate y = P x on the fly from the map (fused de-pointing).
 #pragma once
 
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "dfloat.cuh"
@@ -64,6 +65,7 @@ struct TzArgs {
     int R;                 // right-hand sides (grid: tile-major, RHS fastest)
     int64_t in_stride;     // elements between RHS in y (mode 0) or x (gather modes)
     int64_t out_stride;    // elements between RHS in z
+    int pf_ahead = 0;      // CTAs resident at once: L2 prefetch distance (0: no prefetch)
 };
 
 // (tile, RHS) of a CTA (or cluster) index: RHS fastest, so the R CTAs of one tile read
@@ -452,6 +454,61 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
     }
 }
 
+// Bulk L2 prefetch of the bytes [p, p + nbytes), shrunk inwards to 16-byte boundaries
+// (the alignment cp.async.bulk.prefetch.L2 wants), in pieces of at most 32 KB.
+__device__ __forceinline__ void l2_prefetch(const void* p, int64_t nbytes) {
+    uint64_t a = (uint64_t)__cvta_generic_to_global(p);
+    const uint64_t e = (a + (uint64_t)nbytes) & ~(uint64_t)15;
+    a = (a + 15) & ~(uint64_t)15;
+    for (; a < e; a += 32768) {
+        const uint32_t n = (uint32_t)(e - a < 32768 ? e - a : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+    }
+}
+
+// L2 prefetch of the streamed inputs of CTA cid: the pointing and weights of its tile
+// (gather modes; once per tile, by its first right-hand side) or its time-domain input,
+// over the tile's segments, one lane per segment.  The de-pointing gathers of a tile then
+// wait on L2 instead of HBM: issued for the CTA that will run one wave later, the copy
+// overlaps this CTA's FFTs.  prefetch_seg reads the segment (lane g < TILE_SEGS) early,
+// prefetch_issue starts the copies once the descriptor load has long arrived.
+struct PfSeg {
+    int64_t t0;
+    int n;     // samples (0: nothing to prefetch)
+    int rhs;
+};
+
+template <typename T>
+__device__ __forceinline__ PfSeg prefetch_seg(const TzArgs<T>& A, int cid) {
+    PfSeg sg{0, 0, 0};
+    const int g = threadIdx.x;
+    if (g >= TILE_SEGS) return sg;
+    const TileRhs tr = tile_rhs(cid, A.R);
+    const Tile& tl = A.tiles[tr.tile];
+    const int pb = g == 0 ? tl.pb[0] : (g == 1 ? tl.pb[1] : tl.pb[2]);
+    const int pe = g == 0 ? tl.pe[0] : (g == 1 ? tl.pe[1] : tl.pe[2]);
+    if (pb < pe) {
+        sg.t0 = pb + seg_d(tl, g);
+        sg.n = pe - pb;
+        sg.rhs = tr.rhs;
+    }
+    return sg;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void prefetch_issue(const TzArgs<T>& A, const PfSeg& sg) {
+    if (sg.n == 0) return;
+    const int64_t roff = sg.rhs * A.in_stride, t0 = sg.t0, n = sg.n;
+    if constexpr (MODE == 0) l2_prefetch(A.y + roff + t0, n * (int64_t)sizeof(In<T>));
+    if constexpr (MODE == 2 || MODE >= 4) l2_prefetch(A.yd + roff + t0, n * 8);
+    if constexpr (MODE != 0 && MODE != 2) {
+        if (sg.rhs == 0) {
+            l2_prefetch(A.pixc + t0, n * 4);
+            if constexpr (MODE == 3 || MODE == 5) l2_prefetch(A.w + t0, n * (int64_t)sizeof(A.w[0]));
+        }
+    }
+}
+
 // Store output n (block position lambda + n) at its time, unless it falls between segments.
 template <typename T>
 __device__ __forceinline__ void store_out(const Tile& tile, In<T>* z, int lambda, int n, T v) {
@@ -515,10 +572,17 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const int tid = threadIdx.x;
     // FP32: the split twiddles are computed (sincospif), which leaves the table's 32 KB of
     // shared memory to the L1 cache that serves the de-pointing gathers
+    // the first wave prefetches its own inputs, every CTA those of the CTA one wave on
+    PfSeg next{0, 0, 0};
+    if (A.pf_ahead > 0) {
+        if ((int)blockIdx.x < A.pf_ahead) prefetch_issue<T, MODE>(A, prefetch_seg(A, blockIdx.x));
+        if ((int64_t)blockIdx.x + A.pf_ahead < (int64_t)gridDim.x) next = prefetch_seg(A, blockIdx.x + A.pf_ahead);
+    }
     if constexpr (sizeof(T) != 4)
         for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
     __syncthreads();
+    prefetch_issue<T, MODE>(A, next);
     fft_all<T, LOGN, NT, 0>(a, A.ptw);
     // real-FFT post-processing, spectrum product, pre-processing for the inverse.
     const T* H = A.H + (int64_t)tile.psd * (N + 1);
@@ -544,11 +608,20 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     In<T>* zo = A.z + tr.rhs * A.out_stride;
     if (tile.pb[0] <= A.lambda && A.lambda + tile.nout <= tile.pe[0]) {
         // every output inside the first segment: time = position + d[0]
+        // (four shared-memory reads in flight per thread before their stores)
         In<T>* z0 = zo + tile.d[0];
-        for (int n = tid; n < tile.nout; n += NT) {
-            const int i = n + A.lambda;
-            const C2 v = a[pad<T>(i >> 1)];
-            z0[i] = (In<T>)((i & 1) ? -v.y : v.x);
+        const int nout = tile.nout;
+#pragma unroll 1
+        for (int n0 = tid; n0 < nout; n0 += 4 * NT) {
+            C2 c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (n0 + u * NT < nout) c[u] = a[pad<T>((n0 + u * NT + A.lambda) >> 1)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = n0 + u * NT + A.lambda;
+                if (n0 + u * NT < nout) z0[i] = (In<T>)((i & 1) ? -c[u].y : c[u].x);
+            }
         }
     } else {
         for (int n = tid; n < tile.nout; n += NT) {
@@ -743,7 +816,18 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     const size_t smem = toeplitz_smem_bytes_impl<T>(LOGN);
     auto kern = toeplitz_os_kernel<T, LOGN, NT, MODE>;
     ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(toeplitz)");
-    kern<<<(unsigned)((int64_t)ntiles * A.R), NT, smem, s>>>(A);
+    TzArgs<T> B = A;
+    if (B.pf_ahead > 0) {
+        // resident CTAs = SMs (pf_ahead on entry) x CTAs per SM, measured once per kernel
+        static std::atomic<int> per_sm{0};
+        int occ = per_sm.load();
+        if (occ == 0) {
+            check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem), "toeplitz occupancy");
+            per_sm.store(occ = occ > 0 ? occ : 1);
+        }
+        B.pf_ahead *= occ;
+    }
+    kern<<<(unsigned)((int64_t)ntiles * A.R), NT, smem, s>>>(B);
     check_cuda(cudaGetLastError(), "toeplitz kernel launch");
     note_launch();
 }

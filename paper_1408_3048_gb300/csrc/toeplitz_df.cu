@@ -41,6 +41,7 @@ void launch_toeplitz_df(const Plan& P, const double* y, const double* d, const d
     A.R = R;
     A.in_stride = in_stride;
     A.out_stride = out_stride;
+    A.pf_ahead = P.num_sms;
     if (y != nullptr || d == nullptr || x == nullptr)
         throw Error{MM_ERR_ARG, "double-float Toeplitz: only the residual data d - P x is supported"};
     const int mode = P.ncomp == 1 ? 4 : 5;

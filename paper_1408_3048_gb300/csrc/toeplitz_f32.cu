@@ -32,6 +32,7 @@ void launch_toeplitz_any<float>(const Plan& P, const ToeplitzDev& tz, const floa
     A.R = R;
     A.in_stride = in_stride;
     A.out_stride = out_stride;
+    A.pf_ahead = P.num_sms;
     const int mode = y != nullptr ? 0 : (yd != nullptr ? (x == nullptr ? 2 : (P.ncomp == 1 ? 4 : 5)) : (P.ncomp == 1 ? 1 : 3));
     if (tz.cluster == 2 && tz.logn == 15) {
         launch_mode_cl<float, 14, 2>(A, tz.ntiles, mode, s);
