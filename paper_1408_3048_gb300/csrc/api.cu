@@ -211,7 +211,7 @@ static void destroy_plan(PlanHolder* P) {
     if (P == nullptr) return;
     for (void* p : {(void*)P->pixc, (void*)P->w64, (void*)P->w32, (void*)P->csr_off, (void*)P->tsort,
                     (void*)P->wsort64, (void*)P->wsort32, (void*)P->ioff, (void*)P->ipsd, (void*)P->t0,
-                    (void*)P->bd64, (void*)P->bd32, (void*)P->tod64, (void*)P->tod32, (void*)P->dbuf,
+                    (void*)P->bd64, (void*)P->bd32, (void*)P->tod64, (void*)P->tod32, (void*)P->map4, (void*)P->dbuf,
                     (void*)P->b64, (void*)P->d_dot, (void*)P->x64, (void*)P->r64, (void*)P->ax64,
                     (void*)P->grad_H, (void*)P->grad_u, (void*)P->grad_part})
         dfree(p);
@@ -668,6 +668,7 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
     // scratch
     P.tod64 = dalloc<double>((size_t)nt);
     P.tod32 = dalloc<float>((size_t)nt);
+    if (P.ncomp == 3) P.map4 = dalloc<float4>((size_t)std::max(P.npix_obs, 1));
     P.dbuf = dalloc<double>((size_t)nt);
     P.b64 = dalloc<double>((size_t)P.n);
     P.x64 = dalloc<double>((size_t)P.n);
@@ -740,7 +741,12 @@ template <typename T>
 static void apply_A(Plan& P, const T* x, T* y, const int* done) {
     const bool f64 = sizeof(T) == 8;
     int s0 = prof_begin(P, f64 ? ST_TZ64 : ST_TZ32);
-    launch_toeplitz<T>(P, tz_of<T>(P), nullptr, x, tod_of<T>(P), done, P.stream);
+    if constexpr (sizeof(T) == 4) {
+        if (P.map4 != nullptr) launch_toeplitz_f32_packed(P, x, true, tod_of<T>(P), done, P.stream);
+        else launch_toeplitz<T>(P, tz_of<T>(P), nullptr, x, tod_of<T>(P), done, P.stream);
+    } else {
+        launch_toeplitz<T>(P, tz_of<T>(P), nullptr, x, tod_of<T>(P), done, P.stream);
+    }
     prof_end(P, s0);
     s0 = prof_begin(P, f64 ? ST_SC64 : ST_SC32);
     launch_scatter<T>(P, tod_of<T>(P), y, done, P.stream);
@@ -767,6 +773,7 @@ static PcgArgs<T> pcg_args(PlanHolder& P, bool two, int maxit) {
     a.x = static_cast<T*>(g.x);
     a.r = static_cast<T*>(g.r);
     a.p = static_cast<T*>(g.p);
+    if constexpr (sizeof(T) == 4) a.p4 = P.map4;   // p also kept packed for the gather
     a.q = static_cast<T*>(g.q);
     a.z = static_cast<T*>(g.z);
     a.bd = bd_ptr<T>(P);
@@ -847,7 +854,11 @@ static PcgOutcome run_pcg(PlanHolder& P, int cm, double tol, int maxit, T* zstor
             // q = A p with p^T q fused into the scatter (scal[SC_PQ])
             const bool f64 = sizeof(T) == 8;
             int sl = prof_begin(P, f64 ? ST_TZ64 : ST_TZ32);
-            launch_toeplitz<T>(P, tz_of<T>(P), nullptr, a.p, tod_of<T>(P), P.pcg.flags + F_DONE, s);
+            if (sizeof(T) == 4 && a.p4 != nullptr)
+                launch_toeplitz_f32_packed(P, reinterpret_cast<const float*>(a.p), false,
+                                           reinterpret_cast<float*>(tod_of<T>(P)), P.pcg.flags + F_DONE, s);
+            else
+                launch_toeplitz<T>(P, tz_of<T>(P), nullptr, a.p, tod_of<T>(P), P.pcg.flags + F_DONE, s);
             prof_end(P, sl);
             sl = prof_begin(P, f64 ? ST_SC64 : ST_SC32);
             launch_scatter_dot<T>(P, tod_of<T>(P), static_cast<T*>(P.pcg.q), a.p, P.pcg.sc_part, P.pcg.sc_count,

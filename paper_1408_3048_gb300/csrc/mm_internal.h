@@ -146,6 +146,8 @@ struct Plan {
     // time-domain scratch
     double* tod64 = nullptr;       // [nt]
     float* tod32 = nullptr;        // [nt]
+    float4* map4 = nullptr;        // [npix_obs] FP32 I/Q/U map packed per pixel (ncomp 3): the
+                                   // layout the Toeplitz gather reads in one 16-byte load
     double* dbuf = nullptr;        // [nt] staging for host data
     double* b64 = nullptr;         // [n] last right-hand side
     bool have_b = false;
@@ -216,6 +218,10 @@ void launch_toeplitz_any(const Plan& P, const ToeplitzDev& tz, const T* y_tod, c
 // residual data d - P x; output z FP64 [nt] (R right-hand sides as for launch_toeplitz_rhs)
 void launch_toeplitz_df(const Plan& P, const double* y, const double* d, const double* x, int R, int64_t in_stride,
                         double* z, int64_t out_stride, cudaStream_t s);
+// FP32 I/Q/U N^-1 P x with the gather reading x from P.map4; pack: first write x into
+// P.map4 (one small kernel), else P.map4 already holds x (the FP32 PCG kernels keep it)
+void launch_toeplitz_f32_packed(const Plan& P, const float* x, bool pack, float* z, const int* done,
+                                cudaStream_t s);
 template <typename T>
 size_t toeplitz_smem_bytes(int logn);
 template <typename T>

@@ -292,6 +292,34 @@ __device__ DotAcc<T> apply_precond(const PcgArgs<T>& a, const double* v_sh, int 
 }
 
 // y = M_BD r into a.z on this block's pixels (the first step of the A-DEF2 form).
+// p = z (first step) or p = z + be p over the block's pixels [p0, p1); zs (optional)
+// records z.  FP32 I/Q/U plans also keep p packed per pixel (a.p4) for the Toeplitz gather.
+template <typename T, int NC>
+__device__ __forceinline__ void update_p(const PcgArgs<T>& a, int p0, int p1, bool first, T be, T* zs) {
+    if constexpr (NC == 3 && sizeof(T) == 4) {
+        if (a.p4 != nullptr) {
+            for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+                const int64_t i = 3 * (int64_t)q;
+                T v[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T zi = a.z[i + c];
+                    v[c] = first ? zi : zi + be * a.p[i + c];
+                    a.p[i + c] = v[c];
+                    if (zs != nullptr) zs[i + c] = zi;
+                }
+                a.p4[q] = make_float4(v[0], v[1], v[2], 0.f);
+            }
+            return;
+        }
+    }
+    for (int64_t i = (int64_t)p0 * NC + threadIdx.x; i < (int64_t)p1 * NC; i += blockDim.x) {
+        const T zi = a.z[i];
+        a.p[i] = first ? zi : zi + be * a.p[i];
+        if (zs != nullptr) zs[i] = zi;
+    }
+}
+
 template <typename T, int NC>
 __device__ void bd_into_z(const PcgArgs<T>& a, int p0, int p1) {
     for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
@@ -351,10 +379,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_init_kernel(PcgArgs<T> a) {
     }
     const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
     __syncthreads();
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-        a.p[i] = a.z[i];
-        if (a.zstore != nullptr) a.zstore[i] = a.z[i];
-    }
+    update_p<T, NC>(a, p0, p1, true, (T)0, a.zstore);
     const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
     if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
@@ -457,11 +482,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     const double beta = rzt / rho;
     const T be = (T)beta;
     T* zs = (a.zstore != nullptr && it < a.maxstore) ? a.zstore + (size_t)it * a.n : nullptr;
-    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-        const T zi = a.z[i];
-        a.p[i] = zi + be * a.p[i];
-        if (zs != nullptr) zs[i] = zi;
-    }
+    update_p<T, NC>(a, p0, p1, false, be, zs);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.flags[F_ITER] = it;
         a.scal[SC_RHO] = rzt;

@@ -26,6 +26,7 @@ struct PcgArgs {
     T* x;
     T* r;
     T* p;
+    float4* p4;          // FP32 I/Q/U: p packed per pixel for the Toeplitz gather, or nullptr
     const T* q;
     T* z;
     const T* bd;         // M_BD inverse blocks

@@ -66,6 +66,7 @@ struct TzArgs {
     int64_t in_stride;     // elements between RHS in y (mode 0) or x (gather modes)
     int64_t out_stride;    // elements between RHS in z
     int pf_ahead = 0;      // CTAs resident at once: L2 prefetch distance (0: no prefetch)
+    const float4* x4 = nullptr;   // FP32 I/Q/U map packed per pixel (mode 3), else nullptr
 };
 
 // (tile, RHS) of a CTA (or cluster) index: RHS fastest, so the R CTAs of one tile read
@@ -429,8 +430,21 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
                     if constexpr (!IQU) {
                         r = __ldg(x + q[u]);
                     } else {
-                        const I* xq = x + 3 * (int64_t)q[u];
-                        r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
+                        bool packed = false;
+                        if constexpr (sizeof(I) == 4 && MODE == 3) {
+                            // one 16-byte load per sample instead of three: a warp's gather
+                            // touches a cache line per pixel it visits (eight on a column
+                            // scan) once rather than three times
+                            if (A.x4 != nullptr) {
+                                const float4 m = __ldg(A.x4 + q[u]);
+                                r = m.x + w[u].x * m.y + w[u].y * m.z;
+                                packed = true;
+                            }
+                        }
+                        if (!packed) {
+                            const I* xq = x + 3 * (int64_t)q[u];
+                            r = __ldg(xq) + w[u].x * __ldg(xq + 1) + w[u].y * __ldg(xq + 2);
+                        }
                     }
                 }
                 if constexpr (MODE >= 4) v[u] = (T)(dv[u] - r);
