@@ -58,4 +58,38 @@ struct dfl2 {
     dfl x, y;
 };
 
+// Conversions between double and double-float by bit operations.  FP64 instructions,
+// conversions included, issue at 1/64 of the FP32 rate on this GPU, and the residual
+// kernel converts every sample on the way in and every output on the way out.
+// dfl_from_double: hi = d with its significand cut to 24 bits (exactly a float for the
+// exponents kept here), lo = the remaining 29 bits rounded to a float, then renormalised;
+// |d| below 2^-74 or above 2^127 and non-finite d take the FP64 route.  f64_from_f32 widens
+// a normal float or a zero exactly (subnormal and non-finite floats take the FP64 route),
+// so dfl_to_double equals (double)hi + (double)lo.
+__device__ __forceinline__ dfl dfl_from_double(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);   // biased exponent
+    if (e < 949 || e > 1150) return dfl(d);
+    const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(s | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned m = (unsigned)(b & 0x1fffffffu);   // lo = m 2^(e - 1075)
+    float lo = 0.f;
+    if (m != 0u) lo = __int_as_float(__float_as_int(__uint2float_rn(m)) + (e - 1075) * (1 << 23));
+    return df_renorm(hi, __uint_as_float(__float_as_uint(lo) | s));
+}
+
+__device__ __forceinline__ double f64_from_f32(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned E = (u >> 23) & 0xffu;
+    if (E == 0u || E == 255u) {
+        if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+        return (double)f;
+    }
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(E + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double dfl_to_double(dfl v) { return f64_from_f32(v.hi) + f64_from_f32(v.lo); }
+
 }  // namespace mm

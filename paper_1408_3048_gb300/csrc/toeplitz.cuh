@@ -22,6 +22,7 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "dfloat.cuh"
@@ -41,6 +42,18 @@ template <> struct InT<dfl> { using type = double; };
 template <typename T> using In = typename InT<T>::type;
 
 // Read-only load of a complex table entry.
+// Input-precision value -> arithmetic type and back (bit-level for double-float).
+template <typename T>
+__device__ __forceinline__ T from_in(In<T> v) {
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, double>::value) return dfl_from_double(v);
+    else return (T)v;
+}
+template <typename T>
+__device__ __forceinline__ In<T> to_in(T v) {
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, double>::value) return dfl_to_double(v);
+    else return (In<T>)v;
+}
+
 __device__ __forceinline__ float2 ldc(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldc(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ dfl2 ldc(const dfl2* p) {
@@ -407,7 +420,7 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
         if constexpr (MODE == 0 || MODE == 2) {
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-                if constexpr (MODE == 0) v[u] = okv[u] ? (T)y[tt[u]] : (T)0;
+                if constexpr (MODE == 0) v[u] = okv[u] ? from_in<T>(y[tt[u]]) : (T)0;
                 else v[u] = okv[u] ? (T)yd[tt[u]] : (T)0;
             }
         } else {
@@ -447,7 +460,7 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
                         }
                     }
                 }
-                if constexpr (MODE >= 4) v[u] = (T)(dv[u] - r);
+                if constexpr (MODE >= 4) v[u] = from_in<T>(dv[u] - r);
                 else v[u] = (T)r;
             }
         }
@@ -529,7 +542,7 @@ __device__ __forceinline__ void store_out(const Tile& tile, In<T>* z, int lambda
     bool in;
     const int p = n + lambda;
     const int g = tile_seg(tile, p, in);
-    if (in) z[p + seg_d(tile, g)] = (In<T>)v;
+    if (in) z[p + seg_d(tile, g)] = to_in<T>(v);
 }
 
 // Real-FFT split of the packed spectrum at the bin pair (k, N - k), product with the real
@@ -634,7 +647,7 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int i = n0 + u * NT + A.lambda;
-                if (n0 + u * NT < nout) z0[i] = (In<T>)((i & 1) ? -c[u].y : c[u].x);
+                if (n0 + u * NT < nout) z0[i] = to_in<T>((i & 1) ? -c[u].y : c[u].x);
             }
         }
     } else {
