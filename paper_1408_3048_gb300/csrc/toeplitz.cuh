@@ -495,9 +495,10 @@ __device__ __forceinline__ void l2_prefetch(const void* p, int64_t nbytes) {
 
 // L2 prefetch of the streamed inputs of CTA cid: the pointing and weights of its tile
 // (gather modes; once per tile, by its first right-hand side) or its time-domain input,
-// over the tile's segments, one lane per segment.  The de-pointing gathers of a tile then
-// wait on L2 instead of HBM: issued for the CTA that will run one wave later, the copy
-// overlaps this CTA's FFTs.  prefetch_seg reads the segment (lane g < TILE_SEGS) early,
+// over the tile's segments, one lane per segment.  Issued for the CTA that will run one
+// wave later, once this CTA's own gather is done, the copy overlaps this CTA's FFTs and
+// more of that CTA's gathers wait on L2 instead of HBM.  (Measured on the 2^24-sample
+// bench: two waves ahead, or issued at the start of the CTA, was slower.)  prefetch_seg reads the segment (lane g < TILE_SEGS) early,
 // prefetch_issue starts the copies once the descriptor load has long arrived.
 struct PfSeg {
     int64_t t0;
@@ -599,12 +600,11 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const int tid = threadIdx.x;
     // FP32: the split twiddles are computed (sincospif), which leaves the table's 32 KB of
     // shared memory to the L1 cache that serves the de-pointing gathers
-    // the first wave prefetches its own inputs, every CTA those of the CTA one wave on
+    // every CTA prefetches the inputs of the CTA one wave on (the first wave's own inputs
+    // are not: a prefetch racing the CTA's own loads measured slower than none)
     PfSeg next{0, 0, 0};
-    if (A.pf_ahead > 0) {
-        if ((int)blockIdx.x < A.pf_ahead) prefetch_issue<T, MODE>(A, prefetch_seg(A, blockIdx.x));
-        if ((int64_t)blockIdx.x + A.pf_ahead < (int64_t)gridDim.x) next = prefetch_seg(A, blockIdx.x + A.pf_ahead);
-    }
+    if (A.pf_ahead > 0 && (int64_t)blockIdx.x + A.pf_ahead < (int64_t)gridDim.x)
+        next = prefetch_seg(A, blockIdx.x + A.pf_ahead);
     if constexpr (sizeof(T) != 4)
         for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);
