@@ -12,13 +12,17 @@
 // equal the truncated band product exactly (no wrap-around reaches them when
 // nout <= B - 2 lambda).
 //
-// FFT: Stockham autosort, radix 8 passes (+ one radix 2/4 pass), data in shared memory
-// with one padding slot every 128 bytes so that strided stores of a pass are free of
-// bank conflicts, butterflies of a pass held in registers (in-place with barriers).
-// Twiddles from a quarter-wave cosine table cos(2 pi k / B), k = 0..B/4, in shared
-// memory (host-computed in FP64).
+// FFT: Stockham autosort, radix-16 passes (radix 8 for blocks below 2^10 reals) and one
+// shorter pass where the length asks for it, data in shared
+// memory with one padding slot after every 16 complex values so that the strided stores
+// of a pass are free of bank conflicts, butterflies of a pass held in registers (in
+// place, with barriers).  Twiddles: FP32 computes them in registers (sincospif and a few
+// products); FP64 and double-float read the per-pass tables and a quarter-wave cosine
+// table cos(2 pi k / B), k = 0..B/4 (host-computed in FP64), the latter staged in
+// shared memory.
 //
-// The tile load can evaluate y = P x on the fly from the map (fused de-pointing).
+// The tile load can evaluate y = P x on the fly from the map (fused de-pointing); the
+// FP32 I/Q/U form reads the map packed per pixel (one 16-byte load per sample).
 #pragma once
 
 #include <atomic>
@@ -598,13 +602,13 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
     const TileRhs tr = tile_rhs(blockIdx.x, A.R);
     const Tile tile = A.tiles[tr.tile];
     const int tid = threadIdx.x;
-    // FP32: the split twiddles are computed (sincospif), which leaves the table's 32 KB of
-    // shared memory to the L1 cache that serves the de-pointing gathers
     // every CTA prefetches the inputs of the CTA one wave on (the first wave's own inputs
     // are not: a prefetch racing the CTA's own loads measured slower than none)
     PfSeg next{0, 0, 0};
     if (A.pf_ahead > 0 && (int64_t)blockIdx.x + A.pf_ahead < (int64_t)gridDim.x)
         next = prefetch_seg(A, blockIdx.x + A.pf_ahead);
+    // FP32: the split twiddles are computed (sincospif), which leaves the table's 32 KB of
+    // shared memory to the L1 cache that serves the de-pointing gathers
     if constexpr (sizeof(T) != 4)
         for (int i = tid; i <= Q; i += NT) tab[i] = A.twiddle[i];
     load_block<T, NT, MODE>(A, tile, reinterpret_cast<T*>(a), 0, 2 * N, tr.rhs * A.in_stride);

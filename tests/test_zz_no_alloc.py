@@ -60,6 +60,22 @@ def test_static_matches_apply_A_twice(ncomp):
     plan.close()
 
 
+def test_static_fp32_matches_the_packed_gather_bit_for_bit():
+    # mm_apply_A in FP32 on I/Q/U reads x packed per pixel (one 16-byte load per sample);
+    # the static path gathers the three components one by one.  Same arithmetic, so the
+    # two A x must agree to the bit.
+    plan = _plan(_scan(3))
+    rng = np.random.default_rng(17)
+    x = torch.as_tensor(rng.standard_normal(plan.n), dtype=torch.float32).cuda()
+    ref = torch.empty(plan.n, dtype=torch.float32, device="cuda")
+    out = torch.empty(plan.n, dtype=torch.float32, device="cuda")
+    mm.mm_apply_A(plan.handle, mm.MM_FP32, x, ref)
+    mm.mm_apply_A_static(plan.handle, mm.MM_FP32, x, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    plan.close()
+
+
 def test_static_smaller_plan_after_larger_one():
     big = _plan(_scan(3, nper=60000, seed=8))
     small = _plan(_scan(3, nper=9000, seed=9))
