@@ -258,8 +258,14 @@ template <typename T>
 static double block_weight(int logn);
 template <>
 double block_weight<double>(int logn) { return logn >= 15 ? 2.0 : (logn == 14 ? 1.2 : (logn == 13 ? 1.12 : 1.0)); }
+// FP32 single-CTA blocks below 2^15 reals run several CTAs per SM (1024 threads in all),
+// which hides part of their gathers: measured on the 2^24-sample I/Q/U scan at lambda =
+// 512 .. 8192, their time per unit of the model falls with the block.
 template <>
-double block_weight<float>(int logn) { return fp32_cluster_weight(logn >= 16 ? 4 : (logn == 15 ? 2 : 1)); }
+double block_weight<float>(int logn) {
+    if (logn >= 15) return fp32_cluster_weight(logn >= 16 ? 4 : 2);
+    return logn == 14 ? 1.0 : (logn == 13 ? 0.87 : (logn == 12 ? 0.83 : (logn == 11 ? 0.72 : 0.67)));
+}
 
 // Overlap-save tiles of blocks of B real positions (B - 2 lambda valid outputs each) for
 // the single-right-hand-side kernels.  Consecutive stationary intervals with the same PSD

@@ -591,7 +591,7 @@ __device__ __forceinline__ void split_product(typename Cx<T>::type u1, typename 
 }
 
 template <typename T, int LOGN, int NT, int MODE>
-__global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
+__device__ __forceinline__ void toeplitz_os_tile(const TzArgs<T>& A) {
     using C2 = typename Cx<T>::type;
     constexpr int N = 1 << LOGN;
     constexpr int Q = N / 2;             // B/4
@@ -661,6 +661,24 @@ __global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
             store_out<T>(tile, zo, A.lambda, n, (i & 1) ? -v.y : v.x);
         }
     }
+}
+
+// Resident CTAs per SM: FP32 blocks below 2^15 reals run 1024 / NT CTAs of NT threads per
+// SM (at most 64 registers a thread), so that one CTA's gather overlaps another's FFT;
+// the 1024-thread FP32 block and FP64 / double-float keep one CTA per SM.
+template <typename T, int NT>
+__host__ __device__ constexpr int tz_min_blocks() {
+    return sizeof(T) == 4 && NT < 1024 ? 1024 / NT : 1;
+}
+
+template <typename T, int LOGN, int NT, int MODE>
+__global__ void __launch_bounds__(NT) toeplitz_os_kernel(TzArgs<T> A) {
+    toeplitz_os_tile<T, LOGN, NT, MODE>(A);
+}
+
+template <typename T, int LOGN, int NT, int MODE>
+__global__ void __launch_bounds__(NT, (tz_min_blocks<T, NT>())) toeplitz_os_kernel_mb(TzArgs<T> A) {
+    toeplitz_os_tile<T, LOGN, NT, MODE>(A);
 }
 
 // v * W_C^m for C in {2, 4} (m taken mod C): multiplications by +-1, +-i only.
@@ -845,7 +863,9 @@ template <typename T, int LOGN, int MODE>
 void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
     constexpr int NT = tz_threads<T, LOGN>();
     const size_t smem = toeplitz_smem_bytes_impl<T>(LOGN);
-    auto kern = toeplitz_os_kernel<T, LOGN, NT, MODE>;
+    void (*kern)(TzArgs<T>) = nullptr;
+    if constexpr (tz_min_blocks<T, NT>() > 1) kern = toeplitz_os_kernel_mb<T, LOGN, NT, MODE>;
+    else kern = toeplitz_os_kernel<T, LOGN, NT, MODE>;
     ensure_smem_attr((const void*)kern, (int)smem, "cudaFuncSetAttribute(toeplitz)");
     TzArgs<T> B = A;
     if (B.pf_ahead > 0) {
