@@ -665,10 +665,11 @@ __device__ __forceinline__ void toeplitz_os_tile(const TzArgs<T>& A) {
 
 // Resident CTAs per SM: FP32 blocks below 2^15 reals run 1024 / NT CTAs of NT threads per
 // SM (at most 64 registers a thread), so that one CTA's gather overlaps another's FFT;
-// the 1024-thread FP32 block and FP64 / double-float keep one CTA per SM.
+// the 1024-thread FP32 block and FP64 / double-float keep their own register use (one
+// CTA per SM), and so do 32-thread CTAs, which the 64-register cap would make spill.
 template <typename T, int NT>
 __host__ __device__ constexpr int tz_min_blocks() {
-    return sizeof(T) == 4 && NT < 1024 ? 1024 / NT : 1;
+    return sizeof(T) == 4 && NT < 1024 && NT >= 64 ? 1024 / NT : 1;
 }
 
 template <typename T, int LOGN, int NT, int MODE>
