@@ -210,7 +210,7 @@ static void free_coarse(CoarseDev& c) {
 static void destroy_plan(PlanHolder* P) {
     if (P == nullptr) return;
     for (void* p : {(void*)P->pixc, (void*)P->w64, (void*)P->w32, (void*)P->csr_off, (void*)P->tsort,
-                    (void*)P->wsort64, (void*)P->wsort32, (void*)P->ioff, (void*)P->ipsd, (void*)P->t0,
+                    (void*)P->wsort64, (void*)P->wsort32, (void*)P->asort32, (void*)P->ioff, (void*)P->ipsd, (void*)P->t0,
                     (void*)P->bd64, (void*)P->bd32, (void*)P->tod64, (void*)P->tod32, (void*)P->map4, (void*)P->dbuf,
                     (void*)P->b64, (void*)P->d_dot, (void*)P->x64, (void*)P->r64, (void*)P->ax64,
                     (void*)P->grad_H, (void*)P->grad_u, (void*)P->grad_part})
@@ -646,6 +646,23 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
         P.wsort32 = dalloc<float2>((size_t)P.nkept);
         launch_convert_f64_to_f32(reinterpret_cast<const double*>(P.wsort64), reinterpret_cast<float*>(P.wsort32),
                                   P.nkept * 2, s);
+        // unit-norm weights (cos 2 psi, sin 2 psi): the FP32 scatter forms them from the
+        // angle, (cos pi a, sin pi a) with a = atan2(w2, w1) / pi rounded to FP32, which
+        // halves its weight bytes (the weight is then within ~2e-7 of the FP64 pair)
+        bool unit = P.nkept > 0;
+        for (int64_t j = 0; j < P.nkept && unit; ++j) {
+            const double a = wsort[(size_t)(2 * j)], b = wsort[(size_t)(2 * j + 1)];
+            unit = std::fabs(a * a + b * b - 1.0) <= 1e-12;
+        }
+        if (unit) {
+            std::vector<float> ang((size_t)P.nkept);
+            for (int64_t j = 0; j < P.nkept; ++j)
+                ang[(size_t)j] = (float)(std::atan2(wsort[(size_t)(2 * j + 1)], wsort[(size_t)(2 * j)]) /
+                                         3.14159265358979323846);
+            P.asort32 = dalloc<float>((size_t)P.nkept);
+            h2d(P.asort32, ang.data(), (size_t)P.nkept * 4, s);
+            check_cuda(cudaStreamSynchronize(s), "angle upload");
+        }
     }
     P.ioff = dalloc<int64_t>((size_t)K + 1);
     h2d(P.ioff, P.h_ioff.data(), ((size_t)K + 1) * 8, s);

@@ -132,6 +132,8 @@ struct Plan {
     int32_t* tsort = nullptr;      // [nkept] sample index, pixel-major, ascending t
     double2* wsort64 = nullptr;    // [nkept] weights in sorted order (pol)
     float2* wsort32 = nullptr;     // [nkept]
+    float* asort32 = nullptr;      // [nkept] angle / pi of the sorted weights when every weight
+                                   // pair has unit norm (the FP32 scatter reads 4 bytes, not 8)
     int64_t* ioff = nullptr;       // [K+1]
     int32_t* ipsd = nullptr;       // [K]
     double* t0 = nullptr;          // [npsd] diagonal of each row

@@ -115,10 +115,25 @@ __device__ __forceinline__ T group_total(T v) {
     }
 }
 
-template <typename T, int NC, bool DOT, int LPP>
+// Weight pair of sorted sample j: read, or (ANG, FP32) formed from the stored angle a_j
+// (cos pi a_j, sin pi a_j) -- 4 bytes per sample instead of 8 for unit-norm weights.
+template <typename T, bool ANG>
+__device__ __forceinline__ typename V2<T>::type sorted_weight(const typename V2<T>::type* ws, const float* ang,
+                                                              int64_t j) {
+    if constexpr (ANG) {
+        float sv, cv;
+        sincospif(__ldg(ang + j), &sv, &cv);
+        return make_float2(cv, sv);
+    } else {
+        return __ldg(ws + j);
+    }
+}
+
+template <typename T, int NC, bool DOT, int LPP, bool ANG = false>
 __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t* __restrict__ off,
                                                                   const int32_t* __restrict__ tsort,
                                                                   const typename V2<T>::type* __restrict__ ws,
+                                                                  const float* __restrict__ ang,
                                                                   const T* __restrict__ z, T* __restrict__ w,
                                                                   int npix, const int* done, ScatterDot sd) {
     using W2 = typename V2<T>::type;
@@ -144,7 +159,7 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
             for (int u = 0; u < SCATTER_U; ++u) t[u] = __ldg(tsort + j + LPP * u);
             if constexpr (NC == 3) {
 #pragma unroll
-                for (int u = 0; u < SCATTER_U; ++u) ww[u] = __ldg(ws + j + LPP * u);
+                for (int u = 0; u < SCATTER_U; ++u) ww[u] = sorted_weight<T, ANG>(ws, ang, j + LPP * u);
             }
 #pragma unroll
             for (int u = 0; u < SCATTER_U; ++u) v[u] = z[t[u]];
@@ -161,7 +176,7 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
             const T v = z[__ldg(tsort + j)];
             a0 += v;
             if constexpr (NC == 3) {
-                const W2 ww = __ldg(ws + j);
+                const W2 ww = sorted_weight<T, ANG>(ws, ang, j);
                 a1 += ww.x * v;
                 a2 += ww.y * v;
             }
@@ -236,12 +251,20 @@ int scatter_blocks(const Plan& P) {
 template <typename T, bool DOT, int LPP>
 static void scatter_launch_lpp(const Plan& P, const T* z, T* w, const int* done, ScatterDot sd, cudaStream_t s) {
     const int g = scatter_blocks(P);
-    if (P.ncomp == 1)
-        scatter_kernel<T, 1, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, z, w, P.npix_obs,
-                                                                     done, sd);
-    else
-        scatter_kernel<T, 3, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), z,
-                                                                     w, P.npix_obs, done, sd);
+    if (P.ncomp == 1) {
+        scatter_kernel<T, 1, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, nullptr, z, w,
+                                                                     P.npix_obs, done, sd);
+        return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (P.asort32 != nullptr) {
+            scatter_kernel<T, 3, DOT, LPP, true><<<g, SCATTER_THREADS, 0, s>>>(
+                P.csr_off, P.tsort, nullptr, P.asort32, z, w, P.npix_obs, done, sd);
+            return;
+        }
+    }
+    scatter_kernel<T, 3, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), nullptr, z,
+                                                                 w, P.npix_obs, done, sd);
 }
 
 template <typename T, bool DOT>

@@ -220,6 +220,25 @@ def test_scatter_pixel_tiles(lanes):
     plan.close()
 
 
+def test_fp32_scatter_weights_from_angles_and_pairs():
+    # unit-norm weights: the FP32 scatter forms (cos, sin) from a stored angle; weights
+    # of another norm (a polarisation efficiency of 0.9 here) keep the stored pairs.
+    # Both against the oracle's P^T and A.
+    for eff in (1.0, 0.9):
+        scan = SCANS["P_ragged"]()
+        scan.weights = np.asarray(scan.weights) * eff
+        pr = oracle_problem(scan)
+        plan = _plan(scan)
+        rng = np.random.default_rng(23)
+        z = rng.standard_normal(pr.nt)
+        got = plan.scatter(_cuda(z, torch.float32), mm.MM_FP32).double().cpu().numpy()
+        assert _rel(got, pr.PT(z)) <= 2e-5, eff
+        x = rng.standard_normal(pr.n)
+        ax = plan.apply_A(_cuda(x, torch.float32), mm.MM_FP32).double().cpu().numpy()
+        assert _rel(ax, pr.A(x)) <= 3e-5, eff
+        plan.close()
+
+
 def test_scatter_pixel_tile_autotuned():
     scan = SCANS["c2_small"]()
     plan = _plan(scan, autotune=True)
