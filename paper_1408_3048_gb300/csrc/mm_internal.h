@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mm.h"
@@ -186,6 +187,31 @@ void static_scratch_setup(int device);
 void* static_scratch_ptr(int device);
 size_t static_scratch_bytes();
 void note_launch(int kernels = 1);                   // process-wide kernel launch counter
+
+// Launch with programmatic dependent launch: the kernel may be scheduled before the
+// previous kernel in the stream has finished, and must execute griddep_wait() before it
+// reads anything that kernel wrote (the wait returns once that kernel has completed and
+// its writes are visible).  Only kernels that wait first are launched this way.
+template <typename... KA, typename... A>
+void launch_pdl(void (*kern)(KA...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    check_cuda(cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...), "kernel launch (dependent)");
+}
+
+#ifdef __CUDACC__
+// Wait for the kernel before this one in the stream (programmatic dependent launch);
+// returns at once for a kernel launched the ordinary way.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
 void* dmalloc(size_t bytes);                         // throws Error{MM_ERR_OOM}
 void dfree(void* p);
 

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(SCATTER_THREADS) scatter_kernel(const int32_t*
                                                                   int npix, const int* done, ScatterDot sd) {
     using W2 = typename V2<T>::type;
     constexpr int PPW = 32 / LPP;                 // pixels per warp
+    griddep_wait();   // launched as a dependent launch: the previous kernel's outputs
     if (done != nullptr && *(volatile const int*)done) return;
     const int lane = threadIdx.x & 31;
     const int sl = lane % LPP, seg = lane / LPP;
@@ -251,20 +252,26 @@ int scatter_blocks(const Plan& P) {
 template <typename T, bool DOT, int LPP>
 static void scatter_launch_lpp(const Plan& P, const T* z, T* w, const int* done, ScatterDot sd, cudaStream_t s) {
     const int g = scatter_blocks(P);
+    using W2 = typename V2<T>::type;
+    const int32_t* off = P.csr_off;
+    const int32_t* ts = P.tsort;
+    const W2* nw = nullptr;
+    const float* na = nullptr;
     if (P.ncomp == 1) {
-        scatter_kernel<T, 1, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, nullptr, nullptr, z, w,
-                                                                     P.npix_obs, done, sd);
+        launch_pdl(scatter_kernel<T, 1, DOT, LPP>, g, SCATTER_THREADS, 0, s, off, ts, nw, na, z, w, P.npix_obs, done,
+                   sd);
         return;
     }
     if constexpr (sizeof(T) == 4) {
         if (P.asort32 != nullptr) {
-            scatter_kernel<T, 3, DOT, LPP, true><<<g, SCATTER_THREADS, 0, s>>>(
-                P.csr_off, P.tsort, nullptr, P.asort32, z, w, P.npix_obs, done, sd);
+            const float* ang = P.asort32;
+            launch_pdl(scatter_kernel<T, 3, DOT, LPP, true>, g, SCATTER_THREADS, 0, s, off, ts, nw, ang, z, w,
+                       P.npix_obs, done, sd);
             return;
         }
     }
-    scatter_kernel<T, 3, DOT, LPP><<<g, SCATTER_THREADS, 0, s>>>(P.csr_off, P.tsort, weights_sorted<T>(P), nullptr, z,
-                                                                 w, P.npix_obs, done, sd);
+    const W2* ws = weights_sorted<T>(P);
+    launch_pdl(scatter_kernel<T, 3, DOT, LPP>, g, SCATTER_THREADS, 0, s, off, ts, ws, na, z, w, P.npix_obs, done, sd);
 }
 
 template <typename T, bool DOT>

@@ -592,6 +592,7 @@ __device__ __forceinline__ void split_product(typename Cx<T>::type u1, typename 
 
 template <typename T, int LOGN, int NT, int MODE>
 __device__ __forceinline__ void toeplitz_os_tile(const TzArgs<T>& A) {
+    griddep_wait();   // launched as a dependent launch: the previous kernel's outputs
     using C2 = typename Cx<T>::type;
     constexpr int N = 1 << LOGN;
     constexpr int Q = N / 2;             // B/4
@@ -879,8 +880,7 @@ void launch_one(const TzArgs<T>& A, int ntiles, cudaStream_t s) {
         }
         B.pf_ahead *= occ;
     }
-    kern<<<(unsigned)((int64_t)ntiles * A.R), NT, smem, s>>>(B);
-    check_cuda(cudaGetLastError(), "toeplitz kernel launch");
+    launch_pdl(kern, (unsigned)((int64_t)ntiles * A.R), NT, smem, s, B);
     note_launch();
 }
 
