@@ -177,6 +177,74 @@ __device__ void coarse_solve(const PcgArgs<T>& a, double* v_sh) {
     __syncthreads();
 }
 
+// The iteration kernel's form of coarse_solve: E^-1 already in shared memory (einv, loaded
+// at the start of the step) and the r^T r total reduced in the same round of loads as the
+// first coarse slot (warp 0), so that the step waits on one round trip to the block
+// partials after its first grid barrier instead of three.  Sums in the same order as
+// grid_total and coarse_solve.  Returns r^T r; v_sh as coarse_solve.
+template <typename T>
+__device__ double coarse_solve_rr(const PcgArgs<T>& a, double* v_sh, const double* einv, double* sh) {
+    __shared__ double u_sh[KMAX];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = w; j < a.k; j += nw) {
+        const bool rr_too = j == 0;
+        const double* col = a.partial + S_COARSE + j;
+        double srr = 0.0;
+        if constexpr (sizeof(T) == 4) {
+            float hi = 0.f, lo = 0.f;
+            for (unsigned base = 0; base < gridDim.x; base += 256) {
+                float2 v[8];
+                double vr[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const unsigned b = base + l + 32u * t;
+                    v[t] = b < gridDim.x ? __ldcg(reinterpret_cast<const float2*>(col + (size_t)b * PSTRIDE))
+                                         : make_float2(0.f, 0.f);
+                    vr[t] = rr_too && b < gridDim.x ? __ldcg(a.partial + (size_t)b * PSTRIDE + S_RR) : 0.0;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) pair_add(hi, lo, v[t].x, v[t].y);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) srr += vr[t];
+            }
+            warp_pair_reduce(hi, lo);
+            if (l == 0) u_sh[j] = (double)hi + (double)lo;
+        } else {
+            double s = 0.0;
+            for (unsigned base = 0; base < gridDim.x; base += 256) {
+                double v[8], vr[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const unsigned b = base + l + 32u * t;
+                    v[t] = b < gridDim.x ? __ldcg(col + (size_t)b * PSTRIDE) : 0.0;
+                    vr[t] = rr_too && b < gridDim.x ? __ldcg(a.partial + (size_t)b * PSTRIDE + S_RR) : 0.0;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) s += v[t];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) srr += vr[t];
+            }
+            s = warp_sum64(s);
+            if (l == 0) u_sh[j] = s;
+        }
+        if (rr_too) {
+            srr = warp_sum64(srr);
+            if (l == 0) sh[0] = srr;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < a.k) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int j = 0; j < a.k; ++j) s = fma(einv[(size_t)j * a.k + threadIdx.x], u_sh[j], s);
+        v_sh[threadIdx.x] = s;
+    }
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
 // z = M_BD r (CM 0), M_BD (r - AZ v) + Z v (CM 1) or y + Z v with y = M_BD r in a.z
 // (CM 2) on this block's pixels; returns partial r^T z.  With a coarse space, G = 2 or 4
 // consecutive lanes share a pixel when the block has that many threads per pixel: lane
@@ -409,10 +477,14 @@ template <typename T, int NC, int CM>
 __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
     __shared__ double sh[40];   // [0] total, [1 + w] per-warp sums (up to 32 warps)
     __shared__ double v_sh[KMAX];
+    __shared__ double einv_sh[CM != 0 ? KMAX * KMAX : 1];
     if (*(volatile int*)&a.flags[F_DONE]) return;
     int p0, p1;
     block_pixels(a.npix, p0, p1);
     const int64_t e0 = (int64_t)p0 * NC, e1 = (int64_t)p1 * NC;
+    // E^-1 into shared memory now; it is read after the first grid barrier
+    if constexpr (CM != 0)
+        for (int i = threadIdx.x; i < a.k * a.k; i += blockDim.x) einv_sh[i] = __ldg(a.Einv + i);
     // p^T q comes from the scatter that formed q = A p (its last block summed it)
     const double pqt = __ldcg(a.scal + SC_PQ);
     const double rho = a.scal[SC_RHO];
@@ -446,7 +518,14 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
         coarse_partials<T, 2>(a, a.r, e0, e1);
     }
     if (!grid_sync(a.bar, a.flags, a.bar_absent, a.wait_ns)) return;
-    const double rrt = grid_total(a.partial, S_RR, sh);
+    // r^T r and (two-level) v = E^-1 Z^T r in one round of loads
+    double rrt;
+    if constexpr (CM != 0) {
+        if (a.k > 0) rrt = coarse_solve_rr(a, v_sh, einv_sh, sh);
+        else rrt = grid_total(a.partial, S_RR, sh);
+    } else {
+        rrt = grid_total(a.partial, S_RR, sh);
+    }
     const int it = a.flags[F_ITER] + 1;     // every block reads the same value here
     bool stop = false;
     int status = MM_OK;
@@ -472,8 +551,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_iter_kernel(PcgArgs<T> a) {
         }
         return;
     }
-    // phase C: z = M r, r^T z
-    if constexpr (CM != 0) coarse_solve(a, v_sh);
+    // phase C: z = M r, r^T z (v_sh holds v for the two-level forms)
     const DotAcc<T> rzacc = apply_precond<T, NC, CM>(a, v_sh, p0, p1);
     const double rz = block_total(rzacc, sh);
     if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * PSTRIDE + S_RZ] = rz;
