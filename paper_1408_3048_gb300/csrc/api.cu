@@ -649,19 +649,18 @@ static void build_plan(PlanHolder& P, const int32_t* pix, int64_t nt, int32_t np
         // unit-norm weights (cos 2 psi, sin 2 psi): the FP32 scatter forms them from the
         // angle, (cos pi a, sin pi a) with a = atan2(w2, w1) / pi rounded to FP32, which
         // halves its weight bytes (the weight is then within ~2e-7 of the FP64 pair)
-        bool unit = P.nkept > 0;
-        for (int64_t j = 0; j < P.nkept && unit; ++j) {
-            const double a = wsort[(size_t)(2 * j)], b = wsort[(size_t)(2 * j + 1)];
-            unit = std::fabs(a * a + b * b - 1.0) <= 1e-12;
-        }
-        if (unit) {
-            std::vector<float> ang((size_t)P.nkept);
-            for (int64_t j = 0; j < P.nkept; ++j)
-                ang[(size_t)j] = (float)(std::atan2(wsort[(size_t)(2 * j + 1)], wsort[(size_t)(2 * j)]) /
-                                         3.14159265358979323846);
+        if (P.nkept > 0) {
             P.asort32 = dalloc<float>((size_t)P.nkept);
-            h2d(P.asort32, ang.data(), (size_t)P.nkept * 4, s);
-            check_cuda(cudaStreamSynchronize(s), "angle upload");
+            std::unique_ptr<unsigned, void (*)(unsigned*)> bad(dalloc<unsigned>(1), [](unsigned* q) { dfree(q); });
+            check_cuda(cudaMemsetAsync(bad.get(), 0, 4, s), "memset");
+            launch_angles(P.wsort64, P.asort32, P.nkept, bad.get(), s);
+            unsigned hbad = 1;
+            check_cuda(cudaMemcpyAsync(&hbad, bad.get(), 4, cudaMemcpyDeviceToHost, s), "angle check");
+            check_cuda(cudaStreamSynchronize(s), "angle check");
+            if (hbad != 0) {
+                dfree(P.asort32);
+                P.asort32 = nullptr;
+            }
         }
     }
     P.ioff = dalloc<int64_t>((size_t)K + 1);

@@ -273,6 +273,7 @@ void launch_bd_build(const Plan& P, double* bd64, float* bd32, cudaStream_t s);
 void launch_apriori(const Plan& P, int r, double* Z, cudaStream_t s);
 template <typename T>
 void launch_bd_apply(const Plan& P, const T* r, T* z, cudaStream_t s);
+void launch_angles(const double2* w, float* ang, int64_t n, unsigned* bad, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
 // gradient helpers (grad.cu)

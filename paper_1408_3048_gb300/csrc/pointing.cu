@@ -116,7 +116,8 @@ __device__ __forceinline__ T group_total(T v) {
 }
 
 // Weight pair of sorted sample j: read, or (ANG, FP32) formed from the stored angle a_j
-// (cos pi a_j, sin pi a_j) -- 4 bytes per sample instead of 8 for unit-norm weights.
+// (cos pi a_j, sin pi a_j) -- 4 bytes per sample instead of 8 for unit-norm weights.  (A
+// table-driven form, a 513-entry table plus the angle-addition formula, measured no faster.)
 template <typename T, bool ANG>
 __device__ __forceinline__ typename V2<T>::type sorted_weight(const typename V2<T>::type* ws, const float* ang,
                                                               int64_t j) {
@@ -477,6 +478,25 @@ void launch_convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_
     if (n == 0) return;
     convert_kernel<<<grid_for(n, 256, 160), 256, 0, s>>>(a, b, n);
     check_cuda(cudaGetLastError(), "convert launch");
+    note_launch();
+}
+
+// ang[j] = atan2(w2, w1) / pi rounded to FP32 for the sorted weight pairs; *bad counts the
+// pairs whose squared norm is more than 1e-12 from 1 (the angle form is then not used)
+__global__ void angle_kernel(const double2* __restrict__ w, float* __restrict__ ang, int64_t n, unsigned* bad) {
+    unsigned nb = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = w[i];
+        ang[i] = (float)(atan2(v.y, v.x) * 0.31830988618379067154);   // 1 / pi
+        nb += fabs(v.x * v.x + v.y * v.y - 1.0) > 1e-12;
+    }
+    if (nb) atomicAdd(bad, nb);
+}
+
+void launch_angles(const double2* w, float* ang, int64_t n, unsigned* bad, cudaStream_t s) {
+    if (n == 0) return;
+    angle_kernel<<<grid_for(n, 256, 160), 256, 0, s>>>(w, ang, n, bad);
+    check_cuda(cudaGetLastError(), "angle launch");
     note_launch();
 }
 

@@ -233,6 +233,11 @@ def test_fp32_scatter_weights_from_angles_and_pairs():
         z = rng.standard_normal(pr.nt)
         got = plan.scatter(_cuda(z, torch.float32), mm.MM_FP32).double().cpu().numpy()
         assert _rel(got, pr.PT(z)) <= 2e-5, eff
+        # against the FP64 scatter of the same FP32-rounded values: the weights formed from
+        # the angle (table-driven, ~2e-7) and the FP32 sums stay within 1e-6
+        z32 = _cuda(z, torch.float32)
+        ref64 = plan.scatter(z32.double(), mm.MM_FP64).cpu().numpy()
+        assert _rel(got, ref64) <= 1e-6, eff
         x = rng.standard_normal(pr.n)
         ax = plan.apply_A(_cuda(x, torch.float32), mm.MM_FP32).double().cpu().numpy()
         assert _rel(ax, pr.A(x)) <= 3e-5, eff
