@@ -403,6 +403,35 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
     const bool whole = tile.pb[0] <= s0 && s0 + count <= tile.pe[0];
     const int64_t d0 = tile.d[0];
     const int sbase = 2 * pad<T>(tid >> 1) + (tid & 1);   // real slot of local position tid
+    if constexpr (sizeof(T) == 4 && MODE == 3 && NT % (2 << PadLog<T>::v) == 0) {
+        // FP32 I/Q/U from the packed map on a tile of one segment: indices and weights from
+        // base pointers with 32-bit offsets, eight samples a round (the map's one 16-byte
+        // load per sample leaves the registers for it)
+        if (whole && A.x4 != nullptr && PER % 8 == 0) {
+            const int32_t* pq = A.pixc + d0 + s0 + tid;
+            const float2* pw = A.w + d0 + s0 + tid;
+            constexpr int RSTEP = 2 * (NT / 2 + (NT >> (PadLog<T>::v + 1)));
+#pragma unroll 1
+            for (int base = 0; base < PER; base += 8) {
+                int q[8];
+                float2 w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) q[u] = __ldg(pq + (base + u) * NT);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = pw[(base + u) * NT];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float r = 0.f;
+                    if (q[u] >= 0) {
+                        const float4 m = __ldg(A.x4 + q[u]);
+                        r = m.x + w[u].x * m.y + w[u].y * m.z;
+                    }
+                    ar[sbase + (base + u) * RSTEP] = r;
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll 1
     for (int base = 0; base < PER; base += UMAX) {
         T v[UMAX];
