@@ -431,6 +431,45 @@ __device__ __forceinline__ void load_block(const TzArgs<T>& A, const Tile& tile,
             }
             return;
         }
+        // the same over a tile of several segments: per sample the segment's base pointers
+        // are selected (unused segments have pb = pe = TILE_NONE and are never selected)
+        if (A.x4 != nullptr && PER % 8 == 0) {
+            const int pb1 = tile.pb[1], pb2 = tile.pb[2];
+            const int32_t* q0 = A.pixc + tile.d[0];
+            const int32_t* q1 = A.pixc + (tile.pb[1] < tile.pe[1] ? tile.d[1] : 0);
+            const int32_t* q2 = A.pixc + (tile.pb[2] < tile.pe[2] ? tile.d[2] : 0);
+            const float2* w0 = A.w + tile.d[0];
+            const float2* w1 = A.w + (tile.pb[1] < tile.pe[1] ? tile.d[1] : 0);
+            const float2* w2 = A.w + (tile.pb[2] < tile.pe[2] ? tile.d[2] : 0);
+            constexpr int RSTEP = 2 * (NT / 2 + (NT >> (PadLog<T>::v + 1)));
+#pragma unroll 1
+            for (int base = 0; base < PER; base += 8) {
+                int q[8];
+                float2 w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int p = s0 + (base + u) * NT + tid;
+                    const int g = (p >= pb1) + (p >= pb2);
+                    const int lo = g == 0 ? tile.pb[0] : (g == 1 ? pb1 : pb2);
+                    const int hi = g == 0 ? tile.pe[0] : (g == 1 ? tile.pe[1] : tile.pe[2]);
+                    const bool in = p >= lo && p < hi;
+                    const int32_t* qb = g == 0 ? q0 : (g == 1 ? q1 : q2);
+                    const float2* wb = g == 0 ? w0 : (g == 1 ? w1 : w2);
+                    q[u] = in ? __ldg(qb + p) : -1;
+                    w[u] = in ? wb[p] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float r = 0.f;
+                    if (q[u] >= 0) {
+                        const float4 m = __ldg(A.x4 + q[u]);
+                        r = m.x + w[u].x * m.y + w[u].y * m.z;
+                    }
+                    ar[sbase + (base + u) * RSTEP] = r;
+                }
+            }
+            return;
+        }
     }
 #pragma unroll 1
     for (int base = 0; base < PER; base += UMAX) {
