@@ -200,7 +200,7 @@ mm_status mm_scatter(mm_plan_t plan, int precision, const void* z, void* w);
  * an I/Q/U plan x is first copied, packed four floats per pixel, into a plan-owned buffer
  * that the de-pointing gather reads (one 16-byte load per sample); like the other scratch
  * buffers of a plan it is used in stream order on the plan's stream.  With unit-norm
- * weights the FP32 scatter forms each weight pair from a stored FP32 angle (within ~2e-7
+ * weights the FP32 scatter forms each weight pair from a stored FP32 angle (within ~6e-7
  * of the pair); FP64 uses the pairs as given.
  * Errors of mm_gather, mm_apply_ninv, mm_scatter and mm_apply_A: MM_ERR_ARG for a null
  * vector, an unknown precision, or a precision with no overlap-save block for this

@@ -116,14 +116,16 @@ __device__ __forceinline__ T group_total(T v) {
 }
 
 // Weight pair of sorted sample j: read, or (ANG, FP32) formed from the stored angle a_j
-// (cos pi a_j, sin pi a_j) -- 4 bytes per sample instead of 8 for unit-norm weights.  (A
-// table-driven form, a 513-entry table plus the angle-addition formula, measured no faster.)
+// (cos pi a_j, sin pi a_j) -- 4 bytes per sample instead of 8 for unit-norm weights -- by
+// the hardware's fast sine and cosine (absolute error below 4e-7 on [-pi, pi]; a_j lies in
+// [-1, 1]).  (A table-driven form, a 513-entry table plus the angle-addition formula, was
+// no faster than sincospif; this one is.)
 template <typename T, bool ANG>
 __device__ __forceinline__ typename V2<T>::type sorted_weight(const typename V2<T>::type* ws, const float* ang,
                                                               int64_t j) {
     if constexpr (ANG) {
         float sv, cv;
-        sincospif(__ldg(ang + j), &sv, &cv);
+        __sincosf(3.14159265358979f * __ldg(ang + j), &sv, &cv);
         return make_float2(cv, sv);
     } else {
         return __ldg(ws + j);
