@@ -85,7 +85,7 @@ template void launch_gather<float>(const Plan&, const float*, float*, cudaStream
 // dependent TOD loads, so each lane keeps several random TOD reads in flight; every lane
 // still adds its samples j, j + LPP, j + 2 LPP, ... in ascending order (the result does
 // not depend on the unrolling, only on LPP).
-constexpr int SCATTER_U = 4;
+constexpr int SCATTER_U = 8;
 constexpr int SCATTER_THREADS = 256;
 
 // Optional fused dot product with the output (DOT): *pq = sum_q p_q . w_q.
